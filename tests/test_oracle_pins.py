@@ -1,0 +1,424 @@
+"""Pins of the FP64 oracle to things other than itself (CPU only).
+
+Each test checks the oracle against what the paper or the mathematics fixes:
+matrix identities of Eq. 2.2.4, the pressure identity behind Eq. 2.3.23, an
+independent Fourier (von Neumann) derivation of the linearised step from
+Eqs. 2.2.14-2.2.16 and 2.3.24, conservation laws, lattice symmetry, and the
+closed-form solutions of Sec. 4 (Taylor-Green, four-roll mill, periodic flow,
+Poiseuille) including the derived quantities of Eqs. 2.4.1-2.4.5.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2306_08216_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+CX = np.array([0.0, 1.0, 0.0, -1.0, 0.0])
+CY = np.array([0.0, 0.0, 1.0, 0.0, -1.0])
+
+
+def gre(a, b):
+    """Global relative error, Eq. 4.0."""
+    return np.abs(a - b).sum() / np.abs(b).sum()
+
+
+def gre_vel(f, u, v):
+    return (np.abs(f["u"] - u).sum() + np.abs(f["v"] - v).sum()) / (np.abs(u).sum() + np.abs(v).sum())
+
+
+# ---------------------------------------------------------------- algebra
+
+
+def closed_form_collision(s, sp, c=1.0):
+    """s' I + (s - s') P_c with P_c the orthogonal projector on span(c_x, c_y):
+    the collision matrix every orthogonal D2Q5 moment basis gives for
+    s0 = s3 = s4 = s', s1 = s2 = s (Sec. 3.1)."""
+    cx, cy = CX * c, CY * c
+    Pc = (np.outer(cx, cx) + np.outer(cy, cy)) / (2.0 * c * c)
+    return sp * np.eye(5) + (s - sp) * Pc
+
+
+@pytest.mark.parametrize("c", [1.0, 2.5])
+def test_collision_matrix_constraints(c):
+    o = Oracle(8, 8, nu=0.01, c=c)
+    for s in (0.3, 40.0, 4000.0):
+        Lt = o.collision_matrix(s)
+        e = np.ones(5)
+        # Eq. 2.2.4: sum_j e_j Lt_jk = s0 e_k and sum_j c_j Lt_jk = s c_k
+        np.testing.assert_allclose(e @ Lt, 1.5 * s * e, rtol=1e-13, atol=1e-12 * s)
+        np.testing.assert_allclose((CX * c) @ Lt, s * CX * c, rtol=1e-13, atol=1e-12 * s)
+        np.testing.assert_allclose((CY * c) @ Lt, s * CY * c, rtol=1e-13, atol=1e-12 * s)
+        np.testing.assert_allclose(Lt, closed_form_collision(s, 1.5 * s, c), rtol=1e-12, atol=1e-12 * s)
+
+
+def test_lambda_matrix_eigenvalues():
+    """Lambda = I - (I - dt/2 Lt)(I + dt/2 Lt)^-1 has eigenvalue
+    1 - (1 - dt l/2)/(1 + dt l/2) on each eigenspace of Lt (rate l)."""
+    nu = 1e-3
+    o = Oracle(16, 16, nu=nu)
+    s = o.cs2 / nu
+    dt = o.dt
+    lam = o.lambda_matrix()
+    Pc = (np.outer(CX, CX) + np.outer(CY, CY)) / 2.0
+    rho = lambda r: (1 - dt * r / 2) / (1 + dt * r / 2)
+    expect = (1 - rho(1.5 * s)) * (np.eye(5) - Pc) + (1 - rho(s)) * Pc
+    np.testing.assert_allclose(lam, expect, rtol=1e-12, atol=1e-14)
+
+
+def numpy_equilibrium(f, cs2, c=1.0):
+    """Eq. 2.2.5 with P from Eq. 2.3.23 (R = 0), written for f[alpha, j, ...]."""
+    u = f[0].sum(axis=0)
+    v = f[1].sum(axis=0)
+    first = (CX[:, None, None] * c * f[0]).sum(axis=0) + (CY[:, None, None] * c * f[1]).sum(axis=0)
+    P = (first - u * u - v * v) / 2.0
+    feq = np.empty_like(f)
+    for a, ub in enumerate((u, v)):
+        flx = ub * u + (P if a == 0 else 0.0)
+        fly = ub * v + (P if a == 1 else 0.0)
+        for j in range(5):
+            feq[a, j] = 0.2 * (ub + (CX[j] * c * flx + CY[j] * c * fly) / cs2)
+    return feq, u, v, P
+
+
+def test_pressure_from_fhat_equals_pressure_from_f():
+    """Eq. 2.3.23 defines P from f.  The oracle only holds fhat (Eq. 2.2.2);
+    evaluating the same formula on fhat must give the same u, v, P."""
+    nx = ny = 6
+    nu = 0.002
+    o = Oracle(nx, ny, nu=nu)
+    rng = np.random.default_rng(7)
+    f = 0.05 + 0.1 * rng.standard_normal((2, 5, ny, nx))
+    feq, u, v, P = numpy_equilibrium(f, o.cs2)
+    Lt = o.collision_matrix(o.cs2 / nu)
+    fhat = f + 0.5 * o.dt * np.einsum("jk,akyx->ajyx", Lt, f - feq)
+    o.set_state(fhat)
+    fl = o.fields()
+    np.testing.assert_allclose(fl["u"], u, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(fl["v"], v, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(fl["P"], P, rtol=1e-11, atol=1e-14)
+
+
+# ------------------------------------------------ independent linear symbol
+
+
+def mixed_symbol(theta, d, sgn, eta):
+    """Fourier symbol of Eqs. 2.2.12-2.2.13 on exp(i theta m)."""
+    cen = (np.exp(1j * theta) - np.exp(-1j * theta)) / (2 * d)
+    if sgn >= 0:
+        up = (3 - 4 * np.exp(-1j * theta) + np.exp(-2j * theta)) / (2 * d)
+    else:
+        up = -(3 - 4 * np.exp(1j * theta) + np.exp(2j * theta)) / (2 * d)
+    return eta * cen + (1 - eta) * up
+
+
+def amplification_matrix(kx, ky, dx, dy, dt, nu, c=1.0, eta=0.8, sr=1.5):
+    """One step of the scheme linearised about rest, for the Fourier mode
+    exp(i(kx x + ky y)), built from Eqs. 2.2.14, 2.2.15, 2.3.25, 2.2.16, 2.3.24
+    with the closed-form collision matrix and the linear part of Eq. 2.2.5."""
+    cs2 = 0.4 * c * c
+    s = cs2 / nu
+    cx, cy = CX * c, CY * c
+    I10 = np.eye(10)
+    Lt = np.kron(np.eye(2), closed_form_collision(s, sr * s, c))
+    Lam = I10 - (I10 - dt / 2 * Lt) @ np.linalg.inv(I10 + dt / 2 * Lt)
+    E = np.zeros((10, 10))  # feq = E f, quadratic terms dropped
+    for a in range(2):
+        ca = cx if a == 0 else cy
+        for j in range(5):
+            E[a * 5 + j, a * 5:a * 5 + 5] += 0.2
+            for b in range(2):
+                cb = cx if b == 0 else cy
+                E[a * 5 + j, b * 5:b * 5 + 5] += 0.2 * ca[j] / cs2 * 0.5 * cb
+    dvec = np.zeros(5, complex)
+    for j in range(5):
+        if cx[j] != 0:
+            dvec[j] += cx[j] * mixed_symbol(kx * dx, dx, cx[j], eta)
+        if cy[j] != 0:
+            dvec[j] += cy[j] * mixed_symbol(ky * dy, dy, cy[j], eta)
+    D = np.diag(np.concatenate([dvec, dvec]))
+    h = dt / 2
+    f_plus = (I10 - Lam) + Lam @ E
+    fbar_plus = (I10 - 0.75 * Lam) + 0.75 * Lam @ E
+    fbar = (I10 - h * D) @ fbar_plus
+    recover = np.linalg.inv(I10 + h / 2 * Lt) @ (I10 + h / 2 * Lt @ E)
+    return f_plus - dt * D @ recover @ fbar
+
+
+@pytest.mark.parametrize("eta,sr,c", [(0.8, 1.5, 1.0), (0.3, 1.0, 1.0), (1.0, 2.0, 2.0)])
+def test_linearised_step_matches_fourier_symbol(eta, sr, c):
+    nx, ny, lx, ly, nu, nst = 16, 12, 1.0, 0.9, 0.01, 5
+    o = Oracle(nx, ny, nu=nu, lx=lx, ly=ly, eta=eta, s_ratio=sr, c=c)
+    f0 = W.random_state(nx, ny, 1e-10, 11)
+    o.set_state(f0)
+    o.step(nst)
+    f1 = o.state()
+    F0 = np.fft.fft2(f0.reshape(10, ny, nx), axes=(1, 2))
+    F1 = np.fft.fft2(f1.reshape(10, ny, nx), axes=(1, 2))
+    err = ref = 0.0
+    for qy in range(ny):
+        for qx in range(nx):
+            kx = 2 * math.pi * np.fft.fftfreq(nx)[qx] * nx / lx
+            ky = 2 * math.pi * np.fft.fftfreq(ny)[qy] * ny / ly
+            G = amplification_matrix(kx, ky, lx / nx, ly / ny, o.dt, nu, c=c, eta=eta, sr=sr)
+            pred = np.linalg.matrix_power(G, nst) @ F0[:, qy, qx]
+            err += np.abs(pred - F1[:, qy, qx]).sum()
+            ref += np.abs(F1[:, qy, qx]).sum()
+    assert err / ref < 1e-8
+
+
+# ------------------------------------------------------- invariants
+
+
+def test_equilibrium_states_are_fixed_points():
+    n = 12
+    o = Oracle(n, n, nu=0.01)
+    z = np.zeros((n, n))
+    o.init(z, z, z)
+    o.step(3)
+    assert np.all(o.state() == 0.0)
+    o.init(z + 0.03, z - 0.02, z + 0.001)
+    s0 = o.state()
+    o.step(5)
+    np.testing.assert_allclose(o.state(), s0, rtol=0, atol=1e-16)
+
+
+def test_momentum_conserved_on_periodic_grid():
+    """F = 0, periodic: the difference operators telescope and collision keeps
+    the zeroth moments, so sum_x u and sum_x v are invariant (Eq. 2.3.7)."""
+    n = 24
+    o = Oracle(n, n + 4, nu=0.005, lx=1.0, ly=1.1)
+    u, v, p = W.random_fields(n, n + 4, 0.05, 3)
+    u += 0.01
+    o.init(u, v, p)
+    a = o.fields()
+    o.step(50)
+    b = o.fields()
+    assert abs(b["u"].sum() - a["u"].sum()) < 1e-13 * np.abs(a["u"]).sum()
+    assert abs(b["v"].sum() - a["v"].sum()) < 1e-13 * np.abs(a["v"]).sum()
+
+
+def test_quarter_turn_equivariance():
+    """D2Q5 and the upwind rule are symmetric under a 90-degree rotation:
+    rotating the initial fields rotates the solution, (u, v) -> (-v, u)."""
+    n = 16
+    u, v, p = W.random_fields(n, n, 0.05, 5)
+    yy, xx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+
+    def rot(a):  # A'[y', x'] = A[y, x] with x' = -y mod n, y' = x
+        out = np.empty_like(a)
+        out[xx, (-yy) % n] = a[yy, xx]
+        return out
+
+    o1 = Oracle(n, n, nu=0.01, eta=0.6)
+    o1.init(u, v, p)
+    o1.step(20)
+    o2 = Oracle(n, n, nu=0.01, eta=0.6)
+    o2.init(rot(-v), rot(u), rot(p))
+    o2.step(20)
+    f1, f2 = o1.fields(), o2.fields()
+    np.testing.assert_allclose(f2["u"], rot(-f1["v"]), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(f2["v"], rot(f1["u"]), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(f2["P"], rot(f1["P"]), rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------ closed-form solutions
+
+
+def test_taylor_green_decay():
+    """64^2, U0 = 0.01, nu = 0.01, CFL 0.5, 1000 steps: amplitude decays as
+    exp(-2 nu t) (t = 49.09, factor 0.3747)."""
+    n, nu, U0 = 64, 0.01, 0.01
+    o = Oracle(n, n, nu=nu, lx=2 * math.pi, ly=2 * math.pi)
+    o.init(*W.taylor_green(n, U0))
+    o.step(1000)
+    t = 1000 * o.dt
+    assert abs(math.exp(-2 * nu * t) - 0.3747) < 1e-4
+    f = o.fields()
+    ue, ve, _ = W.taylor_green_exact(n, t, nu, U0)
+    assert gre_vel(f, ue, ve) < 2e-3
+    amp = (f["u"] * ue).sum() / (ue * ue).sum()
+    assert abs(amp - 1.0) < 2e-3
+
+
+def test_second_order_convergence():
+    """Sec. 4.1: error O(dt^2 + dx^2) at fixed CFL (dt proportional to dx)."""
+    nu, U0, T = 0.01, 0.01, 20.0
+    errs = []
+    for n in (16, 32, 64):
+        o = Oracle(n, n, nu=nu, lx=2 * math.pi, ly=2 * math.pi)
+        o.init(*W.taylor_green(n, U0))
+        steps = int(round(T / o.dt))
+        o.step(steps)
+        ue, ve, _ = W.taylor_green_exact(n, steps * o.dt, nu, U0)
+        errs.append(gre_vel(o.fields(), ue, ve))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) > 1.9, (errs, orders)
+
+
+def test_four_roll_mill_and_derived_quantities():
+    """Sec. 4.1, Eqs. 4.1.1-4.1.3 (force sign of F2 that makes the printed
+    velocity steady): velocity, gradient, strain rate and vorticity from the
+    first moment of f^ne (Eqs. 2.4.1-2.4.5); P = 0."""
+    n, nu, U0 = 64, 0.01, 1e-4
+    u, v, p, Fx, Fy, g = W.four_roll_mill(n, U0, nu)
+    o = Oracle(n, n, nu=nu, lx=2 * math.pi, ly=2 * math.pi, force=(Fx, Fy))
+    o.init(u, v, p)
+    o.step(3000)
+    f = o.fields()
+    assert gre_vel(f, u, v) < 1.5e-3
+    for k in ("dudx", "dudy", "dvdx", "dvdy"):
+        assert gre(f[k], g[k]) < 3e-3, k
+    assert gre(f["Sxx"], g["dudx"]) < 3e-3 and gre(f["Syy"], g["dvdy"]) < 3e-3
+    assert np.abs(f["Sxy"]).max() < 1e-2 * np.abs(g["dudx"]).max()
+    assert gre(f["vorticity"], g["dvdx"] - g["dudy"]) < 3e-3
+    assert np.abs(f["div"]).max() < 1e-2 * np.abs(g["dudx"]).max()
+    assert np.abs(f["P"] - f["P"].mean()).max() < 1e-9
+    np.testing.assert_allclose(f["Omega_xy"], -0.5 * f["vorticity"], rtol=1e-12, atol=1e-20)
+    np.testing.assert_allclose(f["sigma_xy"], 2 * nu * f["Sxy"], rtol=1e-12, atol=1e-20)
+
+
+@pytest.mark.parametrize("nx,ny", [(32, 32), (64, 32)])
+def test_periodic_flow_uniform_and_anisotropic(nx, ny):
+    """Sec. 4.2, Eqs. 4.2.1-4.2.2, including the 64 x 32 grid (dx != dy)."""
+    nu, u0 = 0.01, 0.01
+    u, v, p, Fx, Fy, g = W.periodic_flow(nx, ny, u0=u0, nu=nu)
+    o = Oracle(nx, ny, nu=nu, force=(Fx, Fy))
+    z = np.zeros_like(u)
+    o.init(z, z, z)
+    o.step(int(8.0 / o.dt))
+    f = o.fields()
+    assert gre_vel(f, u, v) < 1e-2
+    assert gre(f["P"] - f["P"].mean(), p) < 0.1
+    for k in ("dudx", "dudy", "dvdx", "dvdy"):
+        assert gre(f[k], g[k]) < 2e-2, k
+
+
+def test_poiseuille_walls_table3():
+    """Sec. 4.3: channel with NEE walls, Eq. 4.3.1; GRE within a factor 3 of
+    Table 3 (nu = 0.01, F = 1e-4, CFL 0.5); gradient and vorticity fields."""
+    tab = json.load(open(os.path.join(GOLDEN, "table3_poiseuille_cfl_gre.json")))
+    n, nu, F = 32, 0.01, 1e-4
+    o = Oracle(n, n, nu=nu, walls=(False, True), force=(F, 0.0), cfl=0.5)
+    z = np.zeros((n, n))
+    o.init(z, z, z)
+    o.step(int(15 / (nu * math.pi ** 2) / o.dt) + 1)
+    f = o.fields()
+    y = W.wall_nodes(n, 1.0)
+    ue, dudy = W.poiseuille_exact(y, F, nu)
+    e = gre(f["u"], np.broadcast_to(ue[:, None], (n, n)))
+    ref = tab["nu_0.01"][tab["cfl"].index(0.5)]
+    assert ref / 3 < e < ref * 3, e
+    assert np.abs(f["v"]).max() < 1e-8 * ue.max()
+    assert np.abs(f["u"][[0, -1]]).max() < 1e-12 * ue.max()
+    inner = slice(1, n - 1)
+    assert gre(f["dudy"][inner], np.broadcast_to(dudy[inner, None], (n - 2, n))) < 1e-2
+    assert gre(f["vorticity"][inner], -np.broadcast_to(dudy[inner, None], (n - 2, n))) < 1e-2
+    assert np.abs(f["dudx"][inner]).max() < 1e-6 * np.abs(dudy).max()
+
+
+def test_poiseuille_refinement_reduces_error():
+    nu, F = 0.01, 1e-4
+    errs = []
+    for n in (16, 32):
+        o = Oracle(n, n, nu=nu, walls=(False, True), force=(F, 0.0))
+        z = np.zeros((n, n))
+        o.init(z, z, z)
+        o.step(int(15 / (nu * math.pi ** 2) / o.dt) + 1)
+        ue, _ = W.poiseuille_exact(W.wall_nodes(n, 1.0), F, nu)
+        errs.append(gre(o.fields()["u"][:, 0], ue))
+    assert errs[1] < 0.6 * errs[0]
+
+
+def test_poiseuille_diverges_where_table2_diverges():
+    """Table 2: at nu = 1e-3 and F = 1e-1 on 32 x 32 the scheme diverges."""
+    n = 32
+    o = Oracle(n, n, nu=1e-3, walls=(False, True), force=(1e-1, 0.0))
+    z = np.zeros((n, n))
+    o.init(z, z, z)
+    blew = False
+    for _ in range(20):
+        o.step(250)
+        u = o.fields()["u"]
+        if not np.all(np.isfinite(u)) or np.abs(u).max() > 10.0:
+            blew = True
+            break
+    assert blew
+
+
+# ------------------------------------------- grids and transformations
+
+
+def test_separable_grid_with_uniform_nodes_matches_uniform_path():
+    nx, ny = 20, 16
+    u, v, p = W.random_fields(nx, ny, 0.05, 9)
+    a = Oracle(nx, ny, nu=0.01, lx=1.0, ly=0.8)
+    b = Oracle(nx, ny, nu=0.01, grid="separable", x=W.periodic_nodes(nx, 1.0),
+               y=W.periodic_nodes(ny, 0.8), lx=1.0, ly=0.8)
+    assert abs(a.dt - b.dt) < 1e-15
+    for o in (a, b):
+        o.init(u, v, p)
+        o.step(10)
+    np.testing.assert_allclose(b.state(), a.state(), rtol=0, atol=1e-13)
+
+
+def test_curvilinear_scaled_map_matches_anisotropic_uniform():
+    """An axis-scaling map x = a xi, y = b eta gives metrics 1/a, 1/b."""
+    nx, ny = 18, 14
+    X, Y = np.meshgrid(W.wall_nodes(nx, 1.0), W.wall_nodes(ny, 0.7))
+    u, v, p = W.random_fields(nx, ny, 0.02, 4)
+    kw = dict(nu=0.01, walls=(True, True), u_wall=(0, 0, 0, 0.05))
+    a = Oracle(nx, ny, lx=1.0, ly=0.7, **kw)
+    b = Oracle(nx, ny, grid="curvilinear", x=X, y=Y, **kw)
+    for o in (a, b):
+        o.init(u, v, p)
+        o.step(10)
+    np.testing.assert_allclose(b.state(), a.state(), rtol=0, atol=1e-13)
+
+
+def test_stretched_poiseuille():
+    """tanh-clustered nodes across the channel (beta = 1.5)."""
+    ny, nx, nu, F = 33, 8, 0.01, 1e-4
+    y = W.tanh_nodes(ny, 1.5)
+    o = Oracle(nx, ny, nu=nu, grid="separable", x=W.periodic_nodes(nx, 1.0), y=y, lx=1.0,
+               walls=(False, True), force=(F, 0.0))
+    z = np.zeros((ny, nx))
+    o.init(z, z, z)
+    o.step(int(15 / (nu * math.pi ** 2) / o.dt) + 1)
+    ue, _ = W.poiseuille_exact(y, F, nu)
+    assert gre(o.fields()["u"][:, 0], ue) < 4e-2
+
+
+# --------------------------------------------------------- power law
+
+
+def test_power_law_index_one_is_newtonian_bitwise():
+    n = 16
+    u, v, p = W.random_fields(n, n, 0.05, 2)
+    a = Oracle(n, n, nu=0.01, walls=(True, True), u_wall=(0, 0, 0, 0.1))
+    b = Oracle(n, n, nu=0.01, walls=(True, True), u_wall=(0, 0, 0, 0.1),
+               power_law=(0.01, 1.0, 1e-5, 1.0))
+    for o in (a, b):
+        o.init(u, v, p)
+        o.step(7)
+    assert np.array_equal(a.state(), b.state())
+
+
+@pytest.mark.parametrize("n_index,K,G,c", [(1.5, 0.01, 1e-4, 1.0), (0.5, 1e-3, 2e-4, 4.0)])
+def test_power_law_poiseuille(n_index, K, G, c):
+    """Textbook closed form of a power-law channel flow (nu = K gdot^(n-1)).
+    The shear-thinning case has nu -> nu_max on the centre line; c = 4 keeps
+    the kinetic (Knudsen) error of that high-viscosity core small."""
+    ny, nx = 32, 5
+    o = Oracle(nx, ny, nu=K, walls=(False, True), force=(G, 0.0), c=c,
+               power_law=(K, n_index, 1e-4, 1.0))
+    z = np.zeros((ny, nx))
+    o.init(z, z, z)
+    o.step(int(400 / o.dt))
+    y = W.wall_nodes(ny, 1.0)
+    ue = W.power_law_poiseuille_exact(y, G, K, n_index)
+    assert gre(o.fields()["u"][:, 0], ue) < 5e-3
