@@ -1,0 +1,286 @@
+"""Benchmark of the fused MDF-FDLBM step (one JSON line on rank 0).
+
+Workload: periodic Taylor-Green vortex on a 4096 x 4096 uniform grid, FP32
+state and arithmetic, nu = 0.01, U0 = 0.01, CFL 0.5, eta = 0.8, s'/s = 1.5.
+One bench step = one time step of the method over the whole grid (one fused
+kernel launch).  The two state buffers (2 x 676 MB) are far larger than L2, so
+every step streams the state from HBM; no L2 flush is needed.
+
+  value      MLUPS (million lattice-node updates per second) of the whole job,
+             device-timed with CUDA events on the solver's stream
+  e2e        the same metric through the C ABI with host buffers: upload of
+             the initial fields from pinned host memory, the steps, and the
+             download of u, v, p to pinned host memory, all inside the timed
+             region
+  roofline   HBM roofline of the fused step: algorithmic bytes per node
+             update (state read once + written once) x nodes / launch time,
+             against the measured copy bandwidth of this GPU type
+  cpu_baseline  the FP64 CPU oracle timed on a bounded sample (rank 0, N = 1)
+
+--impl reference times the FP64 CPU oracle on the host cores instead (the
+reference arm of this method: there is no other implementation to run).
+Multi-GPU runs (torchrun, one rank per GPU) are independent replicas of the
+workload (weak scaling); the method needs no exchange between them.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline; time-to-residual 1e-8, warm-start+batch vs cold"
+NX = NY = 4096
+NU, U0 = 0.01, 0.01
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_taylor_green_4096_traffic.json")
+STEP_SOURCE = os.path.join(ROOT, "paper_2306_08216_gb300", "csrc", "mdf_step.cu")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fp:
+            d = json.load(fp)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ncu_traffic_per_launch():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    or None if the summary is missing or was taken on another kernel source."""
+    try:
+        with open(TRAFFIC_FILE) as fp:
+            d = json.load(fp)
+        with open(STEP_SOURCE, "rb") as fp:
+            digest = hashlib.sha256(fp.read()).hexdigest()[:16]
+    except (OSError, ValueError):
+        return None
+    if d.get("source_sha256_16") != digest:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def oracle_sample(steps, n=512):
+    """FP64 oracle on an n x n Taylor-Green grid: (MLUPS, threads, seconds)."""
+    from oracle.oracle import Oracle, max_threads
+    from paper_2306_08216_gb300 import workloads as W
+    o = Oracle(n, n, nu=NU, lx=2 * math.pi, ly=2 * math.pi)
+    o.init(*W.taylor_green(n, U0))
+    o.step(1)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return n * n * steps / dt / 1e6, max_threads(), dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from oracle.oracle import Oracle, max_threads
+    from paper_2306_08216_gb300 import workloads as W
+    n = 512
+    o = Oracle(n, n, nu=NU, lx=2 * math.pi, ly=2 * math.pi)
+    o.init(*W.taylor_green(n, U0))
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    sec = time.perf_counter() - t0
+    val = n * n * args.steps / sec / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "taylor_green_4096x4096_fp32", "sample": "512x512 Taylor-Green, one oracle step per bench step",
+                   "nu": NU, "U0": U0, "cfl": 0.5, "eta": 0.8},
+        "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": max_threads(), "kind": "oracle",
+                         "sample": "512x512 Taylor-Green, %d steps" % args.steps},
+        "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2306_08216_gb300 import build as B
+    from paper_2306_08216_gb300 import mdf
+    from paper_2306_08216_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    u, v, p = W.taylor_green(NX, U0)
+    solver = mdf.Solver(NX, NY, nu=NU, lx=2 * math.pi, ly=2 * math.pi, stream=stream)
+    solver.init(u, v, p)
+    solver.step(args.warmup)
+    solver.synchronize()
+    info = solver.launch_info()
+    bpn = solver.bytes_per_node()
+
+    # ---- device-timed run: K fused steps, CUDA events on the solver stream
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        solver.step(args.steps)
+        stop.record(stream)
+        stop.synchronize()
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(stop)
+    barrier()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    nodes = NX * NY
+    value = world * nodes * args.steps / (ms_max / 1e3) / 1e6
+    ms_step = ms_max / args.steps
+    peak, peak_kind = measured_peaks()
+    achieved = bpn * nodes / (ms / args.steps / 1e3) / 1e9  # GB/s of this rank's launches
+    r, drift = solver.residual()  # also checks for divergence
+
+    # ---- end-to-end through the C ABI with host buffers
+    pin = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory() for a in (u, v, p)]
+    outs = [torch.empty((NY, NX), dtype=torch.float32).pin_memory() for _ in range(3)]
+    e2e_steps = args.steps
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    solver.init(pin[0].numpy(), pin[1].numpy(), pin[2].numpy())
+    solver.step(e2e_steps)
+    res = solver.fields(["u", "v", "P"])
+    for o_, k in zip(outs, ("u", "v", "P")):
+        o_.numpy()[...] = res[k]
+    e2e_sec = time.perf_counter() - t0
+    te = torch.tensor([e2e_sec], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_val = world * nodes * e2e_steps / float(te.item()) / 1e6
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        mlups, cores, sec = oracle_sample(40, 512)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": "512x512 Taylor-Green, 40 steps (%.1f s)" % sec}
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "taylor_green_4096x4096_fp32", "nx": NX, "ny": NY, "nu": NU, "U0": U0, "cfl": 0.5,
+                   "eta": 0.8, "s_ratio": 1.5, "l2": "inputs larger than L2 (2 x 676 MB state), no flush",
+                   "parallelism": "replicas x%d" % world, "launch": info},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": ncu_traffic_per_launch(), "bytes_per_node": bpn,
+                     "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind},
+        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": 3 * nodes * 4 / e2e_steps,
+                "d2h_bytes_per_step": 3 * nodes * 4 / e2e_steps},
+        "gpu_launches": args.steps,
+        "clocks": clocks.summary(),
+        "cpu_baseline": cpu,
+        "check": {"residual": r, "drift_u": drift[0], "drift_v": drift[1]},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * mdf.h -- C ABI of the GB300 MDF-FDLBM library (libmdf.so).
+ *
+ * The library advances the multiple-distribution-function finite-difference
+ * lattice Boltzmann method (MDF-FDLBM) of Chen, Chai, Zhao and Shi
+ * (arXiv:2306.08216) for the 2-D incompressible Navier-Stokes equations
+ * written as convection-diffusion equations (Sec. 2.1, Eq. 2.1.2), on one GPU.
+ * One time step is Steps (1)-(4) of Sec. 2.2 with the simplified evolution
+ * equations of Remark 2 (Eqs. 2.3.24-2.3.25), the D2Q5 lattice of Sec. 3.1
+ * (Eq. 3.1.0), the MRT collision of Eq. 2.2.4 with s0 = s3 = s4 = s',
+ * s1 = s2 = s (Sec. 3.1), the linear equilibrium of Eq. 2.2.5, the mixed
+ * central/upwind differences of Eqs. 2.2.12-2.2.13 and the time step of
+ * Eq. 3.1.  The state is the two distributions fhat_{j,alpha}, alpha = u, v
+ * (the alpha = 0 equation is not evolved, Remark 1).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an mdf_status; the library never aborts, exits or
+ *    traps on the device.  mdf_last_error() gives a one-line reason.
+ *  - Input arrays are copied; the caller keeps ownership.  Output arrays are
+ *    owned by the caller.  `on_device` = 1 means the pointer is CUDA device
+ *    memory of the current device, 0 means host memory.
+ *  - Field arrays are FP32, row-major [ny][nx] (x fastest), unless stated.
+ *  - Device work is enqueued on the stream set by mdf_set_stream (default:
+ *    the legacy default stream) and is asynchronous unless stated.
+ *  - A context belongs to the device that was current at mdf_create; calls
+ *    must be made with that device current.  Contexts are not thread-safe.
+ */
+#ifndef MDF_H
+#define MDF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mdf_ctx mdf_ctx; /* opaque, library-owned */
+
+typedef enum {
+    MDF_OK = 0,
+    MDF_E_INVALID = 1,  /* bad argument; nothing was changed */
+    MDF_E_CUDA = 2,     /* a CUDA runtime/driver call failed */
+    MDF_E_NOMEM = 3,    /* device or host allocation failed */
+    MDF_E_DIVERGED = 4, /* NaN/Inf found in the velocity field */
+    MDF_E_TIMEOUT = 5,  /* a host wait or a bounded device wait ran out */
+    MDF_E_STATE = 6     /* call not valid in the current state */
+} mdf_status;
+
+enum { MDF_GRID_UNIFORM = 0, MDF_GRID_SEPARABLE = 1, MDF_GRID_CURVILINEAR = 2 };
+enum { MDF_BC_PERIODIC = 0, MDF_BC_WALL = 1 };
+enum { MDF_FORCE_NONE = 0, MDF_FORCE_CONSTANT = 1, MDF_FORCE_FIELD = 2 };
+
+/* Grid (Eq. 2.2.13 spacings; Sec. 4.2 anisotropic grids; coordinate
+ * transformation for the keyword of the abstract).
+ *  nx, ny  nodes per axis (>= 5: the stencil reaches two nodes each way).
+ *  kind    MDF_GRID_UNIFORM: spacing lx/nx on a periodic axis, lx/(nx-1) on
+ *          a walled axis (walls sit on the first and last node);
+ *          MDF_GRID_SEPARABLE: node coordinates x[nx], y[ny] (FP64);
+ *          MDF_GRID_CURVILINEAR: node coordinates x[ny*nx], y[ny*nx] (FP64,
+ *          row-major) of a body-fitted grid; the library forms the metric
+ *          coefficients xi_x, xi_y, eta_x, eta_y in FP64 on the GPU from
+ *          second-order differences of the coordinates.
+ *  lx, ly  extent (uniform) or period of a periodic axis (other kinds). */
+typedef struct {
+    int nx, ny;
+    int kind;
+    double lx, ly;
+    const double *x, *y;
+} mdf_grid;
+
+/* Fluid (Eq. 2.1.1).  Newtonian: nu > 0, relaxation rate s = cs^2/nu
+ * (Sec. 2.3).  power_law != 0: nu = K gdot^(n-1), gdot = sqrt(2 S:S) with S
+ * from the non-equilibrium first moment (Eqs. 2.4.1, 2.4.3), solved per node
+ * every step and clamped to [nu_min, nu_max]; `nu` must still be > 0 and
+ * is then unused. */
+typedef struct {
+    double nu;
+    int power_law;
+    double K, n;
+    double nu_min, nu_max;
+} mdf_fluid;
+
+/* Boundaries, sides ordered west, east, south, north.  type: MDF_BC_PERIODIC
+ * or MDF_BC_WALL (non-equilibrium extrapolation velocity wall, Secs. 4.3-4.4);
+ * both sides of an axis must have the same type.  Corner nodes take the
+ * west/east wall velocity. */
+typedef struct {
+    int type[4];
+    double u_wall[4], v_wall[4];
+} mdf_bc;
+
+/* Scheme parameters: lattice speed c (= |c_j|, Eq. 3.1.0), CFL number
+ * (Eq. 3.1, 0 < cfl < 1), mixed-scheme weight eta (Eq. 2.2.12, 0..1) and the
+ * ratio s'/s of the free rates (Sec. 4 uses 1.5).  A NULL params pointer
+ * selects c = 1, cfl = 0.5, eta = 0.8, s_ratio = 1.5. */
+typedef struct {
+    double c, cfl, eta, s_ratio;
+} mdf_params;
+
+/* Create a solver: validates the arguments (MDF_E_INVALID before any CUDA
+ * call), allocates two FP32 state buffers of 10 planes each on the current
+ * device, forms the grid metrics and dt = cfl * dx_min / c (Eq. 3.1), and
+ * sets the state to rest (u = v = p = 0).  *out receives the context. */
+mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc *bc,
+                      const mdf_params *params, mdf_ctx **out);
+
+/* Release every resource of the context (waits for its stream first). */
+void mdf_destroy(mdf_ctx *ctx);
+
+/* Stream for all later device work (a cudaStream_t; NULL = legacy stream). */
+mdf_status mdf_set_stream(mdf_ctx *ctx, void *cuda_stream);
+
+/* Body force F_alpha of Eq. 2.2.6 (F_{j,alpha} = w_j F_alpha).  mode:
+ * MDF_FORCE_NONE, MDF_FORCE_CONSTANT (fx, fy) or MDF_FORCE_FIELD (arrays
+ * Fx, Fy of nx*ny FP32, copied).  dF/dt is taken as zero. */
+mdf_status mdf_set_force(mdf_ctx *ctx, int mode, double fx, double fy,
+                         const float *Fx, const float *Fy, int on_device);
+
+/* Initial state fhat = feq(u, v, p) (Sec. 4: distributions start at
+ * equilibrium); wall nodes take the wall velocity.  Resets the step count
+ * and the residual snapshot. */
+mdf_status mdf_init_fields(mdf_ctx *ctx, const float *u, const float *v, const float *p,
+                           int on_device);
+
+/* Enqueue n time steps (Sec. 2.2 Steps (1)-(4)); one fused kernel launch per
+ * step.  Asynchronous. */
+mdf_status mdf_step(mdf_ctx *ctx, int n);
+
+/* Derived fields from the current state (Sec. 2.4).  mask selects fields by
+ * bit, out[] holds one nx*ny FP32 array per set bit in increasing bit order.
+ * Host outputs (on_device = 0) are complete on return. */
+enum {
+    MDF_FIELD_U = 1u << 0, MDF_FIELD_V = 1u << 1, MDF_FIELD_P = 1u << 2,        /* Eq. 2.3.23 */
+    MDF_FIELD_DUDX = 1u << 3, MDF_FIELD_DUDY = 1u << 4,                          /* Eq. 2.4.1 */
+    MDF_FIELD_DVDX = 1u << 5, MDF_FIELD_DVDY = 1u << 6,
+    MDF_FIELD_DIV = 1u << 7,                                                     /* Eq. 2.4.2 */
+    MDF_FIELD_SXX = 1u << 8, MDF_FIELD_SXY = 1u << 9, MDF_FIELD_SYY = 1u << 10,  /* Eq. 2.4.3 */
+    MDF_FIELD_SIGXX = 1u << 11, MDF_FIELD_SIGXY = 1u << 12, MDF_FIELD_SIGYY = 1u << 13, /* Eq. 2.4.4 */
+    MDF_FIELD_OMEGA = 1u << 14,                                                  /* Eq. 2.4.5, Omega_xy */
+    MDF_FIELD_VORT = 1u << 15,                                                   /* dv/dx - du/dy */
+    MDF_FIELD_NU = 1u << 16                                                      /* local viscosity */
+};
+mdf_status mdf_fields(mdf_ctx *ctx, unsigned mask, float *const *out, int on_device);
+
+/* Windowed residual r = ||U^n - U^m||_2 / ((n - m) ||U^n||_2), U = (u, v) over
+ * all nodes, accumulated in FP64, where m is the step of the previous call
+ * (or of mdf_init_fields); then U^m := U^n.  drift[0..1] = sum of u and of v
+ * over all nodes.  Synchronises the stream (bounded wait).  Returns
+ * MDF_E_DIVERGED if U holds NaN/Inf, MDF_E_STATE if no step was taken since
+ * the previous snapshot (r is then set to NaN). */
+mdf_status mdf_residual(mdf_ctx *ctx, double *residual, double drift[2]);
+
+/* Copy of the state fhat as FP32 [2][5][ny][nx] (alpha, j, y, x). */
+mdf_status mdf_get_distributions(mdf_ctx *ctx, float *out, int on_device);
+/* Replace the state by `in` (same layout). */
+mdf_status mdf_set_distributions(mdf_ctx *ctx, const float *in, int on_device);
+
+/* Wait for all enqueued work, at most timeout_s seconds (<= 0: 60 s).
+ * Returns MDF_E_TIMEOUT if the wait ran out or a bounded device wait gave up. */
+mdf_status mdf_synchronize(mdf_ctx *ctx, double timeout_s);
+
+/* Checkpoint: raw little-endian FP32 state plus a text header (grid size,
+ * step count, dt).  mdf_load requires a context of the same grid size. */
+mdf_status mdf_save(mdf_ctx *ctx, const char *path);
+mdf_status mdf_load(mdf_ctx *ctx, const char *path);
+
+double mdf_dt(const mdf_ctx *ctx);                 /* time step of Eq. 3.1 */
+long long mdf_steps_done(const mdf_ctx *ctx);
+const char *mdf_last_error(const mdf_ctx *ctx);    /* ctx may be NULL */
+
+/* Launch geometry of the fused step kernel: info[0] threads per block,
+ * info[1] output columns per block, info[2] rows per block, info[3] blocks in
+ * x, info[4] blocks in y, info[5] dynamic shared memory bytes,
+ * info[6] blocks resident per SM (occupancy query; 0 without a GPU). */
+mdf_status mdf_launch_info(const mdf_ctx *ctx, int info[8]);
+
+/* Algorithmic bytes moved per node update by the fused step (state read and
+ * written once, plus force/metric planes read once). */
+double mdf_bytes_per_node(const mdf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDF_H */

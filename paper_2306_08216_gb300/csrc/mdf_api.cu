@@ -1,0 +1,591 @@
+// mdf_api.cu -- host runtime behind the C ABI of include/mdf.h.
+//
+// Owns the device state (two FP32 buffers of 10 padded planes), the TMA
+// descriptors of both buffers, the launch plan of the fused step, the grid
+// metrics and force planes, and the FP64 residual machinery.  Argument
+// validation happens before any CUDA call, so MDF_E_INVALID never touches
+// the GPU.
+#include <cudaTypedefs.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+#include <chrono>
+#include <thread>
+
+#include "../../include/mdf.h"
+#include "mdf_aux.cuh"
+#include "mdf_internal.cuh"
+
+using namespace mdf;
+
+struct mdf_ctx {
+    int dev = 0, num_sms = 0;
+    int nx = 0, ny = 0, kind = 0, xwall = 0, ywall = 0;
+    double lx = 0, ly = 0;
+    mdf_fluid fluid{};
+    mdf_bc bc{};
+    mdf_params prm{};
+    double cs2 = 0, dt = 0, dxmin = 0;
+    int pitch = 0;
+    long long plane = 0;
+    float *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    float *kxv = nullptr, *kyv = nullptr;
+    float *mxx = nullptr, *mxy = nullptr, *mex = nullptr, *mey = nullptr;
+    float *Fxp = nullptr, *Fyp = nullptr;
+    int force_mode = 0;
+    double fx = 0, fy = 0;
+    float *snap_u = nullptr, *snap_v = nullptr;
+    long long snap_step = 0;
+    double *partials = nullptr, *result = nullptr, *h_result = nullptr;
+    int *err = nullptr;
+    float *scratch = nullptr;  // dense staging for host transfers
+    size_t scratch_bytes = 0;
+    CUtensorMap tmap[2];
+    StepPlan plan{};
+    StepArgs args{};
+    AuxArgs aux{};
+    cudaStream_t stream = nullptr;
+    long long steps = 0;
+    char last_error[256] = {0};
+};
+
+static char g_create_error[256] = {0};
+
+static mdf_status fail(mdf_ctx *c, mdf_status st, const char *fmt, ...) {
+    char *dst = c ? c->last_error : g_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define CK(ctx, call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MDF_E_NOMEM : MDF_E_CUDA,       \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+static bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
+
+static void free_ctx(mdf_ctx *c) {
+    if (!c) return;
+    float *fp[] = {c->buf[0], c->buf[1], c->kxv, c->kyv, c->mxx, c->mxy, c->mex, c->mey,
+                   c->Fxp, c->Fyp, c->snap_u, c->snap_v, c->scratch};
+    for (float *p : fp)
+        if (p) cudaFree(p);
+    if (c->partials) cudaFree(c->partials);
+    if (c->result) cudaFree(c->result);
+    if (c->err) cudaFree(c->err);
+    if (c->h_result) cudaFreeHost(c->h_result);
+    delete c;
+}
+
+static mdf_status encode_maps(mdf_ctx *c) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        CK(c, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn)
+            return fail(c, MDF_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    for (int b = 0; b < 2; ++b) {
+        cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->ny, (cuuint64_t)NPLANES};
+        cuuint64_t strides[2] = {(cuuint64_t)c->pitch * 4, (cuuint64_t)c->plane * 4};
+        cuuint32_t box[3] = {(cuuint32_t)c->plan.NT, 1, (cuuint32_t)NPLANES};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = encode(&c->tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->buf[b], dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(c, MDF_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    return MDF_OK;
+}
+
+static void fill_rates(mdf_ctx *c) {
+    const double s = c->cs2 / c->fluid.nu, sp = c->prm.s_ratio * s, dt = c->dt;
+    auto rho = [&](double l) { return (1.0 - 0.5 * dt * l) / (1.0 + 0.5 * dt * l); };
+    auto kap = [&](double l) { return 1.0 / (1.0 + 0.25 * dt * l); };
+    StepArgs &a = c->args;
+    a.rpp = (float)rho(sp);
+    a.rp = (float)rho(s);
+    a.rbp = (float)(0.25 * (1.0 + 3.0 * rho(sp)));
+    a.rb = (float)(0.25 * (1.0 + 3.0 * rho(s)));
+    a.rkp = (float)kap(sp);
+    a.rk = (float)kap(s);
+}
+
+static mdf_status ensure_scratch(mdf_ctx *c, size_t bytes) {
+    if (c->scratch_bytes >= bytes) return MDF_OK;
+    if (c->scratch) cudaFree(c->scratch);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+    CK(c, cudaMalloc(&c->scratch, bytes));
+    c->scratch_bytes = bytes;
+    return MDF_OK;
+}
+
+static mdf_status wait_stream(mdf_ctx *c, double timeout_s) {
+    if (timeout_s <= 0) timeout_s = 60.0;
+    cudaEvent_t ev;
+    CK(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, c->stream);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(ev);
+        return fail(c, MDF_E_CUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    while (true) {
+        e = cudaEventQuery(ev);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) {
+            cudaEventDestroy(ev);
+            return fail(c, MDF_E_CUDA, "stream work failed: %s", cudaGetErrorString(e));
+        }
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) {
+            cudaEventDestroy(ev);
+            return fail(c, MDF_E_TIMEOUT, "stream did not finish within %.1f s", timeout_s);
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    cudaEventDestroy(ev);
+    int h_err = 0;
+    CK(c, cudaMemcpy(&h_err, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h_err != 0) return fail(c, MDF_E_TIMEOUT, "a bounded device wait gave up (code %d)", h_err);
+    return MDF_OK;
+}
+
+extern "C" {
+
+mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc *bc, const mdf_params *params,
+                      mdf_ctx **out) {
+    if (!out) return fail(nullptr, MDF_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!grid || !fluid || !bc) return fail(nullptr, MDF_E_INVALID, "grid, fluid and bc are required");
+    if (grid->nx < 5 || grid->ny < 5) return fail(nullptr, MDF_E_INVALID, "nx, ny must be >= 5");
+    if ((long long)grid->nx * grid->ny > (1ll << 31))
+        return fail(nullptr, MDF_E_INVALID, "grid too large (nx*ny > 2^31)");
+    if (grid->kind < 0 || grid->kind > 2) return fail(nullptr, MDF_E_INVALID, "unknown grid kind %d", grid->kind);
+    for (int s = 0; s < 4; ++s)
+        if (bc->type[s] != MDF_BC_PERIODIC && bc->type[s] != MDF_BC_WALL)
+            return fail(nullptr, MDF_E_INVALID, "unknown boundary type on side %d", s);
+    if (bc->type[0] != bc->type[1] || bc->type[2] != bc->type[3])
+        return fail(nullptr, MDF_E_INVALID, "both sides of an axis need the same boundary type");
+    const int xwall = bc->type[0] == MDF_BC_WALL, ywall = bc->type[2] == MDF_BC_WALL;
+    if (grid->kind == MDF_GRID_UNIFORM && (!finite_pos(grid->lx) || !finite_pos(grid->ly)))
+        return fail(nullptr, MDF_E_INVALID, "uniform grid needs lx, ly > 0");
+    if (grid->kind != MDF_GRID_UNIFORM) {
+        if (!grid->x || !grid->y) return fail(nullptr, MDF_E_INVALID, "grid coordinates are required");
+        if ((!xwall && !finite_pos(grid->lx)) || (!ywall && !finite_pos(grid->ly)))
+            return fail(nullptr, MDF_E_INVALID, "periodic axes of a coordinate grid need their period");
+    }
+    if (!finite_pos(fluid->nu)) return fail(nullptr, MDF_E_INVALID, "nu must be > 0");
+    if (fluid->power_law) {
+        if (!finite_pos(fluid->K) || !finite_pos(fluid->n) || !finite_pos(fluid->nu_min) ||
+            !finite_pos(fluid->nu_max) || fluid->nu_min > fluid->nu_max)
+            return fail(nullptr, MDF_E_INVALID, "power law needs K, n > 0 and 0 < nu_min <= nu_max");
+    }
+    mdf_params prm = params ? *params : mdf_params{1.0, 0.5, 0.8, 1.5};
+    if (!finite_pos(prm.c)) return fail(nullptr, MDF_E_INVALID, "c must be > 0");
+    if (!(prm.cfl > 0 && prm.cfl < 1)) return fail(nullptr, MDF_E_INVALID, "cfl must be in (0, 1)");
+    if (!(prm.eta >= 0 && prm.eta <= 1)) return fail(nullptr, MDF_E_INVALID, "eta must be in [0, 1]");
+    if (!finite_pos(prm.s_ratio)) return fail(nullptr, MDF_E_INVALID, "s_ratio must be > 0");
+    for (int s = 0; s < 4; ++s)
+        if (!isfinite(bc->u_wall[s]) || !isfinite(bc->v_wall[s]))
+            return fail(nullptr, MDF_E_INVALID, "wall velocities must be finite");
+
+    mdf_ctx *c = new mdf_ctx();
+    c->nx = grid->nx;
+    c->ny = grid->ny;
+    c->kind = grid->kind;
+    c->xwall = xwall;
+    c->ywall = ywall;
+    c->lx = grid->lx;
+    c->ly = grid->ly;
+    c->fluid = *fluid;
+    c->bc = *bc;
+    c->prm = prm;
+    c->cs2 = 0.4 * prm.c * prm.c;  // second moment of the D2Q5 weights (Eq. 2.3.4)
+
+#define CKC(call)                                          \
+    do {                                                   \
+        mdf_status s_ = (call);                            \
+        if (s_ != MDF_OK) {                                \
+            strncpy(g_create_error, c->last_error, 255);   \
+            free_ctx(c);                                   \
+            return s_;                                     \
+        }                                                  \
+    } while (0)
+#define CKE(call) CKC(([&]() -> mdf_status { CK(c, call); return MDF_OK; })())
+
+    CKE(cudaGetDevice(&c->dev));
+    CKE(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
+    const int metric = grid->kind;
+    CKE(step_plan(metric, fluid->power_law ? 1 : 0, c->nx, c->ny, c->num_sms, &c->plan));
+    c->pitch = step_pitch(c->nx, c->plan.W);
+    c->plane = (long long)c->pitch * c->ny;
+    const size_t state_bytes = (size_t)NPLANES * c->plane * sizeof(float);
+    for (int b = 0; b < 2; ++b) {
+        CKE(cudaMalloc(&c->buf[b], state_bytes));
+        CKE(cudaMemset(c->buf[b], 0, state_bytes));
+    }
+    const size_t N = (size_t)c->nx * c->ny;
+    CKE(cudaMalloc(&c->snap_u, N * sizeof(float)));
+    CKE(cudaMalloc(&c->snap_v, N * sizeof(float)));
+    CKE(cudaMalloc(&c->err, sizeof(int)));
+    CKE(cudaMemset(c->err, 0, sizeof(int)));
+    CKE(cudaMalloc(&c->result, 8 * sizeof(double)));
+    CKE(cudaMallocHost(&c->h_result, 8 * sizeof(double)));
+
+    AuxArgs &x = c->aux;
+    x.nx = c->nx; x.ny = c->ny; x.pitch = c->pitch; x.plane = c->plane;
+    x.xwall = xwall; x.ywall = ywall; x.lx = grid->lx; x.ly = grid->ly;
+    x.c = (float)prm.c; x.inv2c = (float)(0.5 / prm.c);
+    for (int s = 0; s < 4; ++s) { x.uw[s] = (float)bc->u_wall[s]; x.vw[s] = (float)bc->v_wall[s]; }
+    x.power_law = fluid->power_law ? 1 : 0;
+    x.nu = (float)fluid->nu; x.K = (float)fluid->K; x.n_index = (float)fluid->n;
+    x.nu_min = (float)fluid->nu_min; x.nu_max = (float)fluid->nu_max;
+    CKE(cudaMalloc(&c->partials, (size_t)aux_residual_blocks(x) * 5 * sizeof(double)));
+
+    // Grid metrics (FP64 on the GPU) and the time step of Eq. 3.1.
+    if (grid->kind == MDF_GRID_UNIFORM) {
+        const double dx = xwall ? grid->lx / (c->nx - 1) : grid->lx / c->nx;
+        const double dy = ywall ? grid->ly / (c->ny - 1) : grid->ly / c->ny;
+        c->dxmin = fmin(dx, dy);
+        c->args.kx = (float)(prm.c / dx);
+        c->args.ky = (float)(prm.c / dy);
+    } else {
+        const size_t ncoord = grid->kind == MDF_GRID_SEPARABLE ? (size_t)(c->nx + c->ny) : 2 * N;
+        double *dcoord = nullptr, *dedge = nullptr;
+        CKE(cudaMalloc(&dcoord, ncoord * sizeof(double)));
+        const size_t nedge = grid->kind == MDF_GRID_SEPARABLE ? (size_t)(c->nx + c->ny) : N;
+        mdf_status st = MDF_OK;
+        do {
+            cudaError_t e = cudaMalloc(&dedge, nedge * sizeof(double));
+            if (e != cudaSuccess) { st = fail(c, MDF_E_NOMEM, "metric scratch"); break; }
+            double *hedge = (double *)malloc(nedge * sizeof(double));
+            if (!hedge) { st = fail(c, MDF_E_NOMEM, "host metric scratch"); break; }
+            if (grid->kind == MDF_GRID_SEPARABLE) {
+                e = cudaMemcpy(dcoord, grid->x, c->nx * sizeof(double), cudaMemcpyHostToDevice);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(dcoord + c->nx, grid->y, c->ny * sizeof(double), cudaMemcpyHostToDevice);
+                if (e == cudaSuccess) e = cudaMalloc(&c->kxv, c->pitch * sizeof(float));
+                if (e == cudaSuccess) e = cudaMalloc(&c->kyv, c->ny * sizeof(float));
+                if (e == cudaSuccess)
+                    e = aux_metrics1d(x, dcoord, dcoord + c->nx, prm.c, c->kxv, c->kyv, dedge, 0);
+            } else {
+                e = cudaMemcpy(dcoord, grid->x, N * sizeof(double), cudaMemcpyHostToDevice);
+                if (e == cudaSuccess) e = cudaMemcpy(dcoord + N, grid->y, N * sizeof(double), cudaMemcpyHostToDevice);
+                const size_t mp = (size_t)c->pitch * c->ny * sizeof(float);
+                if (e == cudaSuccess) e = cudaMalloc(&c->mxx, mp);
+                if (e == cudaSuccess) e = cudaMalloc(&c->mxy, mp);
+                if (e == cudaSuccess) e = cudaMalloc(&c->mex, mp);
+                if (e == cudaSuccess) e = cudaMalloc(&c->mey, mp);
+                if (e == cudaSuccess)
+                    e = aux_metrics2d(x, dcoord, dcoord + N, prm.c, c->mxx, c->mxy, c->mex, c->mey, dedge, 0);
+            }
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e == cudaSuccess) e = cudaMemcpy(hedge, dedge, nedge * sizeof(double), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                free(hedge);
+                st = fail(c, MDF_E_CUDA, "metric setup: %s", cudaGetErrorString(e));
+                break;
+            }
+            double m = INFINITY;
+            for (size_t i = 0; i < nedge; ++i) m = fmin(m, hedge[i]);
+            free(hedge);
+            if (!(m > 0 && isfinite(m))) { st = fail(c, MDF_E_INVALID, "degenerate grid (min edge %g)", m); break; }
+            c->dxmin = m;
+        } while (0);
+        cudaFree(dcoord);
+        if (dedge) cudaFree(dedge);
+        CKC(st);
+    }
+    c->dt = prm.cfl * c->dxmin / prm.c;  // Eq. 3.1
+
+    StepArgs &a = c->args;
+    a.nx = c->nx; a.ny = c->ny; a.pitch = c->pitch; a.plane = c->plane;
+    a.W = c->plan.W; a.H = c->plan.H;
+    a.xwall = xwall; a.ywall = ywall;
+    a.c = (float)prm.c; a.inv2c = (float)(0.5 / prm.c);
+    a.dt = (float)c->dt; a.h = (float)(0.5 * c->dt);
+    const double eta = prm.eta;
+    a.a1 = (float)(0.5 * eta);
+    a.a0 = (float)(1.5 * (1.0 - eta));
+    a.am1 = (float)(-0.5 * (4.0 - 3.0 * eta));
+    a.am2 = (float)(0.5 * (1.0 - eta));
+    a.kxv = c->kxv; a.kyv = c->kyv;
+    a.mxx = c->mxx; a.mxy = c->mxy; a.mex = c->mex; a.mey = c->mey;
+    fill_rates(c);
+    a.power_law = fluid->power_law ? 1 : 0;
+    a.K = (float)fluid->K; a.n_index = (float)fluid->n; a.nu_min = (float)fluid->nu_min;
+    a.nu_max = (float)fluid->nu_max; a.cs2 = (float)c->cs2; a.s_ratio = (float)prm.s_ratio;
+    a.a_pl = (float)(0.5 * c->cs2 * c->dt);
+    a.force_mode = 0;
+    for (int s = 0; s < 4; ++s) { a.uw[s] = x.uw[s]; a.vw[s] = x.vw[s]; }
+    a.err = c->err;
+    x.a_pl = a.a_pl;
+    CKC(encode_maps(c));
+
+    // Rest state.
+    CKE(ensure_scratch(c, 3 * N * sizeof(float)) == MDF_OK ? cudaSuccess : cudaErrorMemoryAllocation);
+    CKE(cudaMemset(c->scratch, 0, 3 * N * sizeof(float)));
+    CKE(aux_init(x, c->scratch, c->scratch + N, c->scratch + 2 * N, c->buf[0], 0));
+    CKE(aux_snapshot(x, c->buf[0], c->snap_u, c->snap_v, 0));
+    CKE(cudaDeviceSynchronize());
+    c->cur = 0;
+    *out = c;
+    return MDF_OK;
+#undef CKE
+#undef CKC
+}
+
+void mdf_destroy(mdf_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+}
+
+mdf_status mdf_set_stream(mdf_ctx *c, void *stream) {
+    if (!c) return MDF_E_INVALID;
+    c->stream = (cudaStream_t)stream;
+    return MDF_OK;
+}
+
+// Copy caller arrays (host or device) into the dense staging buffer.
+static mdf_status stage_in(mdf_ctx *c, const float *const *src, int count, int on_device) {
+    const size_t N = (size_t)c->nx * c->ny;
+    mdf_status s = ensure_scratch(c, (size_t)count * N * sizeof(float));
+    if (s != MDF_OK) return s;
+    for (int i = 0; i < count; ++i)
+        CK(c, cudaMemcpyAsync(c->scratch + i * N, src[i], N * sizeof(float),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    return MDF_OK;
+}
+
+mdf_status mdf_set_force(mdf_ctx *c, int mode, double fx, double fy, const float *Fx, const float *Fy,
+                         int on_device) {
+    if (!c) return MDF_E_INVALID;
+    if (mode < MDF_FORCE_NONE || mode > MDF_FORCE_FIELD) return fail(c, MDF_E_INVALID, "unknown force mode");
+    if (mode == MDF_FORCE_CONSTANT && (!isfinite(fx) || !isfinite(fy)))
+        return fail(c, MDF_E_INVALID, "force must be finite");
+    if (mode == MDF_FORCE_FIELD) {
+        if (!Fx || !Fy) return fail(c, MDF_E_INVALID, "force field arrays are required");
+        const size_t pb = (size_t)c->pitch * c->ny * sizeof(float);
+        if (!c->Fxp) CK(c, cudaMalloc(&c->Fxp, pb));
+        if (!c->Fyp) CK(c, cudaMalloc(&c->Fyp, pb));
+        const float *src[2] = {Fx, Fy};
+        mdf_status s = stage_in(c, src, 2, on_device);
+        if (s != MDF_OK) return s;
+        const size_t N = (size_t)c->nx * c->ny;
+        CK(c, aux_pad_field(c->aux, c->scratch, c->Fxp, c->stream));
+        CK(c, aux_pad_field(c->aux, c->scratch + N, c->Fyp, c->stream));
+    }
+    c->force_mode = mode;
+    c->args.force_mode = mode;
+    c->args.Fx = (float)fx;
+    c->args.Fy = (float)fy;
+    c->args.Fxp = c->Fxp;
+    c->args.Fyp = c->Fyp;
+    return MDF_OK;
+}
+
+mdf_status mdf_init_fields(mdf_ctx *c, const float *u, const float *v, const float *p, int on_device) {
+    if (!c) return MDF_E_INVALID;
+    if (!u || !v || !p) return fail(c, MDF_E_INVALID, "u, v, p are required");
+    const float *src[3] = {u, v, p};
+    mdf_status s = stage_in(c, src, 3, on_device);
+    if (s != MDF_OK) return s;
+    const size_t N = (size_t)c->nx * c->ny;
+    c->cur = 0;
+    CK(c, aux_init(c->aux, c->scratch, c->scratch + N, c->scratch + 2 * N, c->buf[0], c->stream));
+    CK(c, aux_snapshot(c->aux, c->buf[0], c->snap_u, c->snap_v, c->stream));
+    c->steps = 0;
+    c->snap_step = 0;
+    if (!on_device) return wait_stream(c, 0);
+    return MDF_OK;
+}
+
+mdf_status mdf_step(mdf_ctx *c, int n) {
+    if (!c) return MDF_E_INVALID;
+    if (n < 0) return fail(c, MDF_E_INVALID, "n must be >= 0");
+    for (int i = 0; i < n; ++i) {
+        c->args.fout = c->buf[1 - c->cur];
+        CK(c, step_launch(&c->tmap[c->cur], c->args, c->kind, c->plan, c->stream));
+        c->cur = 1 - c->cur;
+        ++c->steps;
+    }
+    return MDF_OK;
+}
+
+mdf_status mdf_fields(mdf_ctx *c, unsigned mask, float *const *out, int on_device) {
+    if (!c) return MDF_E_INVALID;
+    if (mask >> 17) return fail(c, MDF_E_INVALID, "unknown field bits in mask");
+    if (mask && !out) return fail(c, MDF_E_INVALID, "out is NULL");
+    const size_t N = (size_t)c->nx * c->ny;
+    int count = 0;
+    for (int q = 0; q < 17; ++q)
+        if (mask & (1u << q)) {
+            if (!out[count]) return fail(c, MDF_E_INVALID, "output %d is NULL", count);
+            ++count;
+        }
+    if (!count) return MDF_OK;
+    FieldPtrs dst;
+    if (!on_device) {
+        mdf_status s = ensure_scratch(c, (size_t)count * N * sizeof(float));
+        if (s != MDF_OK) return s;
+    }
+    int k = 0;
+    for (int q = 0; q < 17; ++q) {
+        dst.p[q] = nullptr;
+        if (mask & (1u << q)) {
+            dst.p[q] = on_device ? out[k] : c->scratch + (size_t)k * N;
+            ++k;
+        }
+    }
+    CK(c, aux_fields(c->aux, c->buf[c->cur], dst, c->stream));
+    if (!on_device) {
+        for (int i = 0; i < count; ++i)
+            CK(c, cudaMemcpyAsync(out[i], c->scratch + (size_t)i * N, N * sizeof(float), cudaMemcpyDeviceToHost,
+                                  c->stream));
+        return wait_stream(c, 0);
+    }
+    return MDF_OK;
+}
+
+mdf_status mdf_residual(mdf_ctx *c, double *residual, double drift[2]) {
+    if (!c) return MDF_E_INVALID;
+    CK(c, aux_residual(c->aux, c->buf[c->cur], c->snap_u, c->snap_v, c->partials, c->result, c->stream));
+    CK(c, cudaMemcpyAsync(c->h_result, c->result, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    mdf_status s = wait_stream(c, 0);
+    if (s != MDF_OK) return s;
+    const double *r = c->h_result;
+    const long long window = c->steps - c->snap_step;
+    c->snap_step = c->steps;
+    const double val = window > 0 ? sqrt(r[0]) / ((double)window * sqrt(r[1])) : NAN;
+    if (residual) *residual = val;
+    if (drift) { drift[0] = r[2]; drift[1] = r[3]; }
+    if (r[4] > 0 || !isfinite(r[2]) || !isfinite(r[3]))
+        return fail(c, MDF_E_DIVERGED, "non-finite velocity at %.0f nodes", r[4]);
+    if (window <= 0) return fail(c, MDF_E_STATE, "no step since the previous residual");
+    return MDF_OK;
+}
+
+mdf_status mdf_get_distributions(mdf_ctx *c, float *out, int on_device) {
+    if (!c || !out) return c ? fail(c, MDF_E_INVALID, "out is NULL") : MDF_E_INVALID;
+    const size_t n = (size_t)NPLANES * c->nx * c->ny;
+    if (on_device) {
+        CK(c, aux_pack(c->aux, c->buf[c->cur], out, c->stream));
+        return MDF_OK;
+    }
+    mdf_status s = ensure_scratch(c, n * sizeof(float));
+    if (s != MDF_OK) return s;
+    CK(c, aux_pack(c->aux, c->buf[c->cur], c->scratch, c->stream));
+    CK(c, cudaMemcpyAsync(out, c->scratch, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    return wait_stream(c, 0);
+}
+
+mdf_status mdf_set_distributions(mdf_ctx *c, const float *in, int on_device) {
+    if (!c || !in) return c ? fail(c, MDF_E_INVALID, "in is NULL") : MDF_E_INVALID;
+    const size_t n = (size_t)NPLANES * c->nx * c->ny;
+    const float *src = in;
+    if (!on_device) {
+        mdf_status s = ensure_scratch(c, n * sizeof(float));
+        if (s != MDF_OK) return s;
+        CK(c, cudaMemcpyAsync(c->scratch, in, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        src = c->scratch;
+    }
+    CK(c, aux_unpack(c->aux, src, c->buf[c->cur], c->stream));
+    CK(c, aux_snapshot(c->aux, c->buf[c->cur], c->snap_u, c->snap_v, c->stream));
+    c->snap_step = c->steps;
+    if (!on_device) return wait_stream(c, 0);
+    return MDF_OK;
+}
+
+mdf_status mdf_synchronize(mdf_ctx *c, double timeout_s) {
+    if (!c) return MDF_E_INVALID;
+    return wait_stream(c, timeout_s);
+}
+
+mdf_status mdf_save(mdf_ctx *c, const char *path) {
+    if (!c || !path) return c ? fail(c, MDF_E_INVALID, "path is NULL") : MDF_E_INVALID;
+    const size_t n = (size_t)NPLANES * c->nx * c->ny;
+    float *h = (float *)malloc(n * sizeof(float));
+    if (!h) return fail(c, MDF_E_NOMEM, "host buffer");
+    mdf_status s = mdf_get_distributions(c, h, 0);
+    if (s != MDF_OK) { free(h); return s; }
+    FILE *fp = fopen(path, "wb");
+    if (!fp) { free(h); return fail(c, MDF_E_INVALID, "cannot open %s", path); }
+    char hdr[256];
+    memset(hdr, 0, sizeof(hdr));
+    snprintf(hdr, sizeof(hdr), "MDFCKPT1 nx=%d ny=%d steps=%lld dt=%.17g planes=%d\n", c->nx, c->ny, c->steps, c->dt,
+             NPLANES);
+    const bool ok = fwrite(hdr, 1, sizeof(hdr), fp) == sizeof(hdr) && fwrite(h, sizeof(float), n, fp) == n;
+    fclose(fp);
+    free(h);
+    return ok ? MDF_OK : fail(c, MDF_E_INVALID, "short write to %s", path);
+}
+
+mdf_status mdf_load(mdf_ctx *c, const char *path) {
+    if (!c || !path) return c ? fail(c, MDF_E_INVALID, "path is NULL") : MDF_E_INVALID;
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return fail(c, MDF_E_INVALID, "cannot open %s", path);
+    char hdr[256];
+    if (fread(hdr, 1, sizeof(hdr), fp) != sizeof(hdr)) { fclose(fp); return fail(c, MDF_E_INVALID, "bad header"); }
+    hdr[255] = 0;
+    int nx = 0, ny = 0, planes = 0;
+    long long steps = 0;
+    double dt = 0;
+    if (sscanf(hdr, "MDFCKPT1 nx=%d ny=%d steps=%lld dt=%lg planes=%d", &nx, &ny, &steps, &dt, &planes) != 5 ||
+        nx != c->nx || ny != c->ny || planes != NPLANES) {
+        fclose(fp);
+        return fail(c, MDF_E_INVALID, "checkpoint does not match this grid");
+    }
+    const size_t n = (size_t)NPLANES * c->nx * c->ny;
+    float *h = (float *)malloc(n * sizeof(float));
+    if (!h) { fclose(fp); return fail(c, MDF_E_NOMEM, "host buffer"); }
+    const bool ok = fread(h, sizeof(float), n, fp) == n;
+    fclose(fp);
+    if (!ok) { free(h); return fail(c, MDF_E_INVALID, "short read from %s", path); }
+    mdf_status s = mdf_set_distributions(c, h, 0);
+    free(h);
+    if (s == MDF_OK) { c->steps = steps; c->snap_step = steps; }
+    return s;
+}
+
+double mdf_dt(const mdf_ctx *c) { return c ? c->dt : NAN; }
+long long mdf_steps_done(const mdf_ctx *c) { return c ? c->steps : -1; }
+const char *mdf_last_error(const mdf_ctx *c) { return c ? c->last_error : g_create_error; }
+
+mdf_status mdf_launch_info(const mdf_ctx *c, int info[8]) {
+    if (!c || !info) return MDF_E_INVALID;
+    info[0] = c->plan.NT;
+    info[1] = c->plan.W;
+    info[2] = c->plan.H;
+    info[3] = c->plan.gx;
+    info[4] = c->plan.gy;
+    info[5] = c->plan.smem;
+    info[6] = c->plan.occ;
+    info[7] = c->pitch;
+    return MDF_OK;
+}
+
+double mdf_bytes_per_node(const mdf_ctx *c) {
+    if (!c) return NAN;
+    double b = 2.0 * NPLANES * 4.0;
+    if (c->force_mode == MDF_FORCE_FIELD) b += 8.0;
+    if (c->kind == MDF_GRID_CURVILINEAR) b += 16.0;
+    return b;
+}
+
+}  // extern "C"

@@ -1,0 +1,38 @@
+// mdf_aux.cuh -- auxiliary kernels of libmdf.so (initial state, metrics,
+// derived fields, residual reduction, layout packing) and their launchers.
+#pragma once
+
+#include "mdf_internal.cuh"
+
+namespace mdf {
+
+struct AuxArgs {
+    int nx, ny, pitch;
+    long long plane;
+    int xwall, ywall;
+    double lx, ly;
+    float c, inv2c;
+    float uw[4], vw[4];
+    int power_law;
+    float nu, K, n_index, nu_min, nu_max, a_pl;  // a_pl = cs2 dt / 2
+};
+
+struct FieldPtrs {
+    float *p[17];
+};
+
+cudaError_t aux_init(const AuxArgs &a, const float *u, const float *v, const float *p, float *f, cudaStream_t st);
+cudaError_t aux_pack(const AuxArgs &a, const float *f, float *dense, cudaStream_t st);
+cudaError_t aux_unpack(const AuxArgs &a, const float *dense, float *f, cudaStream_t st);
+cudaError_t aux_pad_field(const AuxArgs &a, const float *src, float *dst, cudaStream_t st);
+cudaError_t aux_metrics2d(const AuxArgs &a, const double *X, const double *Y, double c, float *mxx, float *mxy,
+                          float *mex, float *mey, double *edge_min, cudaStream_t st);
+cudaError_t aux_metrics1d(const AuxArgs &a, const double *xc, const double *yc, double c, float *kxv, float *kyv,
+                          double *edge_min, cudaStream_t st);
+cudaError_t aux_fields(const AuxArgs &a, const float *f, const FieldPtrs &dst, cudaStream_t st);
+int aux_residual_blocks(const AuxArgs &a);
+cudaError_t aux_residual(const AuxArgs &a, const float *f, float *su, float *sv, double *partials, double *out,
+                         cudaStream_t st);
+cudaError_t aux_snapshot(const AuxArgs &a, const float *f, float *su, float *sv, cudaStream_t st);
+
+}  // namespace mdf

@@ -1,0 +1,70 @@
+// mdf_internal.cuh -- declarations shared by the translation units of
+// libmdf.so (the fused MDF-FDLBM step, its auxiliary kernels and the host
+// runtime).  Nothing here is part of the public C ABI (include/mdf.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mdf {
+
+// Storage: each of the 10 planes fhat_{alpha,j} (plane k = 5 alpha + j) is
+// ny rows of `pitch` floats; node (x, y) lives at column GHOST + x.  The
+// GHOST columns on each side hold periodic images on a periodic x axis
+// (written by the step that produces the plane) and are unused otherwise.
+constexpr int GHOST = 4;
+constexpr int NPLANES = 10;
+
+enum MetricKind { METRIC_UNIFORM = 0, METRIC_SEPARABLE = 1, METRIC_CURVILINEAR = 2 };
+
+// Error codes the kernels raise in StepArgs::err (first one wins).
+enum DeviceError { DEVERR_NONE = 0, DEVERR_TMA_TIMEOUT = 1 };
+
+struct StepArgs {
+    float *fout;            // output state (same layout as the input)
+    int nx, ny, pitch;      // nodes, row pitch in floats
+    long long plane;        // floats per plane (pitch * ny)
+    int W, H;               // output columns / rows per block
+    int xwall, ywall;       // 1: NEE walls on that axis, 0: periodic
+    float c, inv2c;         // lattice speed, 1/(2c)
+    float dt, h;            // time step and half step
+    // mixed-scheme weights (Eqs. 2.2.12-2.2.13) on unit spacing, for a
+    // population moving in +chi: a1 Pi(+1) + a0 Pi(0) + am1 Pi(-1) + am2 Pi(-2)
+    float a1, a0, am1, am2;
+    // uniform grid: c/dx and c/dy
+    float kx, ky;
+    // separable grid: c xi_x per column (padded layout) and c eta_y per row
+    const float *kxv, *kyv;
+    // curvilinear grid: c xi_x, c xi_y, c eta_x, c eta_y planes (padded layout)
+    const float *mxx, *mxy, *mex, *mey;
+    // Newtonian rates: eigenvalues (free, first-moment) of
+    // I - Lambda (fhat^+), I - 3 Lambda/4 (fbar^+), (I + h/2 Lt)^-1 (recovery)
+    float rpp, rp, rbp, rb, rkp, rk;
+    // power-law fluid
+    int power_law;
+    float K, n_index, nu_min, nu_max, cs2, s_ratio, a_pl;  // a_pl = cs2 dt / 2
+    // body force
+    int force_mode;
+    float Fx, Fy;
+    const float *Fxp, *Fyp;  // padded layout
+    // wall velocities (west, east, south, north)
+    float uw[4], vw[4];
+    int *err;
+};
+
+// Fused step kernel launcher (mdf_step.cu).
+struct StepPlan {
+    int NT;       // threads per block
+    int W, H;     // output columns / rows per block
+    int gx, gy;   // grid
+    int smem;     // dynamic shared memory bytes
+    int occ;      // resident blocks per SM
+};
+
+cudaError_t step_plan(int metric, int power_law, int nx, int ny, int num_sms, StepPlan *plan);
+cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
+                        cudaStream_t stream);
+int step_pitch(int nx, int W);
+
+}  // namespace mdf

@@ -1,0 +1,91 @@
+"""The C-ABI library loads and exports every entry point that include/mdf.h
+declares; argument validation runs on the host and needs no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2306_08216_gb300 import build as B
+from paper_2306_08216_gb300 import mdf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mdf.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return mdf.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(mdf_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mdf_create", "mdf_step", "mdf_fields", "mdf_residual", "mdf_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert names, "no declarations parsed"
+    for n in names:
+        assert hasattr(lib, n), "libmdf.so does not export %s" % n
+    assert sorted(mdf.exported_symbols()) == names
+
+
+def test_library_links_no_torch(lib):
+    # the boundary takes plain pointers; the library must not pull in torch
+    maps = open("/proc/self/maps").read() if os.path.exists("/proc/self/maps") else ""
+    out = os.popen("ldd %s" % mdf.LIB_PATH).read()
+    assert "torch" not in out and "c10" not in out
+
+
+def _good():
+    g = mdf.Grid(16, 16, 0, 1.0, 1.0)
+    f = mdf.Fluid(0.01, 0, 0.0, 1.0, 0.0, 0.0)
+    b = mdf.BC()
+    p = mdf.Params(1.0, 0.5, 0.8, 1.5)
+    return g, f, b, p
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda g, f, b, p: setattr(g, "nx", 4),
+    lambda g, f, b, p: setattr(g, "ny", 0),
+    lambda g, f, b, p: setattr(g, "kind", 7),
+    lambda g, f, b, p: setattr(g, "lx", 0.0),
+    lambda g, f, b, p: setattr(f, "nu", -1.0),
+    lambda g, f, b, p: setattr(f, "nu", float("nan")),
+    lambda g, f, b, p: setattr(p, "cfl", 1.0),
+    lambda g, f, b, p: setattr(p, "cfl", 0.0),
+    lambda g, f, b, p: setattr(p, "eta", 1.5),
+    lambda g, f, b, p: setattr(p, "c", 0.0),
+    lambda g, f, b, p: setattr(p, "s_ratio", -1.0),
+    lambda g, f, b, p: b.type.__setitem__(0, 1),          # west wall, east periodic
+    lambda g, f, b, p: b.type.__setitem__(2, 5),
+    lambda g, f, b, p: setattr(g, "kind", 1),             # separable grid without coordinates
+    lambda g, f, b, p: (setattr(f, "power_law", 1), setattr(f, "K", 0.0)),
+    lambda g, f, b, p: (setattr(f, "power_law", 1), setattr(f, "K", 1.0), setattr(f, "n", 1.0),
+                        setattr(f, "nu_min", 2.0), setattr(f, "nu_max", 1.0)),
+])
+def test_invalid_arguments_rejected_before_any_cuda_call(lib, mutate):
+    g, f, b, p = _good()
+    mutate(g, f, b, p)
+    st, msg = mdf.create_status(g, f, b, p)
+    assert st == mdf.MDF_E_INVALID, (st, msg)
+    assert msg
+
+
+def test_null_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.mdf_create(None, None, None, None, ctypes.byref(h)) == mdf.MDF_E_INVALID
+    assert lib.mdf_step(None, 1) == mdf.MDF_E_INVALID
+    assert lib.mdf_residual(None, None, None) == mdf.MDF_E_INVALID
+    assert lib.mdf_last_error(None)
+    assert lib.mdf_steps_done(None) == -1

@@ -1,0 +1,286 @@
+"""GPU parity: the fused CUDA step (through the C ABI) against the FP64 oracle.
+
+Every case feeds both sides the same seeded inputs from
+paper_2306_08216_gb300.workloads and compares element by element.  The
+tolerance is the one the work is held to: max |GPU - oracle| <= 1e-5 times the
+reference velocity after the stated number of steps (FP32 state and
+arithmetic against FP64; the scheme is dissipative, so FP32 rounding stays
+bounded).  Short runs on tiny and ragged grids use a tighter bound.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2306_08216_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU runs deselect with -m "not gpu"
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2306_08216_gb300 import build as B  # noqa: E402
+from paper_2306_08216_gb300 import mdf  # noqa: E402
+
+B.build()
+
+
+def pair(nx, ny, **kw):
+    return mdf.Solver(nx, ny, **kw), Oracle(nx, ny, **kw)
+
+
+def run_both(g, o, fields, steps):
+    g.init(*fields)
+    o.init(*fields)
+    g.step(steps)
+    o.step(steps)
+    g.synchronize()
+    return g.state().astype(np.float64), o.state()
+
+
+def maxabs(a, b):
+    return float(np.abs(a - b).max())
+
+
+# ------------------------------------------------------------ spec case
+
+
+def test_taylor_green_64_after_1000_steps():
+    """64^2, U0 = 0.01, nu = 0.01, CFL 0.5, 1000 steps: max abs <= 1e-5 U0."""
+    n, U0 = 64, 0.01
+    g, o = pair(n, n, nu=0.01, lx=2 * math.pi, ly=2 * math.pi)
+    sg, so = run_both(g, o, W.taylor_green(n, U0), 1000)
+    assert maxabs(sg, so) <= 1e-5 * U0
+    fg, fo = g.fields(), o.fields()
+    for k in ("u", "v"):
+        assert maxabs(fg[k], fo[k]) <= 1e-5 * U0
+
+
+# --------------------------------------------- tiny, ragged and multi-tile grids
+
+
+@pytest.mark.parametrize("nx,ny", [(5, 5), (12, 9), (31, 17), (121, 11), (130, 7), (247, 13), (250, 40)])
+@pytest.mark.parametrize("walls", [(False, False), (True, True), (False, True), (True, False)])
+def test_small_and_ragged_grids(nx, ny, walls):
+    if walls[0] and nx < 5 or walls[1] and ny < 5:
+        pytest.skip("too small")
+    U = 0.05
+    kw = dict(nu=0.004, lx=1.0, ly=0.8, walls=walls, u_wall=(0.0, 0.01, -0.02, U), v_wall=(0.02, 0.0, 0.0, -0.01),
+              eta=0.7)
+    g, o = pair(nx, ny, **kw)
+    u, v, p = W.random_fields(nx, ny, U, seed=nx * 131 + ny)
+    sg, so = run_both(g, o, (u, v, p), 6)
+    assert maxabs(sg, so) <= 2e-6 * U
+
+
+def test_set_state_roundtrip_and_single_step():
+    nx, ny = 70, 33
+    g, o = pair(nx, ny, nu=0.01, lx=1.3, ly=1.0)
+    fh = W.random_state(nx, ny, 0.01, seed=3)
+    g.set_state(fh)
+    np.testing.assert_array_equal(g.state(), fh.astype(np.float32))
+    o.set_state(fh.astype(np.float32).astype(np.float64))
+    g.step(1)
+    o.step(1)
+    assert maxabs(g.state().astype(np.float64), o.state()) <= 2e-8
+
+
+# ---------------------------------------------------------- walls and forces
+
+
+def test_lid_driven_cavity_33_after_1000_steps():
+    n, u0 = 33, 0.1
+    kw = dict(nu=0.1 / 100.0, walls=(True, True), u_wall=(0, 0, 0, u0))
+    g, o = pair(n, n, **kw)
+    sg, so = run_both(g, o, W.zeros(n, n), 1000)
+    assert maxabs(sg, so) <= 1e-5 * u0
+    fg, fo = g.fields(), o.fields()
+    assert maxabs(fg["u"], fo["u"]) <= 1e-5 * u0
+    assert np.all(fg["u"][-1, 1:-1] == np.float32(u0))
+
+
+def test_poiseuille_constant_force():
+    n, F, nu = 32, 1e-4, 0.01
+    kw = dict(nu=nu, walls=(False, True), force=(F, 0.0))
+    g, o = pair(n, n, **kw)
+    sg, so = run_both(g, o, W.zeros(n, n), 1000)
+    umax = F / (8 * nu)
+    assert maxabs(sg, so) <= 1e-5 * umax
+
+
+def test_periodic_flow_force_field_anisotropic():
+    nx, ny, nu, u0 = 64, 32, 0.01, 0.05
+    u, v, p, Fx, Fy, _ = W.periodic_flow(nx, ny, u0=u0, nu=nu)
+    kw = dict(nu=nu, force=(Fx, Fy))
+    g, o = pair(nx, ny, **kw)
+    sg, so = run_both(g, o, W.zeros(nx, ny), 500)
+    assert maxabs(sg, so) <= 1e-5 * u0
+
+
+# ------------------------------------------------- grids: separable, curvilinear
+
+
+def test_tanh_stretched_cavity():
+    n, u0 = 41, 0.1
+    xs = W.tanh_nodes(n, 1.5)
+    kw = dict(nu=0.1 / 100.0, grid="separable", x=xs, y=xs, walls=(True, True), u_wall=(0, 0, 0, u0))
+    g, o = pair(n, n, **kw)
+    assert abs(g.dt - o.dt) <= 1e-12 * o.dt
+    sg, so = run_both(g, o, W.zeros(n, n), 600)
+    assert maxabs(sg, so) <= 1e-5 * u0
+
+
+def test_trapezoid_cavity_curvilinear():
+    nx, ny, u0 = 37, 29, 0.1
+    X, Y = W.trapezoid_grid(nx, ny)
+    kw = dict(nu=0.1 / 100.0, grid="curvilinear", x=X, y=Y, walls=(True, True), u_wall=(0, 0, 0, u0))
+    g, o = pair(nx, ny, **kw)
+    assert abs(g.dt - o.dt) <= 1e-12 * o.dt
+    sg, so = run_both(g, o, W.zeros(nx, ny), 400)
+    assert maxabs(sg, so) <= 1e-5 * u0
+
+
+def test_separable_periodic_channel():
+    nx, ny = 24, 33
+    kw = dict(nu=0.01, grid="separable", x=W.periodic_nodes(nx, 1.0), y=W.tanh_nodes(ny, 1.5), lx=1.0,
+              walls=(False, True), force=(1e-4, 0.0))
+    g, o = pair(nx, ny, **kw)
+    sg, so = run_both(g, o, W.zeros(nx, ny), 300)
+    assert maxabs(sg, so) <= 1e-5 * (1e-4 / (8 * 0.01))
+
+
+# ---------------------------------------------------------------- power law
+
+
+@pytest.mark.parametrize("n_index", [0.5, 1.0, 1.5])
+def test_power_law_cavity(n_index):
+    n, u0 = 33, 0.1
+    K = 0.1 * 0.1 ** (n_index - 1) / 100.0  # Re = u0^(2-n) L^n / K = 100
+    kw = dict(nu=K, walls=(True, True), u_wall=(0, 0, 0, u0), power_law=(K, n_index, K / 20, K * 20))
+    g, o = pair(n, n, **kw)
+    sg, so = run_both(g, o, W.zeros(n, n), 500)
+    assert maxabs(sg, so) <= 1e-5 * u0
+    fg, fo = g.fields(["nu"]), o.fields()
+    np.testing.assert_allclose(fg["nu"], fo["nu"], rtol=2e-3)
+
+
+# ----------------------------------------------------------- derived fields
+
+
+def test_derived_fields_match_oracle():
+    nx, ny, nu = 48, 40, 0.01
+    u, v, p, Fx, Fy, _ = W.periodic_flow(nx, ny, u0=0.05, nu=nu)
+    kw = dict(nu=nu, force=(Fx, Fy))
+    g, o = pair(nx, ny, **kw)
+    run_both(g, o, (u, v, p), 200)
+    fg, fo = g.fields(), o.fields()
+    for k in mdf.FIELD_NAMES:
+        scale = max(np.abs(fo[k]).max(), 1e-12)
+        assert maxabs(fg[k], fo[k]) <= 2e-4 * scale, k
+
+
+# --------------------------------------------------------- residual & drift
+
+
+def test_residual_and_drift_follow_their_definition():
+    n, U0, K = 64, 0.01, 50
+    g, o = pair(n, n, nu=0.01, lx=2 * math.pi, ly=2 * math.pi)
+    fields = W.taylor_green(n, U0)
+    g.init(*fields)
+    o.init(*fields)
+    u0, v0 = o.fields()["u"], o.fields()["v"]
+    g.step(K)
+    o.step(K)
+    r, drift = g.residual()
+    fo = o.fields()
+    num = math.sqrt(((fo["u"] - u0) ** 2 + (fo["v"] - v0) ** 2).sum())
+    den = math.sqrt((fo["u"] ** 2 + fo["v"] ** 2).sum())
+    assert r == pytest.approx(num / (K * den), rel=1e-4)
+    assert abs(drift[0] - fo["u"].sum()) <= 1e-9 and abs(drift[1] - fo["v"].sum()) <= 1e-9
+    with pytest.raises(mdf.MdfError) as e:
+        g.residual()  # no step since the snapshot
+    assert e.value.status == mdf.MDF_E_STATE
+
+
+def test_divergence_is_reported():
+    """Table 2: nu = 1e-3, F = 0.1 on 32 x 32 diverges; the library reports it."""
+    n = 32
+    g = mdf.Solver(n, n, nu=1e-3, walls=(False, True), force=(0.1, 0.0))
+    g.init(*W.zeros(n, n))
+    status = None
+    for _ in range(40):
+        g.step(250)
+        try:
+            g.residual()
+        except mdf.MdfError as e:
+            status = e.status
+            break
+    assert status == mdf.MDF_E_DIVERGED
+
+
+# ------------------------------------------------------------- checkpoints
+
+
+def test_checkpoint_resume_is_bitwise(tmp_path):
+    n = 40
+    kw = dict(nu=0.002, walls=(True, True), u_wall=(0, 0, 0, 0.1))
+    a = mdf.Solver(n, n, **kw)
+    a.init(*W.zeros(n, n))
+    a.step(30)
+    a.save(tmp_path / "c.ckpt")
+    a.step(20)
+    b = mdf.Solver(n, n, **kw)
+    b.load(tmp_path / "c.ckpt")
+    assert b.steps == 30
+    b.step(20)
+    np.testing.assert_array_equal(a.state(), b.state())
+
+
+# ------------------------------------------------ device pointers and streams
+
+
+def test_device_inputs_outputs_and_stream():
+    n, U0 = 96, 0.01
+    s = torch.cuda.Stream()
+    g = mdf.Solver(n, n, nu=0.01, lx=2 * math.pi, ly=2 * math.pi, stream=s)
+    u, v, p = W.taylor_green(n, U0)
+    dev = [torch.tensor(t, dtype=torch.float32, device="cuda") for t in (u, v, p)]
+    torch.cuda.synchronize()
+    g.init(*dev)
+    g.step(10)
+    out = {k: torch.empty((n, n), dtype=torch.float32, device="cuda") for k in ("u", "v")}
+    g.fields_device(out)
+    st = torch.empty((2, 5, n, n), dtype=torch.float32, device="cuda")
+    g.state(out=st)
+    g.synchronize()
+    h = mdf.Solver(n, n, nu=0.01, lx=2 * math.pi, ly=2 * math.pi)
+    h.init(u, v, p)
+    h.step(10)
+    np.testing.assert_array_equal(st.cpu().numpy(), h.state())
+    np.testing.assert_array_equal(out["u"].cpu().numpy(), h.fields(["u"])["u"])
+
+
+# ----------------------------------------- full size, bench launch configuration
+
+
+def test_taylor_green_4096_full_size_against_oracle():
+    """The benchmark workload (4096^2, bench launch plan): three steps against
+    the oracle on the full grid, then properties over 200 steps (momentum is
+    conserved, the amplitude decays as exp(-2 nu t))."""
+    n, U0, nu = 4096, 0.01, 0.01
+    u, v, p = W.taylor_green(n, U0)
+    g = mdf.Solver(n, n, nu=nu, lx=2 * math.pi, ly=2 * math.pi)
+    o = Oracle(n, n, nu=nu, lx=2 * math.pi, ly=2 * math.pi)
+    sg, so = run_both(g, o, (u, v, p), 3)
+    assert maxabs(sg, so) <= 1e-7 * U0
+    del o, so, sg
+    g.init(u, v, p)
+    g.step(200)
+    r, drift = g.residual()
+    f = g.fields(["u"])
+    t = 200 * g.dt
+    amp = float((f["u"].astype(np.float64) * u).sum() / (u * u).sum())
+    assert abs(amp - math.exp(-2 * nu * t)) < 1e-4
+    assert abs(drift[0]) < 1e-6 * n * n * U0 and abs(drift[1]) < 1e-6 * n * n * U0
