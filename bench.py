@@ -106,6 +106,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x, world, device="cpu"):
+    """Max of a per-rank scalar over all ranks (identity for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes, steps, world, seconds_max):
+    """Whole-job throughput: every rank updates `nodes` nodes `steps` times;
+    the job takes as long as its slowest rank."""
+    return world * nodes * steps / seconds_max / 1e6
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -178,6 +195,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=NX,
+                    help="grid side (default 4096, the benchmark workload; smaller sides only for profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -201,8 +220,9 @@ def main():
         if world > 1:
             dist.barrier()
 
-    u, v, p = W.taylor_green(NX, U0)
-    solver = mdf.Solver(NX, NY, nu=NU, lx=2 * math.pi, ly=2 * math.pi, stream=stream)
+    nx = ny = args.nx
+    u, v, p = W.taylor_green(nx, U0)
+    solver = mdf.Solver(nx, ny, nu=NU, lx=2 * math.pi, ly=2 * math.pi, stream=stream)
     solver.init(u, v, p)
     solver.step(args.warmup)
     solver.synchronize()
@@ -221,12 +241,9 @@ def main():
     torch.cuda.synchronize()
     ms = start.elapsed_time(stop)
     barrier()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    nodes = NX * NY
-    value = world * nodes * args.steps / (ms_max / 1e3) / 1e6
+    ms_max = max_over_ranks(ms, world, "cuda")
+    nodes = nx * ny
+    value = job_mlups(nodes, args.steps, world, ms_max / 1e3)
     ms_step = ms_max / args.steps
     peak, peak_kind = measured_peaks()
     achieved = bpn * nodes / (ms / args.steps / 1e3) / 1e9  # GB/s of this rank's launches
@@ -234,7 +251,7 @@ def main():
 
     # ---- end-to-end through the C ABI with host buffers
     pin = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory() for a in (u, v, p)]
-    outs = [torch.empty((NY, NX), dtype=torch.float32).pin_memory() for _ in range(3)]
+    outs = [torch.empty((ny, nx), dtype=torch.float32).pin_memory() for _ in range(3)]
     e2e_steps = args.steps
     barrier()
     torch.cuda.synchronize()
@@ -245,10 +262,7 @@ def main():
     for o_, k in zip(outs, ("u", "v", "P")):
         o_.numpy()[...] = res[k]
     e2e_sec = time.perf_counter() - t0
-    te = torch.tensor([e2e_sec], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_val = world * nodes * e2e_steps / float(te.item()) / 1e6
+    e2e_val = job_mlups(nodes, e2e_steps, world, max_over_ranks(e2e_sec, world, "cuda"))
 
     if rank != 0:
         if world > 1:
@@ -263,7 +277,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "taylor_green_4096x4096_fp32", "nx": NX, "ny": NY, "nu": NU, "U0": U0, "cfl": 0.5,
+        "config": {"workload": "taylor_green_%dx%d_fp32" % (nx, ny), "nx": nx, "ny": ny, "nu": NU, "U0": U0, "cfl": 0.5,
                    "eta": 0.8, "s_ratio": 1.5, "l2": "inputs larger than L2 (2 x 676 MB state), no flush",
                    "parallelism": "replicas x%d" % world, "launch": info},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -90,28 +90,6 @@ __device__ __forceinline__ void tma_load_row(const CUtensorMap *map, uint64_t *b
         : "memory");
 }
 
-// Local relaxation map shared by Steps 1 and 3: with zeroth moment ub, odd
-// differences dx = g1 - g3, dy = g2 - g4 and equilibrium flux (Fx, Fy)
-// = ub u + P E_alpha, returns feq + Ap (g - feq) + (A - Ap) P_c (g - feq),
-// Ap / A the eigenvalues on the free / first-moment subspaces.
-struct Map5 {
-    float o0, o1, o2, o3, o4;
-};
-
-__device__ __forceinline__ Map5 relax(const float g[5], float ub, float dx, float dy, float Fx, float Fy, float Ap,
-                                      float A, float inv2c) {
-    const float B = (1.0f - Ap) * 0.2f * ub;
-    const float Ex = fmaf((1.0f - A) * inv2c, Fx, 0.5f * (A - Ap) * dx);
-    const float Ey = fmaf((1.0f - A) * inv2c, Fy, 0.5f * (A - Ap) * dy);
-    Map5 m;
-    m.o0 = fmaf(Ap, g[0], B);
-    m.o1 = fmaf(Ap, g[1], B + Ex);
-    m.o3 = fmaf(Ap, g[3], B - Ex);
-    m.o2 = fmaf(Ap, g[2], B + Ey);
-    m.o4 = fmaf(Ap, g[4], B - Ey);
-    return m;
-}
-
 // Moments of a node (10 values, plane order 5 alpha + j): u, v, the four odd
 // differences and P of Eq. 2.3.23 (R = 0), which fhat, fbar and f share.
 struct Mom {
@@ -130,14 +108,46 @@ __device__ __forceinline__ Mom moments(const float g[10], float c) {
     return m;
 }
 
-__device__ __forceinline__ void relax10(const float g[10], const Mom &m, float Ap, float A, float inv2c,
-                                        float out[10]) {
-    const float F1x = fmaf(m.u, m.u, m.P), F1y = m.u * m.v;
-    const float F2x = F1y, F2y = fmaf(m.v, m.v, m.P);
-    Map5 a = relax(g, m.u, m.d1x, m.d1y, F1x, F1y, Ap, A, inv2c);
-    Map5 b = relax(g + 5, m.v, m.d2x, m.d2y, F2x, F2y, Ap, A, inv2c);
-    out[0] = a.o0; out[1] = a.o1; out[2] = a.o2; out[3] = a.o3; out[4] = a.o4;
-    out[5] = b.o0; out[6] = b.o1; out[7] = b.o2; out[8] = b.o3; out[9] = b.o4;
+// Non-equilibrium part n = g - feq of a node (Eq. 2.2.5 on D2Q5 with
+// w_j = 1/5, cs^2 = 2c^2/5: feq_0 = ub/5, feq_{1,3} = ub/5 +- Phi_x/(2c),
+// feq_{2,4} = ub/5 +- Phi_y/(2c), Phi = ub_alpha u + P E_alpha).  feq_0 is
+// formed as ub - 4 ub/5 so that sum_j feq_j = ub carries no rounding bias of
+// the constant 1/5; otherwise every step would scale the conserved zeroth
+// moment by the same FP32 factor and the drift would grow linearly in time.
+__device__ __forceinline__ void noneq(const float g[10], const Mom &m, float inv2c, float n[10]) {
+    const float u5 = 0.2f * m.u, v5 = 0.2f * m.v;
+    const float f1x = fmaf(m.u, m.u, m.P) * inv2c, uv = m.u * m.v * inv2c;
+    const float f2y = fmaf(m.v, m.v, m.P) * inv2c;
+    n[0] = g[0] - fmaf(-4.0f, u5, m.u);
+    n[1] = g[1] - (u5 + f1x);
+    n[3] = g[3] - (u5 - f1x);
+    n[2] = g[2] - (u5 + uv);
+    n[4] = g[4] - (u5 - uv);
+    n[5] = g[5] - fmaf(-4.0f, v5, m.v);
+    n[6] = g[6] - (v5 + uv);
+    n[8] = g[8] - (v5 - uv);
+    n[7] = g[7] - (v5 + f2y);
+    n[9] = g[9] - (v5 - f2y);
+}
+
+// Local relaxation map shared by Steps 1 and 3, applied as an increment:
+// out = g - (1 - Ap) n + (A - Ap) P_c n, which equals
+// feq + Ap (g - feq) + (A - Ap) P_c (g - feq); Ap / A are the eigenvalues on
+// the free / first-moment subspaces, (P_c n)_{1,3} = +-(n_1 - n_3)/2 and
+// (P_c n)_{2,4} = +-(n_2 - n_4)/2.  Written this way the zeroth moment is
+// kept up to unbiased per-node rounding.
+__device__ __forceinline__ void relax10(const float g[10], const float n[10], float Ap, float A, float out[10]) {
+    const float K = 1.0f - Ap, D = 0.5f * (A - Ap);
+#pragma unroll
+    for (int b = 0; b < 10; b += 5) {
+        const float dx = D * (n[b + 1] - n[b + 3]);
+        const float dy = D * (n[b + 2] - n[b + 4]);
+        out[b + 0] = fmaf(-K, n[b + 0], g[b + 0]);
+        out[b + 1] = fmaf(-K, n[b + 1], g[b + 1]) + dx;
+        out[b + 3] = fmaf(-K, n[b + 3], g[b + 3]) - dx;
+        out[b + 2] = fmaf(-K, n[b + 2], g[b + 2]) + dy;
+        out[b + 4] = fmaf(-K, n[b + 4], g[b + 4]) - dy;
+    }
 }
 
 // Non-equilibrium extrapolation: node value = g_nb + feq(u_w, P) - feq(u_nb, P)
@@ -206,9 +216,13 @@ __device__ __forceinline__ float power_law_nu(float g, const StepArgs &a) {
 // Streaming term along one axis, population moving towards +chi (sgn > 0) or
 // -chi: a1 Pi(+-1) + a0 Pi(0) + am1 Pi(-+1) + am2 Pi(-+2), with the far
 // upwind point replaced by 2 Pi(-+1) - Pi(0) next to a wall.
+// Written in differences from Pi(-+1) (the weights sum to zero), so a
+// uniform field gives exactly zero and the FP32 rounding of the weights puts
+// no bias on conserved sums.
 __device__ __forceinline__ float stencil(float pf, float p0, float pb1, float pb2, bool wall_adj, const StepArgs &a) {
-    const float far = wall_adj ? (2.0f * pb1 - p0) : pb2;
-    return fmaf(a.a1, pf, fmaf(a.a0, p0, fmaf(a.am1, pb1, a.am2 * far)));
+    const float d0 = p0 - pb1;
+    const float dfar = wall_adj ? -d0 : (pb2 - pb1);
+    return fmaf(a.a1, pf - pb1, fmaf(a.a0, d0, a.am2 * dfar));
 }
 
 __device__ __forceinline__ int wrap(int i, int n) {
@@ -311,12 +325,13 @@ __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ CUtens
             } else {
                 R.rpp = a.rpp; R.rp = a.rp; R.rbp = a.rbp; R.rb = a.rb;
             }
-            float o[10];
-            relax10(g, m, R.rpp, R.rp, inv2c, o);
+            float nq[10], o[10];
+            noneq(g, m, inv2c, nq);
+            relax10(g, nq, R.rpp, R.rp, o);
             float *dP = rP + (it % RP) * ROW;
 #pragma unroll
             for (int k = 0; k < NPLANES; ++k) dP[k * NT + t] = o[k];
-            relax10(g, m, R.rbp, R.rb, inv2c, o);
+            relax10(g, nq, R.rbp, R.rb, o);
             float *dB = rB + (it % RB) * ROW;
 #pragma unroll
             for (int k = 0; k < NPLANES; ++k) dB[k * NT + t] = o[k];
@@ -428,8 +443,9 @@ __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ CUtens
                         rk = k[NT + t];
                     }
                     const Mom m = moments(fb, c);
-                    float f[10];
-                    relax10(fb, m, rkp, rk, inv2c, f);
+                    float nq[10], f[10];
+                    noneq(fb, m, inv2c, nq);
+                    relax10(fb, nq, rkp, rk, f);
 #pragma unroll
                     for (int k = 0; k < NPLANES; ++k) Fq[k * NT + t] = f[k];
                     float w[10];
