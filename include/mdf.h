@@ -176,6 +176,31 @@ mdf_status mdf_launch_info(const mdf_ctx *ctx, int info[8]);
  * written once, plus force/metric planes read once). */
 double mdf_bytes_per_node(const mdf_ctx *ctx);
 
+/* Residual and drift with no allocation at all (the paper has no
+ * counterpart; this is a service for callers that may not allocate device
+ * memory -- inside stream capture, under an allocator that owns all device
+ * memory, or in a loop that must not risk an allocation or the implicit
+ * device synchronisation of cudaMalloc/cudaFree).
+ *   fhat            device, FP32 [2][5][ny][nx] (the layout of
+ *                   mdf_get_distributions with on_device = 1)
+ *   u_prev, v_prev  device, FP32 [ny][nx], velocity `window` steps earlier
+ *                   (e.g. from mdf_fields with on_device = 1); not modified
+ *   window          steps between u_prev/v_prev and fhat (>= 1)
+ *   cuda_stream     stream to enqueue on (NULL = legacy stream); asynchronous
+ *   out             device, 4 doubles: residual as defined for mdf_residual,
+ *                   sum of u, sum of v, count of non-finite nodes
+ * The only scratch is a fixed array of 160 KiB of device memory that the
+ * library holds on every GPU that loads it, so nx * ny may not exceed
+ * 16,777,216 (4096 x 4096): larger fields, NULL pointers or window < 1
+ * return MDF_E_INVALID before anything is enqueued.  The first call on a
+ * device looks up that array's device address (once per device); make that
+ * first call outside any stream capture.  All calls share the one array, so
+ * calls that may run at the same time on the GPU (other streams, other host
+ * threads) race; serialise them.  Allocates nothing: no cudaMalloc, cudaFree
+ * or allocating library call on any path. */
+mdf_status mdf_residual_noalloc(const float *fhat, const float *u_prev, const float *v_prev, int nx, int ny,
+                                long long window, void *cuda_stream, double *out);
+
 #ifdef __cplusplus
 }
 #endif

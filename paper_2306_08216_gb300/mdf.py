@@ -78,6 +78,8 @@ _SIGNATURES = [
     ("mdf_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("mdf_launch_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     ("mdf_bytes_per_node", ctypes.c_double, [ctypes.c_void_p]),
+    ("mdf_residual_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
 ]
 
 _lib = None
