@@ -231,7 +231,7 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
     CKE(cudaGetDevice(&c->dev));
     CKE(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
     const int metric = grid->kind;
-    CKE(step_plan(metric, fluid->power_law ? 1 : 0, c->nx, c->ny, c->num_sms, &c->plan));
+    CKE(step_plan(metric, fluid->power_law ? 1 : 0, (xwall || ywall) ? 1 : 0, c->nx, c->ny, c->num_sms, &c->plan));
     c->pitch = step_pitch(c->nx, c->plan.W);
     c->plane = (long long)c->pitch * c->ny;
     const size_t state_bytes = (size_t)NPLANES * c->plane * sizeof(float);

@@ -62,7 +62,7 @@ struct StepPlan {
     int occ;      // resident blocks per SM
 };
 
-cudaError_t step_plan(int metric, int power_law, int nx, int ny, int num_sms, StepPlan *plan);
+cudaError_t step_plan(int metric, int power_law, int walls, int nx, int ny, int num_sms, StepPlan *plan);
 cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
                         cudaStream_t stream);
 int step_pitch(int nx, int W);

@@ -14,53 +14,101 @@
 // (Eq. 2.2.5) each of the three local maps costs a handful of FMAs per
 // population and no 5x5 product appears (cf. the 2x5x5 loop count of Sec. 4.2).
 //
-// Work decomposition.  A block owns a strip of W output columns and marches
-// down a band of H rows.  Thread t holds column x0 - 4 + t; the 8 extra
-// columns are the halo the two chained stencils need (reach 2 + 2).  Each
-// iteration of the march
-//   A: takes row p of fhat from a TMA ring (cp.async.bulk.tensor, one 3-D box
-//      of 10 planes x NT columns per row) and writes fhat^+ and fbar^+ of row
-//      p to shared rings;
-//   B: forms fbar and then f(t+h) of row q = p - 2 from the fbar^+ ring
-//      (x stencils across threads, y stencils across ring rows);
-//   C: forms fhat(t+dt) of row r = p - 4 from the f ring and stores it.
-// Only the x halo is recomputed; rows are streamed once.  Walls use
-// non-equilibrium extrapolation written by the interior neighbour's thread,
-// and the one-sided second-order upwind point beyond a wall is replaced by
-// its linear extrapolation (Pi(-1) = 2 Pi(0) - Pi(1)).
+// Arithmetic layout.  The two distributions alpha = u, v (Eq. 2.1.2 with
+// alpha = 1, 2) see the same collision rates and the same difference
+// weights, so each population j is carried as one 64-bit pair
+// (fhat_{j,u}, fhat_{j,v}) and processed with the packed FP32 instructions
+// of sm_100-family GPUs (add/sub/mul/fma .f32x2); shared rings hold the
+// pairs, so every ring access is one 64-bit load or store.
+//
+// Work decomposition.  A block owns a strip of W = NT - 8 output columns and
+// marches down a band of H rows.  Thread t holds column x0 - 4 + t; the 8
+// extra columns are the halo of the two chained stencils (reach 2 + 2).  Per
+// row of the march, with p the newest row:
+//   C: fhat(t+dt) of row r = p - 5 from the f ring and the fhat^+ ring -> HBM;
+//   A: row p of fhat arrives by TMA (one 3-D box of 10 planes x NT columns);
+//      fhat^+ and fbar^+ of row p go to their rings;
+//   -- barrier --
+//   B: fbar and f(t+h) of row q = p - 2 (x stencils across threads, y
+//      stencils across ring rows) go to the f ring; walls by NEE;
+//   -- barrier --
+// All rings have five rows; slot offsets rotate by one each row.  Only the x
+// halo (8 of NT columns) and 9 rows per band are recomputed; every row is
+// read from HBM once.  Walls use non-equilibrium extrapolation written by the
+// interior neighbour's thread, and the second-order upwind point beyond a
+// wall is replaced by its linear extrapolation Pi(-1) = 2 Pi(0) - Pi(1).
 #include "mdf_internal.cuh"
 
 namespace mdf {
 
 namespace {
 
-constexpr int TMA_SLOTS = 3;   // rows in flight
-constexpr int RB = 5;          // fbar^+ ring rows (y stencil reach 2 + 2)
-constexpr int RF = 5;          // f(t+h) ring rows
-constexpr int RP = 6;          // fhat^+ ring rows (used 4 iterations later)
-constexpr int RK = 5;          // power-law recovery rates ring
+constexpr int TMA_SLOTS = 3;  // rows of fhat in flight
+constexpr int RING = 5;       // rows of every shared ring (stencil reach 2 + 2)
+
+// ------------------------------------------------------------ f32x2 pairs
+
+struct F2 {
+    unsigned long long r;
+};
+
+__device__ __forceinline__ F2 mk2(float x, float y) {
+    F2 a;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a.r) : "f"(x), "f"(y));
+    return a;
+}
+__device__ __forceinline__ F2 splat(float x) { return mk2(x, x); }
+__device__ __forceinline__ void split2(F2 a, float &x, float &y) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.r));
+}
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) {
+    F2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+    F2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) {
+    F2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
+    F2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.r) : "l"(a.r), "l"(b.r), "l"(c.r));
+    return d;
+}
+__device__ __forceinline__ F2 sel2(bool p, F2 a, F2 b) {
+    F2 d;
+    d.r = p ? a.r : b.r;
+    return d;
+}
+__device__ __forceinline__ F2 lds2(const unsigned char *base, int byte_off) {
+    F2 a;
+    a.r = *reinterpret_cast<const unsigned long long *>(base + byte_off);
+    return a;
+}
+__device__ __forceinline__ void sts2(unsigned char *base, int byte_off, F2 a) {
+    *reinterpret_cast<unsigned long long *>(base + byte_off) = a.r;
+}
+
+// ------------------------------------------------------------ TMA, mbarrier
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -72,7 +120,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-
 // Bounded wait: gives up after ~2^32 clock cycles (about two seconds).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -82,101 +129,90 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         if (clock64() - t0 > (1ll << 32)) return false;
     }
 }
-
-__device__ __forceinline__ void tma_load_row(const CUtensorMap *map, uint64_t *bar, float *dst, int x, int y) {
+__device__ __forceinline__ void tma_load_row(const CUtensorMap *map, uint64_t *bar, void *dst, int x, int y) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
         ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(0), "r"(smem_u32(bar))
         : "memory");
 }
 
-// Moments of a node (10 values, plane order 5 alpha + j): u, v, the four odd
-// differences and P of Eq. 2.3.23 (R = 0), which fhat, fbar and f share.
-struct Mom {
-    float u, v, d1x, d1y, d2x, d2y, P;
+// ------------------------------------------------------------ local maps
+
+// Node in pair form: g[j] = (g_{j,u}, g_{j,v}), j = 0..4.
+// Moments shared by fhat, fbar and f: (u, v) = sum_j g_j, the odd
+// differences (g1 - g3), (g2 - g4) and P of Eq. 2.3.23 (R = 0).
+struct Mom2 {
+    F2 uv, d13, d24;
+    float u, v, P;
 };
 
-__device__ __forceinline__ Mom moments(const float g[10], float c) {
-    Mom m;
-    m.u = g[0] + g[1] + g[2] + g[3] + g[4];
-    m.v = g[5] + g[6] + g[7] + g[8] + g[9];
-    m.d1x = g[1] - g[3];
-    m.d1y = g[2] - g[4];
-    m.d2x = g[6] - g[8];
-    m.d2y = g[7] - g[9];
-    m.P = 0.5f * (c * (m.d1x + m.d2y) - m.u * m.u - m.v * m.v);
+__device__ __forceinline__ Mom2 moments2(const F2 g[5], float c) {
+    Mom2 m;
+    m.uv = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
+    m.d13 = g[1] - g[3];
+    m.d24 = g[2] - g[4];
+    float d1x, d2x, d1y, d2y;
+    split2(m.d13, d1x, d2x);
+    split2(m.d24, d1y, d2y);
+    split2(m.uv, m.u, m.v);
+    m.P = 0.5f * (c * (d1x + d2y) - m.u * m.u - m.v * m.v);
     return m;
 }
 
-// Non-equilibrium part n = g - feq of a node (Eq. 2.2.5 on D2Q5 with
-// w_j = 1/5, cs^2 = 2c^2/5: feq_0 = ub/5, feq_{1,3} = ub/5 +- Phi_x/(2c),
+// Non-equilibrium part n = g - feq (Eq. 2.2.5 on D2Q5 with w_j = 1/5 and
+// cs^2 = 2c^2/5: feq_0 = ub/5, feq_{1,3} = ub/5 +- Phi_x/(2c),
 // feq_{2,4} = ub/5 +- Phi_y/(2c), Phi = ub_alpha u + P E_alpha).  feq_0 is
 // formed as ub - 4 ub/5 so that sum_j feq_j = ub carries no rounding bias of
 // the constant 1/5; otherwise every step would scale the conserved zeroth
-// moment by the same FP32 factor and the drift would grow linearly in time.
-__device__ __forceinline__ void noneq(const float g[10], const Mom &m, float inv2c, float n[10]) {
-    const float u5 = 0.2f * m.u, v5 = 0.2f * m.v;
-    const float f1x = fmaf(m.u, m.u, m.P) * inv2c, uv = m.u * m.v * inv2c;
-    const float f2y = fmaf(m.v, m.v, m.P) * inv2c;
-    n[0] = g[0] - fmaf(-4.0f, u5, m.u);
-    n[1] = g[1] - (u5 + f1x);
-    n[3] = g[3] - (u5 - f1x);
-    n[2] = g[2] - (u5 + uv);
-    n[4] = g[4] - (u5 - uv);
-    n[5] = g[5] - fmaf(-4.0f, v5, m.v);
-    n[6] = g[6] - (v5 + uv);
-    n[8] = g[8] - (v5 - uv);
-    n[7] = g[7] - (v5 + f2y);
-    n[9] = g[9] - (v5 - f2y);
+// moments by the same FP32 factor and the drift would grow linearly in time.
+__device__ __forceinline__ void noneq2(const F2 g[5], const Mom2 &m, float inv2c, F2 n[5]) {
+    const F2 u5 = splat(0.2f) * m.uv;
+    const float uu = fmaf(m.u, m.u, m.P) * inv2c, uv = m.u * m.v * inv2c, vv = fmaf(m.v, m.v, m.P) * inv2c;
+    const F2 fx = mk2(uu, uv), fy = mk2(uv, vv);
+    n[0] = g[0] - fma2(splat(-4.0f), u5, m.uv);
+    n[1] = g[1] - (u5 + fx);
+    n[3] = g[3] - (u5 - fx);
+    n[2] = g[2] - (u5 + fy);
+    n[4] = g[4] - (u5 - fy);
 }
 
-// Local relaxation map shared by Steps 1 and 3, applied as an increment:
+// Local relaxation shared by Steps 1 and 3, as an increment:
 // out = g - (1 - Ap) n + (A - Ap) P_c n, which equals
 // feq + Ap (g - feq) + (A - Ap) P_c (g - feq); Ap / A are the eigenvalues on
 // the free / first-moment subspaces, (P_c n)_{1,3} = +-(n_1 - n_3)/2 and
-// (P_c n)_{2,4} = +-(n_2 - n_4)/2.  Written this way the zeroth moment is
-// kept up to unbiased per-node rounding.
-__device__ __forceinline__ void relax10(const float g[10], const float n[10], float Ap, float A, float out[10]) {
-    const float K = 1.0f - Ap, D = 0.5f * (A - Ap);
-#pragma unroll
-    for (int b = 0; b < 10; b += 5) {
-        const float dx = D * (n[b + 1] - n[b + 3]);
-        const float dy = D * (n[b + 2] - n[b + 4]);
-        out[b + 0] = fmaf(-K, n[b + 0], g[b + 0]);
-        out[b + 1] = fmaf(-K, n[b + 1], g[b + 1]) + dx;
-        out[b + 3] = fmaf(-K, n[b + 3], g[b + 3]) - dx;
-        out[b + 2] = fmaf(-K, n[b + 2], g[b + 2]) + dy;
-        out[b + 4] = fmaf(-K, n[b + 4], g[b + 4]) - dy;
-    }
+// (P_c n)_{2,4} = +-(n_2 - n_4)/2.  The zeroth moment is kept up to unbiased
+// per-node rounding.  n13 = n1 - n3, n24 = n2 - n4; mK = -(1 - Ap),
+// D = (A - Ap)/2.
+__device__ __forceinline__ void relax2(const F2 g[5], const F2 n[5], F2 n13, F2 n24, F2 mK, F2 D, F2 out[5]) {
+    const F2 dx = D * n13, dy = D * n24;
+    out[0] = fma2(mK, n[0], g[0]);
+    out[1] = fma2(mK, n[1], g[1]) + dx;
+    out[3] = fma2(mK, n[3], g[3]) - dx;
+    out[2] = fma2(mK, n[2], g[2]) + dy;
+    out[4] = fma2(mK, n[4], g[4]) - dy;
 }
 
 // Non-equilibrium extrapolation: node value = g_nb + feq(u_w, P) - feq(u_nb, P)
 // (the pressure cancels in the difference of the linear equilibria).
-__device__ __forceinline__ void nee(const float g[10], float uw, float vw, float inv2c, float out[10]) {
-    const float un = g[0] + g[1] + g[2] + g[3] + g[4];
-    const float vn = g[5] + g[6] + g[7] + g[8] + g[9];
+__device__ __forceinline__ void nee2(const F2 g[5], float uw, float vw, float inv2c, F2 out[5]) {
+    float un, vn;
+    split2((g[0] + g[1]) + (g[2] + g[3]) + g[4], un, vn);
     const float du = 0.2f * (uw - un), dv = 0.2f * (vw - vn);
     const float uux = (uw * uw - un * un) * inv2c, uvy = (uw * vw - un * vn) * inv2c;
     const float vvy = (vw * vw - vn * vn) * inv2c;
-    out[0] = g[0] + du;
-    out[1] = g[1] + du + uux;
-    out[3] = g[3] + du - uux;
-    out[2] = g[2] + du + uvy;
-    out[4] = g[4] + du - uvy;
-    out[5] = g[5] + dv;
-    out[6] = g[6] + dv + uvy;
-    out[8] = g[8] + dv - uvy;
-    out[7] = g[7] + dv + vvy;
-    out[9] = g[9] + dv - vvy;
+    out[0] = g[0] + mk2(du, dv);
+    out[1] = g[1] + mk2(du + uux, dv + uvy);
+    out[3] = g[3] + mk2(du - uux, dv - uvy);
+    out[2] = g[2] + mk2(du + uvy, dv + vvy);
+    out[4] = g[4] + mk2(du - uvy, dv - vvy);
 }
 
-// Rates of the three local maps for first-moment rate s (s' = s_ratio s):
+// Eigenvalues of the three local maps for first-moment rate s (s' = s_ratio s):
 // rho(l) = (1 - dt l/2)/(1 + dt l/2) for I - Lambda, (1 + 3 rho)/4 for
 // I - 3 Lambda/4, 1/(1 + h l/2) for (I + h/2 Lt)^-1.
 struct Rates {
     float rpp, rp, rbp, rb, rkp, rk;
 };
-
 __device__ __forceinline__ Rates rates_for(float s, float s_ratio, float dt) {
     const float sp = s_ratio * s;
     Rates r;
@@ -199,7 +235,6 @@ __device__ __forceinline__ float power_law_nu(float g, const StepArgs &a) {
     if (!(g > 1e-30f)) return n < 1.0f ? a.nu_max : a.nu_min;
     const float lnK = __logf(a.K), lng = __logf(g);
     const float lmin = __logf(a.nu_min), lmax = __logf(a.nu_max);
-    // start: solution without the a term, clamped
     float l = (lnK + (n - 1.0f) * lng) / n;
     l = fminf(fmaxf(l, lmin), lmax);
 #pragma unroll
@@ -213,16 +248,18 @@ __device__ __forceinline__ float power_law_nu(float g, const StepArgs &a) {
     return fminf(fmaxf(__expf(l), a.nu_min), a.nu_max);
 }
 
-// Streaming term along one axis, population moving towards +chi (sgn > 0) or
-// -chi: a1 Pi(+-1) + a0 Pi(0) + am1 Pi(-+1) + am2 Pi(-+2), with the far
-// upwind point replaced by 2 Pi(-+1) - Pi(0) next to a wall.
-// Written in differences from Pi(-+1) (the weights sum to zero), so a
-// uniform field gives exactly zero and the FP32 rounding of the weights puts
-// no bias on conserved sums.
-__device__ __forceinline__ float stencil(float pf, float p0, float pb1, float pb2, bool wall_adj, const StepArgs &a) {
-    const float d0 = p0 - pb1;
-    const float dfar = wall_adj ? -d0 : (pb2 - pb1);
-    return fmaf(a.a1, pf - pb1, fmaf(a.a0, d0, a.am2 * dfar));
+// Streaming increment along one axis for a population moving towards +chi
+// (pf = Pi(+1), pb1 = Pi(-1), pb2 = Pi(-2)) or -chi (mirrored), added to
+// `base`:  w1 (Pi(+1) - Pi(-1)) + w0 (Pi(0) - Pi(-1)) + w2 (Pi(-2) - Pi(-1)),
+// the mixed scheme of Eqs. 2.2.12-2.2.13 written in differences (its weights
+// sum to zero, so a uniform field gives exactly zero).  Next to a wall the
+// far point is 2 Pi(-1) - Pi(0).  The weights carry -h c/dx (or -dt c/dx).
+template <bool WALLS>
+__device__ __forceinline__ F2 stream2(F2 base, F2 pf, F2 p0, F2 pb1, F2 pb2, bool wall_adj, F2 w1, F2 w0, F2 w2) {
+    const F2 d0 = p0 - pb1;
+    F2 dfar = pb2 - pb1;
+    if (WALLS) dfar = sel2(wall_adj, splat(0.0f) - d0, dfar);
+    return fma2(w1, pf - pb1, fma2(w0, d0, fma2(w2, dfar, base)));
 }
 
 __device__ __forceinline__ int wrap(int i, int n) {
@@ -230,37 +267,108 @@ __device__ __forceinline__ int wrap(int i, int n) {
     return i < 0 ? i + n : i;
 }
 
-// Store one node of the output (10 planes), with its periodic image in the
-// ghost columns when the x axis is periodic.
-__device__ __forceinline__ void store_node(const StepArgs &a, int row, int X, const float v[10]) {
+// Store one node (5 pairs -> 10 planes), with its periodic image in the ghost
+// columns when the x axis is periodic.
+template <bool XPER>
+__device__ __forceinline__ void store_node(const StepArgs &a, int row, int X, const F2 v[5]) {
     const long long base = (long long)row * a.pitch + GHOST + X;
+    float lo[5], hi[5];
 #pragma unroll
-    for (int k = 0; k < NPLANES; ++k) a.fout[k * a.plane + base] = v[k];
-    if (!a.xwall) {
+    for (int j = 0; j < 5; ++j) split2(v[j], lo[j], hi[j]);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        a.fout[j * a.plane + base] = lo[j];
+        a.fout[(5 + j) * a.plane + base] = hi[j];
+    }
+    if (XPER) {
         // a node can be the image of a ghost on both sides when nx < 2 GHOST
         if (X < GHOST) {
-            const long long b2 = (long long)row * a.pitch + GHOST + X + a.nx;
+            const long long b2 = base + a.nx;
 #pragma unroll
-            for (int k = 0; k < NPLANES; ++k) a.fout[k * a.plane + b2] = v[k];
+            for (int j = 0; j < 5; ++j) {
+                a.fout[j * a.plane + b2] = lo[j];
+                a.fout[(5 + j) * a.plane + b2] = hi[j];
+            }
         }
         if (X >= a.nx - GHOST) {
-            const long long b2 = (long long)row * a.pitch + GHOST + X - a.nx;
+            const long long b2 = base - a.nx;
 #pragma unroll
-            for (int k = 0; k < NPLANES; ++k) a.fout[k * a.plane + b2] = v[k];
+            for (int j = 0; j < 5; ++j) {
+                a.fout[j * a.plane + b2] = lo[j];
+                a.fout[(5 + j) * a.plane + b2] = hi[j];
+            }
         }
     }
 }
 
-template <int NT, int MK, bool PL>
+// Shared-memory layout of one ring row: 5 pairs x NT columns, 8 bytes each.
+template <int NT>
+struct Ring {
+    static constexpr int ROW = 5 * NT * 8;  // bytes per ring row
+    static __device__ __forceinline__ int at(int j, int t) { return (j * NT + t) * 8; }
+};
+
+// Difference weights of one axis for pass 1 (h) and pass 2 (dt):
+// w = -step * k * (a1, a0, am2) with k = c/dx (or c times the metric).
+struct AxisW {
+    F2 h1, h0, h2, d1, d0, d2;
+};
+__device__ __forceinline__ AxisW axis_weights(float k, const StepArgs &a) {
+    AxisW w;
+    w.h1 = splat(-a.h * k * a.a1);
+    w.h0 = splat(-a.h * k * a.a0);
+    w.h2 = splat(-a.h * k * a.am2);
+    w.d1 = splat(-a.dt * k * a.a1);
+    w.d0 = splat(-a.dt * k * a.a0);
+    w.d2 = splat(-a.dt * k * a.am2);
+    return w;
+}
+
+// Streaming increment of population j (1..4) at a curvilinear node, added to
+// base: -step (|ct_xi| D_xi + |ct_eta| D_eta), upwinded by the sign of ct.
+// rows[0..4] are the ring rows of chi_eta - 2 .. chi_eta + 2.
+template <int NT>
+__device__ __forceinline__ F2 curvi_term(const unsigned char *const rows[5], int j, int t, float cxi, float ceta,
+                                         bool xadj_p, bool xadj_m, bool yadj_p, bool yadj_m, float step,
+                                         const StepArgs &a, F2 base) {
+    using R = Ring<NT>;
+    const unsigned char *mid = rows[2];
+    const F2 p0 = lds2(mid, R::at(j, t));
+    F2 acc = base;
+    if (cxi != 0.0f) {
+        const float k = -step * fabsf(cxi);
+        const F2 w1 = splat(k * a.a1), w0 = splat(k * a.a0), w2 = splat(k * a.am2);
+        if (cxi > 0.0f)
+            acc = stream2<true>(acc, lds2(mid, R::at(j, t + 1)), p0, lds2(mid, R::at(j, t - 1)),
+                                lds2(mid, R::at(j, t - 2)), xadj_p, w1, w0, w2);
+        else
+            acc = stream2<true>(acc, lds2(mid, R::at(j, t - 1)), p0, lds2(mid, R::at(j, t + 1)),
+                                lds2(mid, R::at(j, t + 2)), xadj_m, w1, w0, w2);
+    }
+    if (ceta != 0.0f) {
+        const float k = -step * fabsf(ceta);
+        const F2 w1 = splat(k * a.a1), w0 = splat(k * a.a0), w2 = splat(k * a.am2);
+        if (ceta > 0.0f)
+            acc = stream2<true>(acc, lds2(rows[3], R::at(j, t)), p0, lds2(rows[1], R::at(j, t)),
+                                lds2(rows[0], R::at(j, t)), yadj_p, w1, w0, w2);
+        else
+            acc = stream2<true>(acc, lds2(rows[1], R::at(j, t)), p0, lds2(rows[3], R::at(j, t)),
+                                lds2(rows[4], R::at(j, t)), yadj_m, w1, w0, w2);
+    }
+    return acc;
+}
+
+template <int NT, int MK, bool PL, bool WALLS>
 __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    constexpr int ROW = NPLANES * NT;
-    float *tma = reinterpret_cast<float *>(smem_raw);
-    float *rB = tma + TMA_SLOTS * ROW;
-    float *rF = rB + RB * ROW;
-    float *rP = rF + RF * ROW;
-    float *rK = rP + RP * ROW;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(rK + (PL ? RK * 2 * NT : 0));
+    using R = Ring<NT>;
+    constexpr int TROW = NPLANES * NT * 4;  // bytes of one TMA row (10 planes x NT floats)
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *tma = smem;
+    unsigned char *ringP = tma + TMA_SLOTS * TROW;   // fhat^+
+    unsigned char *ringB = ringP + RING * R::ROW;    // fbar^+
+    unsigned char *ringF = ringB + RING * R::ROW;    // f(t+h)
+    float *ringK = reinterpret_cast<float *>(ringF + RING * R::ROW);  // power law: recovery rates
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(ringK + (PL ? RING * 2 * NT : 0));
     __shared__ int s_abort;
 
     const int t = threadIdx.x;
@@ -268,7 +376,7 @@ __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ CUtens
     const int X = x0 - 4 + t;
     const int y0 = blockIdx.y * a.H;
     const int y1 = min(y0 + a.H, a.ny);
-    const int nIt = (y1 - y0) + 8;
+    const int nIt = (y1 - y0) + 9;
     const int rowBase = y0 - 4;
     const float c = a.c, inv2c = a.inv2c;
 
@@ -278,287 +386,279 @@ __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ CUtens
         fence_mbar_init();
     }
     __syncthreads();
-    auto load_row = [&](int it) {
+    auto load_row = [&](int it, int slot) {
         const int p = rowBase + it;
-        const int yy = a.ywall ? p : wrap(p, a.ny);
-        const int slot = it % TMA_SLOTS;
-        mbar_expect_tx(&mbar[slot], ROW * 4);
-        tma_load_row(&tmap, &mbar[slot], tma + slot * ROW, x0, yy);
+        const int yy = (WALLS && a.ywall) ? p : wrap(p, a.ny);
+        mbar_expect_tx(&mbar[slot], TROW);
+        tma_load_row(&tmap, &mbar[slot], tma + slot * TROW, x0, yy);
     };
+    int issued = min(TMA_SLOTS, nIt);
     if (t == 0)
-        for (int i = 0; i < TMA_SLOTS && i < nIt; ++i) load_row(i);
+        for (int i = 0; i < issued; ++i) load_row(i, i);
 
     // per-column constants
-    const bool colx_wall = a.xwall && (X == 0 || X == a.nx - 1);
-    const bool colx_out = a.xwall ? (X < 0 || X >= a.nx) : false;
-    const bool xadj_plus = a.xwall && X == 1;            // +x population: far point beyond west wall
-    const bool xadj_minus = a.xwall && X == a.nx - 2;    // -x population: far point beyond east wall
-    float kxc = a.kx;
-    if (MK == METRIC_SEPARABLE) kxc = a.kxv[GHOST + X];
+    const bool xwall = WALLS && a.xwall;
+    const bool ywall = WALLS && a.ywall;
+    const bool colx_wall = xwall && (X == 0 || X == a.nx - 1);
+    const bool colx_out = xwall && (X < 0 || X >= a.nx);
+    const bool xadj_p = xwall && X == 1;
+    const bool xadj_m = xwall && X == a.nx - 2;
+    AxisW wx{}, wy{};
+    if (MK == METRIC_UNIFORM) {
+        wx = axis_weights(a.kx, a);
+        wy = axis_weights(a.ky, a);
+    } else if (MK == METRIC_SEPARABLE) {
+        wx = axis_weights(a.kxv[GHOST + X], a);
+    }
+    const F2 hw = splat(a.h * 0.2f), dw = splat(a.dt * 0.2f);
+    const F2 mKp = splat(-(1.0f - a.rpp)), Dp = splat(0.5f * (a.rp - a.rpp));
+    const F2 mKb = splat(-(1.0f - a.rbp)), Db = splat(0.5f * (a.rb - a.rbp));
+    const F2 mKk = splat(-(1.0f - a.rkp)), Dk = splat(0.5f * (a.rk - a.rkp));
 
-    int issued = min(TMA_SLOTS, nIt);
+    // Rotating slot offsets: o_k = byte offset of the ring row written k
+    // iterations ago (every ring is indexed by iteration mod 5; o0 is the
+    // slot written in the current iteration).
+    int o0 = 0, o1 = 4 * R::ROW, o2 = 3 * R::ROW, o3 = 2 * R::ROW, o4 = 1 * R::ROW;
+    int k0 = 0, k2 = 3 * 2 * NT;  // the same rotation for the power-law ring (floats)
+    int tslot = 0;
+
     for (int it = 0; it < nIt; ++it) {
         const int p = rowBase + it;
+        // ------------------------------------------------ Stage C: row r = p - 5
+        if (it >= 9 && t >= 4 && t < NT - 4) {
+            const int r = p - 5;
+            bool active = (X >= 0 && X < a.nx);
+            if (WALLS) active = active && !colx_wall && !(ywall && (r == 0 || r == a.ny - 1));
+            if (active) {
+                // F rows r-2..r+2 were written 5..1 iterations ago; fhat^+ of
+                // row r 5 iterations ago (slot o0, rewritten by stage A below).
+                const unsigned char *Fm2 = ringF + o0, *Fm1 = ringF + o4, *F0 = ringF + o3;
+                const unsigned char *Fp1 = ringF + o2, *Fp2 = ringF + o1;
+                const unsigned char *Pr = ringP + o0;
+                const bool yadj_p = ywall && r == 1, yadj_m = ywall && r == a.ny - 2;
+                F2 fF = splat(0.0f);
+                if (a.force_mode == 1) fF = dw * mk2(a.Fx, a.Fy);
+                else if (a.force_mode == 2) {
+                    const long long fi = (long long)r * a.pitch + GHOST + X;
+                    fF = dw * mk2(a.Fxp[fi], a.Fyp[fi]);
+                }
+                F2 out[5];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) out[j] = lds2(Pr, R::at(j, t)) + fF;
+                if (MK != METRIC_CURVILINEAR) {
+                    AxisW wyr = wy;
+                    if (MK == METRIC_SEPARABLE) wyr = axis_weights(a.kyv[r], a);
+                    out[1] = stream2<WALLS>(out[1], lds2(F0, R::at(1, t + 1)), lds2(F0, R::at(1, t)),
+                                            lds2(F0, R::at(1, t - 1)), lds2(F0, R::at(1, t - 2)), xadj_p, wx.d1,
+                                            wx.d0, wx.d2);
+                    out[3] = stream2<WALLS>(out[3], lds2(F0, R::at(3, t - 1)), lds2(F0, R::at(3, t)),
+                                            lds2(F0, R::at(3, t + 1)), lds2(F0, R::at(3, t + 2)), xadj_m, wx.d1,
+                                            wx.d0, wx.d2);
+                    out[2] = stream2<WALLS>(out[2], lds2(Fp1, R::at(2, t)), lds2(F0, R::at(2, t)),
+                                            lds2(Fm1, R::at(2, t)), lds2(Fm2, R::at(2, t)), yadj_p, wyr.d1, wyr.d0,
+                                            wyr.d2);
+                    out[4] = stream2<WALLS>(out[4], lds2(Fm1, R::at(4, t)), lds2(F0, R::at(4, t)),
+                                            lds2(Fp1, R::at(4, t)), lds2(Fp2, R::at(4, t)), yadj_m, wyr.d1, wyr.d0,
+                                            wyr.d2);
+                } else {
+                    const long long mi = (long long)r * a.pitch + GHOST + X;
+                    const float cxx = a.mxx[mi], cxy = a.mxy[mi], cex = a.mex[mi], cey = a.mey[mi];
+                    const unsigned char *const rows[5] = {Fm2, Fm1, F0, Fp1, Fp2};
+                    out[1] = curvi_term<NT>(rows, 1, t, cxx, cex, xadj_p, xadj_m, yadj_p, yadj_m, a.dt, a, out[1]);
+                    out[2] = curvi_term<NT>(rows, 2, t, cxy, cey, xadj_p, xadj_m, yadj_p, yadj_m, a.dt, a, out[2]);
+                    out[3] = curvi_term<NT>(rows, 3, t, -cxx, -cex, xadj_p, xadj_m, yadj_p, yadj_m, a.dt, a, out[3]);
+                    out[4] = curvi_term<NT>(rows, 4, t, -cxy, -cey, xadj_p, xadj_m, yadj_p, yadj_m, a.dt, a, out[4]);
+                }
+                if (!WALLS) {
+                    store_node<true>(a, r, X, out);
+                } else {
+                    // the x axis of a walled kernel may still be periodic
+                    if (xwall) store_node<false>(a, r, X, out);
+                    else store_node<true>(a, r, X, out);
+                    F2 w[5];
+                    if (xadj_p) { nee2(out, a.uw[0], a.vw[0], inv2c, w); store_node<false>(a, r, 0, w); }
+                    if (xadj_m) { nee2(out, a.uw[1], a.vw[1], inv2c, w); store_node<false>(a, r, a.nx - 1, w); }
+                    if (ywall && (r == 1 || r == a.ny - 2)) {
+                        const int rr = (r == 1) ? 0 : a.ny - 1;
+                        const int side = (r == 1) ? 2 : 3;
+                        nee2(out, a.uw[side], a.vw[side], inv2c, w);
+                        if (xwall) store_node<false>(a, rr, X, w);
+                        else store_node<true>(a, rr, X, w);
+                        if (xadj_p) { nee2(out, a.uw[0], a.vw[0], inv2c, w); store_node<false>(a, rr, 0, w); }
+                        if (xadj_m) { nee2(out, a.uw[1], a.vw[1], inv2c, w); store_node<false>(a, rr, a.nx - 1, w); }
+                    }
+                }
+            }
+        }
         // ------------------------------------------------ Stage A: row p
         {
-            const int slot = it % TMA_SLOTS;
-            const bool ok = mbar_wait_bounded(&mbar[slot], (uint32_t)((it / TMA_SLOTS) & 1));
+            const bool ok = mbar_wait_bounded(&mbar[tslot], (uint32_t)((it / TMA_SLOTS) & 1));
             if (!ok) atomicExch(&s_abort, 1);
-            const float *src = tma + slot * ROW;
-            float g[10];
+            const float *src = reinterpret_cast<const float *>(tma + tslot * TROW);
+            F2 g[5];
 #pragma unroll
-            for (int k = 0; k < NPLANES; ++k) g[k] = src[k * NT + t];
-            const Mom m = moments(g, c);
-            Rates R;
+            for (int j = 0; j < 5; ++j) g[j] = mk2(src[j * NT + t], src[(5 + j) * NT + t]);
+            const Mom2 m = moments2(g, c);
+            F2 n[5];
+            noneq2(g, m, inv2c, n);
+            const F2 n13 = n[1] - n[3], n24 = n[2] - n[4];
+            F2 mKp_ = mKp, Dp_ = Dp, mKb_ = mKb, Db_ = Db;
             if (PL) {
-                const float F1x = fmaf(m.u, m.u, m.P), F1y = m.u * m.v;
-                const float F2y = fmaf(m.v, m.v, m.P);
-                const float gx1 = c * m.d1x - F1x, gy1 = c * m.d1y - F1y;
-                const float gx2 = c * m.d2x - F1y, gy2 = c * m.d2y - F2y;
+                float gx1, gx2, gy1, gy2;
+                split2(splat(c) * n13, gx1, gx2);
+                split2(splat(c) * n24, gy1, gy2);
                 const float sxy = 0.5f * (gy1 + gx2);
                 const float gg = sqrtf(2.0f * (gx1 * gx1 + gy2 * gy2 + 2.0f * sxy * sxy));
-                const float nu = power_law_nu(gg, a);
-                R = rates_for(a.cs2 / nu, a.s_ratio, a.dt);
-                float *k = rK + (it % RK) * 2 * NT;
-                k[t] = R.rkp;
-                k[NT + t] = R.rk;
-            } else {
-                R.rpp = a.rpp; R.rp = a.rp; R.rbp = a.rbp; R.rb = a.rb;
+                const Rates Rr = rates_for(a.cs2 / power_law_nu(gg, a), a.s_ratio, a.dt);
+                mKp_ = splat(-(1.0f - Rr.rpp));
+                Dp_ = splat(0.5f * (Rr.rp - Rr.rpp));
+                mKb_ = splat(-(1.0f - Rr.rbp));
+                Db_ = splat(0.5f * (Rr.rb - Rr.rbp));
+                float *k = ringK + k0;
+                k[t] = Rr.rkp;
+                k[NT + t] = Rr.rk;
             }
-            float nq[10], o[10];
-            noneq(g, m, inv2c, nq);
-            relax10(g, nq, R.rpp, R.rp, o);
-            float *dP = rP + (it % RP) * ROW;
+            F2 o[5];
+            relax2(g, n, n13, n24, mKp_, Dp_, o);
+            unsigned char *dP = ringP + o0;
 #pragma unroll
-            for (int k = 0; k < NPLANES; ++k) dP[k * NT + t] = o[k];
-            relax10(g, nq, R.rbp, R.rb, o);
-            float *dB = rB + (it % RB) * ROW;
+            for (int j = 0; j < 5; ++j) sts2(dP, R::at(j, t), o[j]);
+            relax2(g, n, n13, n24, mKb_, Db_, o);
+            unsigned char *dB = ringB + o0;
 #pragma unroll
-            for (int k = 0; k < NPLANES; ++k) dB[k * NT + t] = o[k];
+            for (int j = 0; j < 5; ++j) sts2(dB, R::at(j, t), o[j]);
         }
-        // all threads are done with TMA slot `it % TMA_SLOTS` and ring rows
+        // all threads are done with TMA slot `tslot`, with the rows stage C
+        // read, and have written the ring rows of stage A
         if (__syncthreads_or(s_abort)) break;
         if (t == 0 && issued < nIt) {
             fence_proxy_async();
-            load_row(issued);
+            load_row(issued, tslot);
             ++issued;
         }
+        tslot = (tslot == TMA_SLOTS - 1) ? 0 : tslot + 1;
         // ------------------------------------------------ Stage B: row q = p - 2
         if (it >= 4 && t >= 2 && t < NT - 2) {
             const int q = p - 2;
-            const bool qwall = a.ywall && (q == 0 || q == a.ny - 1);
-            const bool qout = a.ywall && (q < 0 || q >= a.ny);
-            const int qw = a.ywall ? q : wrap(q, a.ny);
-            float *Fq = rF + ((it - 2) % RF) * ROW;
-            if (!qout && !colx_out) {
-                if (a.ywall && q == a.ny - 1) {
+            bool skip = false;
+            if (WALLS) skip = colx_out || (ywall && (q < 0 || q >= a.ny));
+            // the f row of q goes to slot o0 (the oldest f row, read by stage C above)
+            unsigned char *Fq = ringF + o0;
+            if (!skip) {
+                if (WALLS && ywall && q == a.ny - 1) {
                     // north wall row: NEE from row ny-2 (this column, written last iteration)
                     if (!colx_wall) {
-                        const float *Fn = rF + ((it - 3) % RF) * ROW;
-                        float g[10], w[10];
+                        const unsigned char *Fn = ringF + o1;
+                        F2 g[5], w[5];
 #pragma unroll
-                        for (int k = 0; k < NPLANES; ++k) g[k] = Fn[k * NT + t];
-                        nee(g, a.uw[3], a.vw[3], inv2c, w);
+                        for (int j = 0; j < 5; ++j) g[j] = lds2(Fn, R::at(j, t));
+                        nee2(g, a.uw[3], a.vw[3], inv2c, w);
 #pragma unroll
-                        for (int k = 0; k < NPLANES; ++k) Fq[k * NT + t] = w[k];
-                        if (xadj_plus) {  // north-west corner from the diagonal node
-                            nee(g, a.uw[0], a.vw[0], inv2c, w);
+                        for (int j = 0; j < 5; ++j) sts2(Fq, R::at(j, t), w[j]);
+                        if (xadj_p) {
+                            nee2(g, a.uw[0], a.vw[0], inv2c, w);
 #pragma unroll
-                            for (int k = 0; k < NPLANES; ++k) Fq[k * NT + t - 1] = w[k];
+                            for (int j = 0; j < 5; ++j) sts2(Fq, R::at(j, t - 1), w[j]);
                         }
-                        if (xadj_minus) {
-                            nee(g, a.uw[1], a.vw[1], inv2c, w);
+                        if (xadj_m) {
+                            nee2(g, a.uw[1], a.vw[1], inv2c, w);
 #pragma unroll
-                            for (int k = 0; k < NPLANES; ++k) Fq[k * NT + t + 1] = w[k];
+                            for (int j = 0; j < 5; ++j) sts2(Fq, R::at(j, t + 1), w[j]);
                         }
                     }
-                } else if (!qwall && !colx_wall) {
-                    // Step 2: fbar = fbar^+ - h c.grad fbar^+ + h w F
-                    const float *Bq = rB + ((it - 2) % RB) * ROW;
-                    const float *Bm2 = rB + ((it - 4) % RB) * ROW;
-                    const float *Bm1 = rB + ((it - 3) % RB) * ROW;
-                    const float *Bp1 = rB + ((it - 1) % RB) * ROW;
-                    const float *Bp2 = rB + (it % RB) * ROW;
-                    const bool yadj_plus = a.ywall && q == 1;
-                    const bool yadj_minus = a.ywall && q == a.ny - 2;
-                    float fx = 0.0f, fy = 0.0f;
-                    if (a.force_mode == 1) { fx = a.Fx; fy = a.Fy; }
+                } else if (!(WALLS && ((ywall && q == 0) || colx_wall))) {
+                    // fbar^+ rows q-2..q+2 were written 4..0 iterations ago
+                    const unsigned char *Bm2 = ringB + o4, *Bm1 = ringB + o3, *B0 = ringB + o2;
+                    const unsigned char *Bp1 = ringB + o1, *Bp2 = ringB + o0;
+                    const int qw = (WALLS && ywall) ? q : wrap(q, a.ny);
+                    const bool yadj_p = ywall && q == 1, yadj_m = ywall && q == a.ny - 2;
+                    F2 fF = splat(0.0f);
+                    if (a.force_mode == 1) fF = hw * mk2(a.Fx, a.Fy);
                     else if (a.force_mode == 2) {
                         const long long fi = (long long)qw * a.pitch + GHOST + X;
-                        fx = a.Fxp[fi]; fy = a.Fyp[fi];
+                        fF = hw * mk2(a.Fxp[fi], a.Fyp[fi]);
                     }
-                    float fb[10];
+                    // Step 2 (pass 1): fbar = fbar^+ - h c.grad fbar^+ + h w F
+                    F2 fb[5];
 #pragma unroll
-                    for (int al = 0; al < 2; ++al) {
-                        const int b = 5 * al;
-                        const float hF = a.h * 0.2f * (al == 0 ? fx : fy);
-                        fb[b] = Bq[b * NT + t] + hF;
-                        // populations 1 (+x) and 3 (-x) along x
-                        const float *P1 = Bq + (b + 1) * NT + t;
-                        const float *P3 = Bq + (b + 3) * NT + t;
-                        const float *P2c = Bq + (b + 2) * NT + t;
-                        const float *P4c = Bq + (b + 4) * NT + t;
-                        if (MK != METRIC_CURVILINEAR) {
-                            const float kyq = (MK == METRIC_SEPARABLE) ? a.kyv[qw] : a.ky;
-                            const float s1 = kxc * stencil(P1[1], P1[0], P1[-1], P1[-2], xadj_plus, a);
-                            const float s3 = kxc * stencil(P3[-1], P3[0], P3[1], P3[2], xadj_minus, a);
-                            const float s2 = kyq * stencil(Bp1[(b + 2) * NT + t], P2c[0], Bm1[(b + 2) * NT + t],
-                                                           Bm2[(b + 2) * NT + t], yadj_plus, a);
-                            const float s4 = kyq * stencil(Bm1[(b + 4) * NT + t], P4c[0], Bp1[(b + 4) * NT + t],
-                                                           Bp2[(b + 4) * NT + t], yadj_minus, a);
-                            fb[b + 1] = fmaf(-a.h, s1, P1[0]) + hF;
-                            fb[b + 3] = fmaf(-a.h, s3, P3[0]) + hF;
-                            fb[b + 2] = fmaf(-a.h, s2, P2c[0]) + hF;
-                            fb[b + 4] = fmaf(-a.h, s4, P4c[0]) + hF;
-                        } else {
-                            const long long mi = (long long)qw * a.pitch + GHOST + X;
-                            const float cxx = a.mxx[mi], cxy = a.mxy[mi], cex = a.mex[mi], cey = a.mey[mi];
-#pragma unroll
-                            for (int j = 1; j <= 4; ++j) {
-                                const float sx = (j == 1) ? cxx : (j == 2) ? cxy : (j == 3) ? -cxx : -cxy;
-                                const float se = (j == 1) ? cex : (j == 2) ? cey : (j == 3) ? -cex : -cey;
-                                const float *Px = Bq + (b + j) * NT + t;
-                                float acc = 0.0f;
-                                if (sx != 0.0f) {
-                                    const float st = sx > 0.0f ? stencil(Px[1], Px[0], Px[-1], Px[-2], xadj_plus, a)
-                                                               : stencil(Px[-1], Px[0], Px[1], Px[2], xadj_minus, a);
-                                    acc = fabsf(sx) * st;
-                                }
-                                if (se != 0.0f) {
-                                    const float pm2 = Bm2[(b + j) * NT + t], pm1 = Bm1[(b + j) * NT + t];
-                                    const float pp1 = Bp1[(b + j) * NT + t], pp2 = Bp2[(b + j) * NT + t];
-                                    const float st = se > 0.0f ? stencil(pp1, Px[0], pm1, pm2, yadj_plus, a)
-                                                               : stencil(pm1, Px[0], pp1, pp2, yadj_minus, a);
-                                    acc = fmaf(fabsf(se), st, acc);
-                                }
-                                fb[b + j] = fmaf(-a.h, acc, Px[0]) + hF;
-                            }
-                        }
+                    for (int j = 0; j < 5; ++j) fb[j] = lds2(B0, R::at(j, t)) + fF;
+                    if (MK != METRIC_CURVILINEAR) {
+                        AxisW wyq = wy;
+                        if (MK == METRIC_SEPARABLE) wyq = axis_weights(a.kyv[qw], a);
+                        fb[1] = stream2<WALLS>(fb[1], lds2(B0, R::at(1, t + 1)), lds2(B0, R::at(1, t)),
+                                               lds2(B0, R::at(1, t - 1)), lds2(B0, R::at(1, t - 2)), xadj_p, wx.h1,
+                                               wx.h0, wx.h2);
+                        fb[3] = stream2<WALLS>(fb[3], lds2(B0, R::at(3, t - 1)), lds2(B0, R::at(3, t)),
+                                               lds2(B0, R::at(3, t + 1)), lds2(B0, R::at(3, t + 2)), xadj_m, wx.h1,
+                                               wx.h0, wx.h2);
+                        fb[2] = stream2<WALLS>(fb[2], lds2(Bp1, R::at(2, t)), lds2(B0, R::at(2, t)),
+                                               lds2(Bm1, R::at(2, t)), lds2(Bm2, R::at(2, t)), yadj_p, wyq.h1, wyq.h0,
+                                               wyq.h2);
+                        fb[4] = stream2<WALLS>(fb[4], lds2(Bm1, R::at(4, t)), lds2(B0, R::at(4, t)),
+                                               lds2(Bp1, R::at(4, t)), lds2(Bp2, R::at(4, t)), yadj_m, wyq.h1, wyq.h0,
+                                               wyq.h2);
+                    } else {
+                        const long long mi = (long long)qw * a.pitch + GHOST + X;
+                        const float cxx = a.mxx[mi], cxy = a.mxy[mi], cex = a.mex[mi], cey = a.mey[mi];
+                        const unsigned char *const rows[5] = {Bm2, Bm1, B0, Bp1, Bp2};
+                        fb[1] = curvi_term<NT>(rows, 1, t, cxx, cex, xadj_p, xadj_m, yadj_p, yadj_m, a.h, a, fb[1]);
+                        fb[2] = curvi_term<NT>(rows, 2, t, cxy, cey, xadj_p, xadj_m, yadj_p, yadj_m, a.h, a, fb[2]);
+                        fb[3] = curvi_term<NT>(rows, 3, t, -cxx, -cex, xadj_p, xadj_m, yadj_p, yadj_m, a.h, a, fb[3]);
+                        fb[4] = curvi_term<NT>(rows, 4, t, -cxy, -cey, xadj_p, xadj_m, yadj_p, yadj_m, a.h, a, fb[4]);
                     }
                     // Step 3: f = feq + (I + h/2 Lt)^-1 (fbar - feq)
-                    float rkp = a.rkp, rk = a.rk;
+                    F2 mKk_ = mKk, Dk_ = Dk;
                     if (PL) {
-                        const float *k = rK + ((it - 2) % RK) * 2 * NT;
-                        rkp = k[t];
-                        rk = k[NT + t];
+                        const float *k = ringK + k2;  // rates of row q, written 2 iterations ago
+                        mKk_ = splat(-(1.0f - k[t]));
+                        Dk_ = splat(0.5f * (k[NT + t] - k[t]));
                     }
-                    const Mom m = moments(fb, c);
-                    float nq[10], f[10];
-                    noneq(fb, m, inv2c, nq);
-                    relax10(fb, nq, rkp, rk, f);
+                    const Mom2 m = moments2(fb, c);
+                    F2 n[5], f[5];
+                    noneq2(fb, m, inv2c, n);
+                    relax2(fb, n, n[1] - n[3], n[2] - n[4], mKk_, Dk_, f);
 #pragma unroll
-                    for (int k = 0; k < NPLANES; ++k) Fq[k * NT + t] = f[k];
-                    float w[10];
-                    if (xadj_plus) {  // west wall node of this row
-                        nee(f, a.uw[0], a.vw[0], inv2c, w);
+                    for (int j = 0; j < 5; ++j) sts2(Fq, R::at(j, t), f[j]);
+                    if (WALLS) {
+                        F2 w[5];
+                        if (xadj_p) {  // west wall node of this row
+                            nee2(f, a.uw[0], a.vw[0], inv2c, w);
 #pragma unroll
-                        for (int k = 0; k < NPLANES; ++k) Fq[k * NT + t - 1] = w[k];
-                    }
-                    if (xadj_minus) {
-                        nee(f, a.uw[1], a.vw[1], inv2c, w);
-#pragma unroll
-                        for (int k = 0; k < NPLANES; ++k) Fq[k * NT + t + 1] = w[k];
-                    }
-                    if (a.ywall && q == 1) {  // south wall row (and corners) from row 1
-                        float *F0 = rF + ((it - 3) % RF) * ROW;
-                        nee(f, a.uw[2], a.vw[2], inv2c, w);
-#pragma unroll
-                        for (int k = 0; k < NPLANES; ++k) F0[k * NT + t] = w[k];
-                        if (xadj_plus) {
-                            nee(f, a.uw[0], a.vw[0], inv2c, w);
-#pragma unroll
-                            for (int k = 0; k < NPLANES; ++k) F0[k * NT + t - 1] = w[k];
+                            for (int j = 0; j < 5; ++j) sts2(Fq, R::at(j, t - 1), w[j]);
                         }
-                        if (xadj_minus) {
-                            nee(f, a.uw[1], a.vw[1], inv2c, w);
+                        if (xadj_m) {
+                            nee2(f, a.uw[1], a.vw[1], inv2c, w);
 #pragma unroll
-                            for (int k = 0; k < NPLANES; ++k) F0[k * NT + t + 1] = w[k];
+                            for (int j = 0; j < 5; ++j) sts2(Fq, R::at(j, t + 1), w[j]);
+                        }
+                        if (ywall && q == 1) {  // south wall row (and corners) from row 1
+                            unsigned char *F0r = ringF + o1;
+                            nee2(f, a.uw[2], a.vw[2], inv2c, w);
+#pragma unroll
+                            for (int j = 0; j < 5; ++j) sts2(F0r, R::at(j, t), w[j]);
+                            if (xadj_p) {
+                                nee2(f, a.uw[0], a.vw[0], inv2c, w);
+#pragma unroll
+                                for (int j = 0; j < 5; ++j) sts2(F0r, R::at(j, t - 1), w[j]);
+                            }
+                            if (xadj_m) {
+                                nee2(f, a.uw[1], a.vw[1], inv2c, w);
+#pragma unroll
+                                for (int j = 0; j < 5; ++j) sts2(F0r, R::at(j, t + 1), w[j]);
+                            }
                         }
                     }
                 }
             }
         }
         __syncthreads();
-        // ------------------------------------------------ Stage C: row r = p - 4
-        if (it >= 8 && t >= 4 && t < NT - 4) {
-            const int r = p - 4;
-            const bool active = (X >= 0 && X < a.nx) && !colx_wall && !(a.ywall && (r == 0 || r == a.ny - 1));
-            if (active) {
-                const int rw = r;  // r is inside [0, ny) by construction
-                const float *Pr = rP + ((it - 4) % RP) * ROW;
-                const float *Fr = rF + ((it - 4) % RF) * ROW;
-                const float *Fm2 = rF + ((it - 6) % RF) * ROW;
-                const float *Fm1 = rF + ((it - 5) % RF) * ROW;
-                const float *Fp1 = rF + ((it - 3) % RF) * ROW;
-                const float *Fp2 = rF + ((it - 2) % RF) * ROW;
-                const bool yadj_plus = a.ywall && r == 1;
-                const bool yadj_minus = a.ywall && r == a.ny - 2;
-                float fx = 0.0f, fy = 0.0f;
-                if (a.force_mode == 1) { fx = a.Fx; fy = a.Fy; }
-                else if (a.force_mode == 2) {
-                    const long long fi = (long long)rw * a.pitch + GHOST + X;
-                    fx = a.Fxp[fi]; fy = a.Fyp[fi];
-                }
-                float out[10];
-#pragma unroll
-                for (int al = 0; al < 2; ++al) {
-                    const int b = 5 * al;
-                    const float dF = a.dt * 0.2f * (al == 0 ? fx : fy);
-                    out[b] = Pr[b * NT + t] + dF;
-                    const float *P1 = Fr + (b + 1) * NT + t;
-                    const float *P3 = Fr + (b + 3) * NT + t;
-                    if (MK != METRIC_CURVILINEAR) {
-                        const float kyr = (MK == METRIC_SEPARABLE) ? a.kyv[rw] : a.ky;
-                        const float s1 = kxc * stencil(P1[1], P1[0], P1[-1], P1[-2], xadj_plus, a);
-                        const float s3 = kxc * stencil(P3[-1], P3[0], P3[1], P3[2], xadj_minus, a);
-                        const float s2 = kyr * stencil(Fp1[(b + 2) * NT + t], Fr[(b + 2) * NT + t],
-                                                       Fm1[(b + 2) * NT + t], Fm2[(b + 2) * NT + t], yadj_plus, a);
-                        const float s4 = kyr * stencil(Fm1[(b + 4) * NT + t], Fr[(b + 4) * NT + t],
-                                                       Fp1[(b + 4) * NT + t], Fp2[(b + 4) * NT + t], yadj_minus, a);
-                        out[b + 1] = fmaf(-a.dt, s1, Pr[(b + 1) * NT + t]) + dF;
-                        out[b + 3] = fmaf(-a.dt, s3, Pr[(b + 3) * NT + t]) + dF;
-                        out[b + 2] = fmaf(-a.dt, s2, Pr[(b + 2) * NT + t]) + dF;
-                        out[b + 4] = fmaf(-a.dt, s4, Pr[(b + 4) * NT + t]) + dF;
-                    } else {
-                        const long long mi = (long long)rw * a.pitch + GHOST + X;
-                        const float cxx = a.mxx[mi], cxy = a.mxy[mi], cex = a.mex[mi], cey = a.mey[mi];
-#pragma unroll
-                        for (int j = 1; j <= 4; ++j) {
-                            const float sx = (j == 1) ? cxx : (j == 2) ? cxy : (j == 3) ? -cxx : -cxy;
-                            const float se = (j == 1) ? cex : (j == 2) ? cey : (j == 3) ? -cex : -cey;
-                            const float *Px = Fr + (b + j) * NT + t;
-                            float acc = 0.0f;
-                            if (sx != 0.0f) {
-                                const float st = sx > 0.0f ? stencil(Px[1], Px[0], Px[-1], Px[-2], xadj_plus, a)
-                                                           : stencil(Px[-1], Px[0], Px[1], Px[2], xadj_minus, a);
-                                acc = fabsf(sx) * st;
-                            }
-                            if (se != 0.0f) {
-                                const float pm2 = Fm2[(b + j) * NT + t], pm1 = Fm1[(b + j) * NT + t];
-                                const float pp1 = Fp1[(b + j) * NT + t], pp2 = Fp2[(b + j) * NT + t];
-                                const float st = se > 0.0f ? stencil(pp1, Px[0], pm1, pm2, yadj_plus, a)
-                                                           : stencil(pm1, Px[0], pp1, pp2, yadj_minus, a);
-                                acc = fmaf(fabsf(se), st, acc);
-                            }
-                            out[b + j] = fmaf(-a.dt, acc, Pr[(b + j) * NT + t]) + dF;
-                        }
-                    }
-                }
-                store_node(a, rw, X, out);
-                // Walls after Step 4: NEE from this interior node.
-                if (a.xwall || a.ywall) {
-                    float w[10];
-                    if (xadj_plus) { nee(out, a.uw[0], a.vw[0], inv2c, w); store_node(a, rw, 0, w); }
-                    if (xadj_minus) { nee(out, a.uw[1], a.vw[1], inv2c, w); store_node(a, rw, a.nx - 1, w); }
-                    if (a.ywall && (r == 1 || r == a.ny - 2)) {
-                        const int rr = (r == 1) ? 0 : a.ny - 1;
-                        const int side = (r == 1) ? 2 : 3;
-                        nee(out, a.uw[side], a.vw[side], inv2c, w);
-                        store_node(a, rr, X, w);
-                        if (xadj_plus) { nee(out, a.uw[0], a.vw[0], inv2c, w); store_node(a, rr, 0, w); }
-                        if (xadj_minus) { nee(out, a.uw[1], a.vw[1], inv2c, w); store_node(a, rr, a.nx - 1, w); }
-                    }
-                }
+        // rotate: the slot written in this iteration becomes "1 iteration ago"
+        {
+            const int tmp = o4;
+            o4 = o3; o3 = o2; o2 = o1; o1 = o0; o0 = tmp;
+            if (PL) {
+                k0 = (k0 == 4 * 2 * NT) ? 0 : k0 + 2 * NT;
+                k2 = (k2 == 4 * 2 * NT) ? 0 : k2 + 2 * NT;
             }
         }
     }
@@ -575,15 +675,15 @@ __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ CUtens
     }
 }
 
-template <int NT, int MK, bool PL>
+template <int NT, int MK, bool PL, bool WALLS>
 int smem_bytes() {
-    return (TMA_SLOTS + RB + RF + RP) * NPLANES * NT * 4 + (PL ? RK * 2 * NT * 4 : 0) + TMA_SLOTS * 8;
+    return TMA_SLOTS * NPLANES * NT * 4 + 3 * RING * Ring<NT>::ROW + (PL ? RING * 2 * NT * 4 : 0) + TMA_SLOTS * 8;
 }
 
-template <int NT, int MK, bool PL>
+template <int NT, int MK, bool PL, bool WALLS>
 cudaError_t launch_t(const CUtensorMap *tmap, const StepArgs &args, const StepPlan &plan, cudaStream_t stream) {
-    auto k = step_kernel<NT, MK, PL>;
-    const int smem = smem_bytes<NT, MK, PL>();
+    auto k = step_kernel<NT, MK, PL, WALLS>;
+    const int smem = smem_bytes<NT, MK, PL, WALLS>();
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -594,16 +694,36 @@ cudaError_t launch_t(const CUtensorMap *tmap, const StepArgs &args, const StepPl
     return cudaGetLastError();
 }
 
-template <int NT, int MK, bool PL>
-cudaError_t occupancy_t(int *occ) {
-    auto k = step_kernel<NT, MK, PL>;
-    const int smem = smem_bytes<NT, MK, PL>();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+template <int NT, int MK, bool PL, bool WALLS>
+cudaError_t occupancy_t(int *occ, int *smem) {
+    auto k = step_kernel<NT, MK, PL, WALLS>;
+    *smem = smem_bytes<NT, MK, PL, WALLS>();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, NT, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, NT, *smem);
 }
 
 constexpr int kNT = 128;
+
+#define MDF_DISPATCH(FN, ...)                                                         \
+    switch (metric * 4 + (power_law ? 2 : 0) + (walls ? 1 : 0)) {                     \
+        case 0: return FN<kNT, METRIC_UNIFORM, false, false>(__VA_ARGS__);            \
+        case 1: return FN<kNT, METRIC_UNIFORM, false, true>(__VA_ARGS__);             \
+        case 2: return FN<kNT, METRIC_UNIFORM, true, false>(__VA_ARGS__);             \
+        case 3: return FN<kNT, METRIC_UNIFORM, true, true>(__VA_ARGS__);              \
+        case 4: return FN<kNT, METRIC_SEPARABLE, false, false>(__VA_ARGS__);          \
+        case 5: return FN<kNT, METRIC_SEPARABLE, false, true>(__VA_ARGS__);           \
+        case 6: return FN<kNT, METRIC_SEPARABLE, true, false>(__VA_ARGS__);           \
+        case 7: return FN<kNT, METRIC_SEPARABLE, true, true>(__VA_ARGS__);            \
+        case 8: return FN<kNT, METRIC_CURVILINEAR, false, false>(__VA_ARGS__);        \
+        case 9: return FN<kNT, METRIC_CURVILINEAR, false, true>(__VA_ARGS__);         \
+        case 10: return FN<kNT, METRIC_CURVILINEAR, true, false>(__VA_ARGS__);        \
+        default: return FN<kNT, METRIC_CURVILINEAR, true, true>(__VA_ARGS__);         \
+    }
+
+cudaError_t occupancy(int metric, int power_law, int walls, int *occ, int *smem) {
+    MDF_DISPATCH(occupancy_t, occ, smem)
+}
 
 }  // namespace
 
@@ -613,36 +733,17 @@ int step_pitch(int nx, int W) {
     return ((cols + 31) / 32) * 32;
 }
 
-#define MDF_DISPATCH(FN, ...)                                                              \
-    switch (metric * 2 + (power_law ? 1 : 0)) {                                             \
-        case 0: return FN<kNT, METRIC_UNIFORM, false>(__VA_ARGS__);                         \
-        case 1: return FN<kNT, METRIC_UNIFORM, true>(__VA_ARGS__);                          \
-        case 2: return FN<kNT, METRIC_SEPARABLE, false>(__VA_ARGS__);                       \
-        case 3: return FN<kNT, METRIC_SEPARABLE, true>(__VA_ARGS__);                        \
-        case 4: return FN<kNT, METRIC_CURVILINEAR, false>(__VA_ARGS__);                     \
-        default: return FN<kNT, METRIC_CURVILINEAR, true>(__VA_ARGS__);                     \
-    }
-
-static cudaError_t occupancy(int metric, int power_law, int *occ) { MDF_DISPATCH(occupancy_t, occ) }
-
-cudaError_t step_plan(int metric, int power_law, int nx, int ny, int num_sms, StepPlan *plan) {
+cudaError_t step_plan(int metric, int power_law, int walls, int nx, int ny, int num_sms, StepPlan *plan) {
     plan->NT = kNT;
     plan->W = kNT - 8;
-    int occ = 0;
-    cudaError_t e = occupancy(metric, power_law, &occ);
+    int occ = 0, smem = 0;
+    cudaError_t e = occupancy(metric, power_law, walls, &occ, &smem);
     if (e != cudaSuccess) return e;
     plan->occ = occ;
-    switch (metric * 2 + (power_law ? 1 : 0)) {
-        case 0: plan->smem = smem_bytes<kNT, METRIC_UNIFORM, false>(); break;
-        case 1: plan->smem = smem_bytes<kNT, METRIC_UNIFORM, true>(); break;
-        case 2: plan->smem = smem_bytes<kNT, METRIC_SEPARABLE, false>(); break;
-        case 3: plan->smem = smem_bytes<kNT, METRIC_SEPARABLE, true>(); break;
-        case 4: plan->smem = smem_bytes<kNT, METRIC_CURVILINEAR, false>(); break;
-        default: plan->smem = smem_bytes<kNT, METRIC_CURVILINEAR, true>(); break;
-    }
+    plan->smem = smem;
     plan->gx = (nx + plan->W - 1) / plan->W;
     // Bands: enough blocks to fill every SM at the measured occupancy, but no
-    // band shorter than 8 rows (the march recomputes 8 halo rows per band).
+    // band shorter than 8 rows (the march recomputes 9 halo rows per band).
     const int slots = (occ > 0 ? occ : 1) * (num_sms > 0 ? num_sms : 1);
     int bands = slots / plan->gx;
     if (bands < 1) bands = 1;
@@ -656,6 +757,7 @@ cudaError_t step_plan(int metric, int power_law, int nx, int ny, int num_sms, St
 cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
                         cudaStream_t stream) {
     const int power_law = args.power_law;
+    const int walls = (args.xwall || args.ywall) ? 1 : 0;
     MDF_DISPATCH(launch_t, tmap, args, plan, stream)
 }
 

@@ -278,7 +278,7 @@ def test_taylor_green_4096_full_size_against_oracle():
     g = mdf.Solver(n, n, nu=nu, lx=2 * math.pi, ly=2 * math.pi)
     o = Oracle(n, n, nu=nu, lx=2 * math.pi, ly=2 * math.pi)
     sg, so = run_both(g, o, (u, v, p), 3)
-    assert maxabs(sg, so) <= 1e-7 * U0
+    assert maxabs(sg, so) <= 5e-7 * U0  # a few FP32 ulps of the largest fhat (~U0/5)
     del o, so, sg
     g.init(u, v, p)
     g.step(200)
