@@ -335,6 +335,24 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
     for (int s = 0; s < 4; ++s) { a.uw[s] = x.uw[s]; a.vw[s] = x.vw[s]; }
     a.err = c->err;
     x.a_pl = a.a_pl;
+    if (grid->kind == MDF_GRID_UNIFORM) {
+        const float kxs = a.kx, kys = a.ky;
+        const float w[3] = {a.a1, a.a0, a.am2};
+        for (int i = 0; i < 3; ++i) {
+            a.pwxh[i] = pack_pair(-a.h * kxs * w[i]);
+            a.pwxd[i] = pack_pair(-a.dt * kxs * w[i]);
+            a.pwyh[i] = pack_pair(-a.h * kys * w[i]);
+            a.pwyd[i] = pack_pair(-a.dt * kys * w[i]);
+        }
+    }
+    a.pmKp = pack_pair(-(1.0f - a.rpp));
+    a.pDp = pack_pair(0.5f * (a.rp - a.rpp));
+    a.pmKb = pack_pair(-(1.0f - a.rbp));
+    a.pDb = pack_pair(0.5f * (a.rb - a.rbp));
+    a.pmKk = pack_pair(-(1.0f - a.rkp));
+    a.pDk = pack_pair(0.5f * (a.rk - a.rkp));
+    a.phw = pack_pair(a.h * 0.2f);
+    a.pdw = pack_pair(a.dt * 0.2f);
     CKC(encode_maps(c));
 
     // Rest state.

@@ -51,7 +51,24 @@ struct StepArgs {
     // wall velocities (west, east, south, north)
     float uw[4], vw[4];
     int *err;
+    // Packed (x, x) pairs of the constants above for the f32x2 fast path:
+    // difference weights -h k a and -dt k a of each axis (uniform grids),
+    // the relaxation increments -(1 - A') and (A - A')/2 of the three maps,
+    // and the source factors h/5, dt/5.
+    unsigned long long pwxh[3], pwxd[3], pwyh[3], pwyd[3];
+    unsigned long long pmKp, pDp, pmKb, pDb, pmKk, pDk, phw, pdw;
 };
+
+// Pair (x, x) as the 64-bit pattern the f32x2 instructions read.
+inline unsigned long long pack_pair(float x) {
+    union {
+        float f[2];
+        unsigned long long u;
+    } v;
+    v.f[0] = x;
+    v.f[1] = x;
+    return v.u;
+}
 
 // Fused step kernel launcher (mdf_step.cu).
 struct StepPlan {
@@ -66,5 +83,11 @@ cudaError_t step_plan(int metric, int power_law, int walls, int nx, int ny, int 
 cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
                         cudaStream_t stream);
 int step_pitch(int nx, int W);
+
+// Periodic Newtonian fast path on uniform/separable grids (mdf_step_fast.cu).
+bool fast_path_applies(int metric, int power_law, int walls);
+cudaError_t fast_occupancy(int metric, int *nt, int *occ, int *smem);
+cudaError_t fast_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
+                        cudaStream_t stream);
 
 }  // namespace mdf

@@ -37,269 +37,13 @@
 // read from HBM once.  Walls use non-equilibrium extrapolation written by the
 // interior neighbour's thread, and the second-order upwind point beyond a
 // wall is replaced by its linear extrapolation Pi(-1) = 2 Pi(0) - Pi(1).
-#include "mdf_internal.cuh"
+#include "mdf_device.cuh"
 
 namespace mdf {
 
 namespace {
 
-constexpr int TMA_SLOTS = 3;  // rows of fhat in flight
-constexpr int RING = 5;       // rows of every shared ring (stencil reach 2 + 2)
-
-// ------------------------------------------------------------ f32x2 pairs
-
-struct F2 {
-    unsigned long long r;
-};
-
-__device__ __forceinline__ F2 mk2(float x, float y) {
-    F2 a;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(a.r) : "f"(x), "f"(y));
-    return a;
-}
-__device__ __forceinline__ F2 splat(float x) { return mk2(x, x); }
-__device__ __forceinline__ void split2(F2 a, float &x, float &y) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.r));
-}
-__device__ __forceinline__ F2 operator+(F2 a, F2 b) {
-    F2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
-    return d;
-}
-__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
-    F2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
-    return d;
-}
-__device__ __forceinline__ F2 operator*(F2 a, F2 b) {
-    F2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
-    return d;
-}
-__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
-    F2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.r) : "l"(a.r), "l"(b.r), "l"(c.r));
-    return d;
-}
-__device__ __forceinline__ F2 sel2(bool p, F2 a, F2 b) {
-    F2 d;
-    d.r = p ? a.r : b.r;
-    return d;
-}
-__device__ __forceinline__ F2 lds2(const unsigned char *base, int byte_off) {
-    F2 a;
-    a.r = *reinterpret_cast<const unsigned long long *>(base + byte_off);
-    return a;
-}
-__device__ __forceinline__ void sts2(unsigned char *base, int byte_off, F2 a) {
-    *reinterpret_cast<unsigned long long *>(base + byte_off) = a.r;
-}
-
-// ------------------------------------------------------------ TMA, mbarrier
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: gives up after ~2^32 clock cycles (about two seconds).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > (1ll << 32)) return false;
-    }
-}
-__device__ __forceinline__ void tma_load_row(const CUtensorMap *map, uint64_t *bar, void *dst, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(0), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// ------------------------------------------------------------ local maps
-
-// Node in pair form: g[j] = (g_{j,u}, g_{j,v}), j = 0..4.
-// Moments shared by fhat, fbar and f: (u, v) = sum_j g_j, the odd
-// differences (g1 - g3), (g2 - g4) and P of Eq. 2.3.23 (R = 0).
-struct Mom2 {
-    F2 uv, d13, d24;
-    float u, v, P;
-};
-
-__device__ __forceinline__ Mom2 moments2(const F2 g[5], float c) {
-    Mom2 m;
-    m.uv = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
-    m.d13 = g[1] - g[3];
-    m.d24 = g[2] - g[4];
-    float d1x, d2x, d1y, d2y;
-    split2(m.d13, d1x, d2x);
-    split2(m.d24, d1y, d2y);
-    split2(m.uv, m.u, m.v);
-    m.P = 0.5f * (c * (d1x + d2y) - m.u * m.u - m.v * m.v);
-    return m;
-}
-
-// Non-equilibrium part n = g - feq (Eq. 2.2.5 on D2Q5 with w_j = 1/5 and
-// cs^2 = 2c^2/5: feq_0 = ub/5, feq_{1,3} = ub/5 +- Phi_x/(2c),
-// feq_{2,4} = ub/5 +- Phi_y/(2c), Phi = ub_alpha u + P E_alpha).  feq_0 is
-// formed as ub - 4 ub/5 so that sum_j feq_j = ub carries no rounding bias of
-// the constant 1/5; otherwise every step would scale the conserved zeroth
-// moments by the same FP32 factor and the drift would grow linearly in time.
-__device__ __forceinline__ void noneq2(const F2 g[5], const Mom2 &m, float inv2c, F2 n[5]) {
-    const F2 u5 = splat(0.2f) * m.uv;
-    const float uu = fmaf(m.u, m.u, m.P) * inv2c, uv = m.u * m.v * inv2c, vv = fmaf(m.v, m.v, m.P) * inv2c;
-    const F2 fx = mk2(uu, uv), fy = mk2(uv, vv);
-    n[0] = g[0] - fma2(splat(-4.0f), u5, m.uv);
-    n[1] = g[1] - (u5 + fx);
-    n[3] = g[3] - (u5 - fx);
-    n[2] = g[2] - (u5 + fy);
-    n[4] = g[4] - (u5 - fy);
-}
-
-// Local relaxation shared by Steps 1 and 3, as an increment:
-// out = g - (1 - Ap) n + (A - Ap) P_c n, which equals
-// feq + Ap (g - feq) + (A - Ap) P_c (g - feq); Ap / A are the eigenvalues on
-// the free / first-moment subspaces, (P_c n)_{1,3} = +-(n_1 - n_3)/2 and
-// (P_c n)_{2,4} = +-(n_2 - n_4)/2.  The zeroth moment is kept up to unbiased
-// per-node rounding.  n13 = n1 - n3, n24 = n2 - n4; mK = -(1 - Ap),
-// D = (A - Ap)/2.
-__device__ __forceinline__ void relax2(const F2 g[5], const F2 n[5], F2 n13, F2 n24, F2 mK, F2 D, F2 out[5]) {
-    const F2 dx = D * n13, dy = D * n24;
-    out[0] = fma2(mK, n[0], g[0]);
-    out[1] = fma2(mK, n[1], g[1]) + dx;
-    out[3] = fma2(mK, n[3], g[3]) - dx;
-    out[2] = fma2(mK, n[2], g[2]) + dy;
-    out[4] = fma2(mK, n[4], g[4]) - dy;
-}
-
-// Non-equilibrium extrapolation: node value = g_nb + feq(u_w, P) - feq(u_nb, P)
-// (the pressure cancels in the difference of the linear equilibria).
-__device__ __forceinline__ void nee2(const F2 g[5], float uw, float vw, float inv2c, F2 out[5]) {
-    float un, vn;
-    split2((g[0] + g[1]) + (g[2] + g[3]) + g[4], un, vn);
-    const float du = 0.2f * (uw - un), dv = 0.2f * (vw - vn);
-    const float uux = (uw * uw - un * un) * inv2c, uvy = (uw * vw - un * vn) * inv2c;
-    const float vvy = (vw * vw - vn * vn) * inv2c;
-    out[0] = g[0] + mk2(du, dv);
-    out[1] = g[1] + mk2(du + uux, dv + uvy);
-    out[3] = g[3] + mk2(du - uux, dv - uvy);
-    out[2] = g[2] + mk2(du + uvy, dv + vvy);
-    out[4] = g[4] + mk2(du - uvy, dv - vvy);
-}
-
-// Eigenvalues of the three local maps for first-moment rate s (s' = s_ratio s):
-// rho(l) = (1 - dt l/2)/(1 + dt l/2) for I - Lambda, (1 + 3 rho)/4 for
-// I - 3 Lambda/4, 1/(1 + h l/2) for (I + h/2 Lt)^-1.
-struct Rates {
-    float rpp, rp, rbp, rb, rkp, rk;
-};
-__device__ __forceinline__ Rates rates_for(float s, float s_ratio, float dt) {
-    const float sp = s_ratio * s;
-    Rates r;
-    r.rpp = (1.0f - 0.5f * dt * sp) / (1.0f + 0.5f * dt * sp);
-    r.rp = (1.0f - 0.5f * dt * s) / (1.0f + 0.5f * dt * s);
-    r.rbp = 0.25f * (1.0f + 3.0f * r.rpp);
-    r.rb = 0.25f * (1.0f + 3.0f * r.rp);
-    r.rkp = 1.0f / (1.0f + 0.25f * dt * sp);
-    r.rk = 1.0f / (1.0f + 0.25f * dt * s);
-    return r;
-}
-
-// Power-law viscosity nu = K gdot^(n-1), gdot = g/(nu + a), solved by Newton
-// iterations on l = ln nu (the residual l - ln K - (n-1)(ln g - ln(e^l + a))
-// has a derivative in (min(1,n), max(1,n)), so the iteration is safe), then
-// clamped to [nu_min, nu_max].
-__device__ __forceinline__ float power_law_nu(float g, const StepArgs &a) {
-    const float n = a.n_index;
-    if (n == 1.0f) return fminf(fmaxf(a.K, a.nu_min), a.nu_max);
-    if (!(g > 1e-30f)) return n < 1.0f ? a.nu_max : a.nu_min;
-    const float lnK = __logf(a.K), lng = __logf(g);
-    const float lmin = __logf(a.nu_min), lmax = __logf(a.nu_max);
-    float l = (lnK + (n - 1.0f) * lng) / n;
-    l = fminf(fmaxf(l, lmin), lmax);
-#pragma unroll
-    for (int it = 0; it < 8; ++it) {
-        const float e = __expf(l);
-        const float F = l - lnK - (n - 1.0f) * (lng - __logf(e + a.a_pl));
-        const float dF = 1.0f + (n - 1.0f) * e / (e + a.a_pl);
-        l = l - F / dF;
-        l = fminf(fmaxf(l, lmin - 1.0f), lmax + 1.0f);
-    }
-    return fminf(fmaxf(__expf(l), a.nu_min), a.nu_max);
-}
-
-// Streaming increment along one axis for a population moving towards +chi
-// (pf = Pi(+1), pb1 = Pi(-1), pb2 = Pi(-2)) or -chi (mirrored), added to
-// `base`:  w1 (Pi(+1) - Pi(-1)) + w0 (Pi(0) - Pi(-1)) + w2 (Pi(-2) - Pi(-1)),
-// the mixed scheme of Eqs. 2.2.12-2.2.13 written in differences (its weights
-// sum to zero, so a uniform field gives exactly zero).  Next to a wall the
-// far point is 2 Pi(-1) - Pi(0).  The weights carry -h c/dx (or -dt c/dx).
-template <bool WALLS>
-__device__ __forceinline__ F2 stream2(F2 base, F2 pf, F2 p0, F2 pb1, F2 pb2, bool wall_adj, F2 w1, F2 w0, F2 w2) {
-    const F2 d0 = p0 - pb1;
-    F2 dfar = pb2 - pb1;
-    if (WALLS) dfar = sel2(wall_adj, splat(0.0f) - d0, dfar);
-    return fma2(w1, pf - pb1, fma2(w0, d0, fma2(w2, dfar, base)));
-}
-
-__device__ __forceinline__ int wrap(int i, int n) {
-    i %= n;
-    return i < 0 ? i + n : i;
-}
-
-// Store one node (5 pairs -> 10 planes), with its periodic image in the ghost
-// columns when the x axis is periodic.
-template <bool XPER>
-__device__ __forceinline__ void store_node(const StepArgs &a, int row, int X, const F2 v[5]) {
-    const long long base = (long long)row * a.pitch + GHOST + X;
-    float lo[5], hi[5];
-#pragma unroll
-    for (int j = 0; j < 5; ++j) split2(v[j], lo[j], hi[j]);
-#pragma unroll
-    for (int j = 0; j < 5; ++j) {
-        a.fout[j * a.plane + base] = lo[j];
-        a.fout[(5 + j) * a.plane + base] = hi[j];
-    }
-    if (XPER) {
-        // a node can be the image of a ghost on both sides when nx < 2 GHOST
-        if (X < GHOST) {
-            const long long b2 = base + a.nx;
-#pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                a.fout[j * a.plane + b2] = lo[j];
-                a.fout[(5 + j) * a.plane + b2] = hi[j];
-            }
-        }
-        if (X >= a.nx - GHOST) {
-            const long long b2 = base - a.nx;
-#pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                a.fout[j * a.plane + b2] = lo[j];
-                a.fout[(5 + j) * a.plane + b2] = hi[j];
-            }
-        }
-    }
-}
+using namespace dev;
 
 // Shared-memory layout of one ring row: 5 pairs x NT columns, 8 bytes each.
 template <int NT>
@@ -735,10 +479,11 @@ int step_pitch(int nx, int W) {
 
 cudaError_t step_plan(int metric, int power_law, int walls, int nx, int ny, int num_sms, StepPlan *plan) {
     plan->NT = kNT;
-    plan->W = kNT - 8;
     int occ = 0, smem = 0;
-    cudaError_t e = occupancy(metric, power_law, walls, &occ, &smem);
+    cudaError_t e = fast_path_applies(metric, power_law, walls) ? fast_occupancy(metric, &plan->NT, &occ, &smem)
+                                                               : occupancy(metric, power_law, walls, &occ, &smem);
     if (e != cudaSuccess) return e;
+    plan->W = plan->NT - 8;
     plan->occ = occ;
     plan->smem = smem;
     plan->gx = (nx + plan->W - 1) / plan->W;
@@ -758,6 +503,7 @@ cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metri
                         cudaStream_t stream) {
     const int power_law = args.power_law;
     const int walls = (args.xwall || args.ywall) ? 1 : 0;
+    if (fast_path_applies(metric, power_law, walls)) return fast_launch(tmap, args, metric, plan, stream);
     MDF_DISPATCH(launch_t, tmap, args, plan, stream)
 }
 

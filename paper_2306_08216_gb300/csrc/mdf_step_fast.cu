@@ -1,0 +1,297 @@
+// mdf_step_fast.cu -- fused MDF-FDLBM step for periodic Newtonian problems on
+// uniform or separable (stretched) grids.
+//
+// Same time step as mdf_step.cu (Sec. 2.2 Steps (1)-(4) of arXiv:2306.08216
+// with Eqs. 2.3.24-2.3.25, f32x2 pairs for alpha = u, v), with less shared
+// memory per column so that more warps fit on an SM:
+//  * populations 2 and 4 stream along y only, which is the direction each
+//    thread marches, so their five-row windows of fbar^+ (pass 1) and of
+//    f(t+h) (pass 2) live in registers;
+//  * populations 1 and 3 stream along x only: their x stencils run on the row
+//    just formed, through one-row exchange buffers, and the results wait in
+//    registers until the y part of their row is ready;
+//  * fhat^+ waits five rows in a shared ring (it is needed when the output
+//    row is formed).
+// The march is unrolled by five so every window index is a compile-time
+// constant.  Per row, with p the newest row:
+//   S1: x increments of pass 2 for row p-3 (exchange buffer of f) and the
+//       output fhat(t+dt) of row r = p-5;
+//   S2: row p of fhat by TMA; fhat^+ -> ring, fbar^+ of pops 1,3 -> exchange
+//       buffer, of pops 2,4 -> register window;
+//   -- barrier --
+//   S3: pass 1 x part of row p; pass 1 y part, fbar and f(t+h) of row q = p-2;
+//       f of pops 1,3 -> exchange buffer, of pops 2,4 -> register window;
+//   -- barrier --
+#include "mdf_device.cuh"
+
+namespace mdf {
+
+namespace {
+
+using namespace dev;
+
+__device__ __forceinline__ F2 pair_of(unsigned long long bits) {
+    F2 a;
+    a.r = bits;
+    return a;
+}
+
+struct W3 {
+    F2 w1, w0, w2;
+};
+
+__device__ __forceinline__ W3 weights(float k, float step, const StepArgs &a) {
+    W3 w;
+    w.w1 = splat(-step * k * a.a1);
+    w.w0 = splat(-step * k * a.a0);
+    w.w2 = splat(-step * k * a.am2);
+    return w;
+}
+
+// Force increment factor (step/5) (Fx, Fy) at a node, F_{j,alpha} = w_j F_alpha.
+__device__ __forceinline__ F2 force_at(const StepArgs &a, int row, int X, F2 factor) {
+    if (a.force_mode == 1) return factor * mk2(a.Fx, a.Fy);
+    const long long fi = (long long)row * a.pitch + GHOST + X;
+    return factor * mk2(a.Fxp[fi], a.Fyp[fi]);
+}
+
+template <int NT, int MK>
+__global__ void __launch_bounds__(NT, 4) fast_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
+    constexpr int TROW = NPLANES * NT * 4;  // one TMA row: 10 planes x NT floats
+    constexpr int PROW = 5 * NT * 8;        // one fhat^+ ring row: 5 pairs x NT
+    constexpr int XROW = 2 * NT * 8;        // one exchange row: pops 1, 3 x NT
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *tma = smem;
+    unsigned char *ringP = tma + TMA_SLOTS * TROW;
+    unsigned char *xB = ringP + RING * PROW;  // fbar^+ of pops 1, 3 of row p
+    unsigned char *xF = xB + XROW;            // f(t+h) of pops 1, 3 of row q
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(xF + XROW);
+    __shared__ int s_abort;
+
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * a.W;
+    const int X = x0 - 4 + t;
+    const int y0 = blockIdx.y * a.H;
+    const int y1 = min(y0 + a.H, a.ny);
+    const int nIt = (y1 - y0) + 9;
+    const int rowBase = y0 - 4;
+    const float c = a.c, inv2c = a.inv2c;
+    const bool forced = a.force_mode != 0;
+
+    if (t == 0) {
+        s_abort = 0;
+        for (int i = 0; i < TMA_SLOTS; ++i) mbar_init(&mbar[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto load_row = [&](int it, int slot) {
+        mbar_expect_tx(&mbar[slot], TROW);
+        tma_load_row(&tmap, &mbar[slot], tma + slot * TROW, x0, wrap(rowBase + it, a.ny));
+    };
+    int issued = min(TMA_SLOTS, nIt);
+    if (t == 0)
+        for (int i = 0; i < issued; ++i) load_row(i, i);
+
+    W3 wxh, wxd;
+    if (MK == METRIC_UNIFORM) {
+        wxh = {pair_of(a.pwxh[0]), pair_of(a.pwxh[1]), pair_of(a.pwxh[2])};
+        wxd = {pair_of(a.pwxd[0]), pair_of(a.pwxd[1]), pair_of(a.pwxd[2])};
+    } else {
+        const float kx = a.kxv[GHOST + X];
+        wxh = weights(kx, a.h, a);
+        wxd = weights(kx, a.dt, a);
+    }
+    const F2 zero = splat(0.0f);
+    const bool calc = t >= 2 && t < NT - 2;   // forms fbar and f
+    const bool outc = t >= 4 && t < NT - 4 && X < a.nx;  // forms outputs
+
+    // register windows, slot = (row - rowBase) mod 5
+    F2 BY[5][2];    // fbar^+ of pops 2, 4
+    F2 D013[5][3];  // fbar of pops 0, 1, 3 (x part done)
+    F2 FY[5][2];    // f(t+h) of pops 2, 4
+    F2 XF[5][2];    // pass-2 x increments of pops 1, 3
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        BY[s][0] = BY[s][1] = FY[s][0] = FY[s][1] = XF[s][0] = XF[s][1] = zero;
+        D013[s][0] = D013[s][1] = D013[s][2] = zero;
+    }
+
+    int tslot = 0;
+    bool aborted = false;
+    for (int it0 = 0; it0 < nIt && !aborted; it0 += 5) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int it = it0 + k;
+            if (it >= nIt) break;
+            const int p = rowBase + it;
+            // slots of rows p-1 .. p-4 (row p-5 shares slot k with row p)
+            const int s1 = (k + 4) % 5, s2 = (k + 3) % 5, s3 = (k + 2) % 5, s4 = (k + 1) % 5;
+            // ---------------------------------------------- S1
+            if (it >= 5 && outc) {
+                // x increments of pass 2 for row p-3 (slot s3), from xF
+                const F2 f1p1 = lds2(xF, (t + 1) * 8), f1 = lds2(xF, t * 8);
+                const F2 f1m1 = lds2(xF, (t - 1) * 8), f1m2 = lds2(xF, (t - 2) * 8);
+                const F2 f3m1 = lds2(xF, (NT + t - 1) * 8), f3 = lds2(xF, (NT + t) * 8);
+                const F2 f3p1 = lds2(xF, (NT + t + 1) * 8), f3p2 = lds2(xF, (NT + t + 2) * 8);
+                XF[s3][0] = stream2<false>(zero, f1p1, f1, f1m1, f1m2, false, wxd.w1, wxd.w0, wxd.w2);
+                XF[s3][1] = stream2<false>(zero, f3m1, f3, f3p1, f3p2, false, wxd.w1, wxd.w0, wxd.w2);
+            }
+            if (it >= 9 && outc) {
+                // output row r = p - 5 (slot k of every window and of the ring)
+                const int r = p - 5;
+                const unsigned char *Pr = ringP + k * PROW;
+                F2 out[5];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) out[j] = lds2(Pr, (j * NT + t) * 8);
+                if (forced) {
+                    const F2 fF = force_at(a, r, X, pair_of(a.pdw));
+#pragma unroll
+                    for (int j = 0; j < 5; ++j) out[j] = out[j] + fF;
+                }
+                out[1] = out[1] + XF[k][0];
+                out[3] = out[3] + XF[k][1];
+                W3 wy;
+                if (MK == METRIC_UNIFORM) wy = {pair_of(a.pwyd[0]), pair_of(a.pwyd[1]), pair_of(a.pwyd[2])};
+                else wy = weights(a.kyv[r], a.dt, a);
+                // rows r-2, r-1, r, r+1, r+2 -> slots s2, s1, k, s4, s3
+                out[2] = stream2<false>(out[2], FY[s4][0], FY[k][0], FY[s1][0], FY[s2][0], false, wy.w1, wy.w0,
+                                        wy.w2);
+                out[4] = stream2<false>(out[4], FY[s1][1], FY[k][1], FY[s4][1], FY[s3][1], false, wy.w1, wy.w0,
+                                        wy.w2);
+                store_node<true>(a, r, X, out);
+            }
+            // ---------------------------------------------- S2: row p
+            F2 own1, own3;
+            {
+                const bool ok = mbar_wait_bounded(&mbar[tslot], (uint32_t)((it / TMA_SLOTS) & 1));
+                if (!ok) atomicExch(&s_abort, 1);
+                const float *src = reinterpret_cast<const float *>(tma + tslot * TROW);
+                F2 g[5];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) g[j] = mk2(src[j * NT + t], src[(5 + j) * NT + t]);
+                const Mom2 m = moments2(g, c);
+                F2 n[5], o[5];
+                noneq2(g, m, inv2c, n);
+                const F2 n13 = n[1] - n[3], n24 = n[2] - n[4];
+                relax2(g, n, n13, n24, pair_of(a.pmKp), pair_of(a.pDp), o);
+                unsigned char *dP = ringP + k * PROW;
+#pragma unroll
+                for (int j = 0; j < 5; ++j) sts2(dP, (j * NT + t) * 8, o[j]);
+                relax2(g, n, n13, n24, pair_of(a.pmKb), pair_of(a.pDb), o);
+                sts2(xB, t * 8, o[1]);
+                sts2(xB, (NT + t) * 8, o[3]);
+                own1 = o[1];
+                own3 = o[3];
+                BY[k][0] = o[2];
+                BY[k][1] = o[4];
+                D013[k][0] = o[0];
+            }
+            if (__syncthreads_or(s_abort)) {
+                aborted = true;
+                break;
+            }
+            if (t == 0 && issued < nIt) {
+                fence_proxy_async();
+                load_row(issued, tslot);
+                ++issued;
+            }
+            tslot = (tslot == TMA_SLOTS - 1) ? 0 : tslot + 1;
+            // ---------------------------------------------- S3
+            if (calc) {
+                // pass 1, x part of row p: fbar = fbar^+ - h c.grad fbar^+ + h w F
+                F2 hF = zero;
+                if (forced) hF = force_at(a, wrap(p, a.ny), X, pair_of(a.phw));
+                D013[k][0] = D013[k][0] + hF;
+                D013[k][1] = stream2<false>(own1 + hF, lds2(xB, (t + 1) * 8), own1, lds2(xB, (t - 1) * 8),
+                                            lds2(xB, (t - 2) * 8), false, wxh.w1, wxh.w0, wxh.w2);
+                D013[k][2] = stream2<false>(own3 + hF, lds2(xB, (NT + t - 1) * 8), own3, lds2(xB, (NT + t + 1) * 8),
+                                            lds2(xB, (NT + t + 2) * 8), false, wxh.w1, wxh.w0, wxh.w2);
+                if (it >= 4) {
+                    // row q = p - 2 (slot s2); fbar^+ rows q-2..q+2 -> slots s4, s3, s2, s1, k
+                    const int qw = wrap(p - 2, a.ny);
+                    F2 hFq = zero;
+                    if (forced) hFq = force_at(a, qw, X, pair_of(a.phw));
+                    W3 wy;
+                    if (MK == METRIC_UNIFORM) wy = {pair_of(a.pwyh[0]), pair_of(a.pwyh[1]), pair_of(a.pwyh[2])};
+                    else wy = weights(a.kyv[qw], a.h, a);
+                    F2 fb[5];
+                    fb[0] = D013[s2][0];
+                    fb[1] = D013[s2][1];
+                    fb[3] = D013[s2][2];
+                    fb[2] = stream2<false>(BY[s2][0] + hFq, BY[s1][0], BY[s2][0], BY[s3][0], BY[s4][0], false, wy.w1,
+                                           wy.w0, wy.w2);
+                    fb[4] = stream2<false>(BY[s2][1] + hFq, BY[s3][1], BY[s2][1], BY[s1][1], BY[k][1], false, wy.w1,
+                                           wy.w0, wy.w2);
+                    // Step 3: f = feq + (I + h/2 Lt)^-1 (fbar - feq)
+                    const Mom2 m = moments2(fb, c);
+                    F2 n[5], f[5];
+                    noneq2(fb, m, inv2c, n);
+                    relax2(fb, n, n[1] - n[3], n[2] - n[4], pair_of(a.pmKk), pair_of(a.pDk), f);
+                    sts2(xF, t * 8, f[1]);
+                    sts2(xF, (NT + t) * 8, f[3]);
+                    FY[s2][0] = f[2];
+                    FY[s2][1] = f[4];
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (s_abort) {
+        if (t == 0) {
+            for (int it = issued - TMA_SLOTS; it < issued; ++it) {
+                if (it < 0) continue;
+                mbar_wait_bounded(&mbar[it % TMA_SLOTS], (uint32_t)((it / TMA_SLOTS) & 1));
+            }
+            atomicCAS(a.err, DEVERR_NONE, DEVERR_TMA_TIMEOUT);
+        }
+    }
+}
+
+template <int NT>
+constexpr int fast_smem() {
+    return TMA_SLOTS * NPLANES * NT * 4 + RING * 5 * NT * 8 + 2 * (2 * NT * 8) + TMA_SLOTS * 8;
+}
+
+template <int NT, int MK>
+cudaError_t fast_launch_t(const CUtensorMap *tmap, const StepArgs &args, const StepPlan &plan, cudaStream_t stream) {
+    auto k = fast_kernel<NT, MK>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem<NT>());
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k<<<dim3(plan.gx, plan.gy), NT, fast_smem<NT>(), stream>>>(*tmap, args);
+    return cudaGetLastError();
+}
+
+template <int NT, int MK>
+cudaError_t fast_occupancy_t(int *occ, int *smem) {
+    auto k = fast_kernel<NT, MK>;
+    *smem = fast_smem<NT>();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, NT, *smem);
+}
+
+constexpr int kFastNT = 128;
+
+}  // namespace
+
+bool fast_path_applies(int metric, int power_law, int walls) {
+    return !walls && !power_law && (metric == METRIC_UNIFORM || metric == METRIC_SEPARABLE);
+}
+
+cudaError_t fast_occupancy(int metric, int *nt, int *occ, int *smem) {
+    *nt = kFastNT;
+    return metric == METRIC_UNIFORM ? fast_occupancy_t<kFastNT, METRIC_UNIFORM>(occ, smem)
+                                    : fast_occupancy_t<kFastNT, METRIC_SEPARABLE>(occ, smem);
+}
+
+cudaError_t fast_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
+                        cudaStream_t stream) {
+    return metric == METRIC_UNIFORM ? fast_launch_t<kFastNT, METRIC_UNIFORM>(tmap, args, plan, stream)
+                                    : fast_launch_t<kFastNT, METRIC_SEPARABLE>(tmap, args, plan, stream);
+}
+
+}  // namespace mdf
