@@ -195,6 +195,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch", default=None,
+                    help="threads,rows_per_block: pin the launch plan instead of the autotuned one (profiling)")
     ap.add_argument("--nx", type=int, default=NX,
                     help="grid side (default 4096, the benchmark workload; smaller sides only for profiling)")
     args = ap.parse_args()
@@ -223,6 +225,9 @@ def main():
     nx = ny = args.nx
     u, v, p = W.taylor_green(nx, U0)
     solver = mdf.Solver(nx, ny, nu=NU, lx=2 * math.pi, ly=2 * math.pi, stream=stream)
+    if args.launch:
+        threads, rows = (int(x) for x in args.launch.split(","))
+        solver.set_launch(threads, rows)
     solver.init(u, v, p)
     solver.step(args.warmup)
     solver.synchronize()

@@ -172,6 +172,14 @@ const char *mdf_last_error(const mdf_ctx *ctx);    /* ctx may be NULL */
  * info[6] blocks resident per SM (occupancy query; 0 without a GPU). */
 mdf_status mdf_launch_info(const mdf_ctx *ctx, int info[8]);
 
+/* Override the launch plan the library chose (tile-shape tuning): `threads`
+ * per block (128, or 256 on periodic Newtonian uniform/separable problems)
+ * and `rows_per_block` (>= 8) rows per block.  mdf_create times the
+ * candidate plans on grids of 2^20 nodes or more and keeps the fastest; this
+ * call replaces that choice.  Waits for the context's stream; MDF_E_INVALID
+ * for an unsupported block size. */
+mdf_status mdf_set_launch(mdf_ctx *ctx, int threads, int rows_per_block);
+
 /* Algorithmic bytes moved per node update by the fused step (state read and
  * written once, plus force/metric planes read once). */
 double mdf_bytes_per_node(const mdf_ctx *ctx);

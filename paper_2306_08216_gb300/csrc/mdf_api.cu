@@ -46,6 +46,9 @@ struct mdf_ctx {
     float *scratch = nullptr;  // dense staging for host transfers
     size_t scratch_bytes = 0;
     CUtensorMap tmap[2];
+    static constexpr int kMaxCandidates = 8;
+    StepPlan cand[kMaxCandidates];
+    int ncand = 0;
     StepPlan plan{};
     StepArgs args{};
     AuxArgs aux{};
@@ -165,6 +168,49 @@ static mdf_status wait_stream(mdf_ctx *c, double timeout_s) {
     return MDF_OK;
 }
 
+// Launch-plan autotuner: on grids of a million nodes or more, time every
+// candidate plan (block size, band height) for a few steps on the rest state
+// (a fixed point of the step, so buffer 0 keeps its contents; the output goes
+// to buffer 1) and keep the fastest.  Smaller grids keep the default plan.
+static mdf_status autotune(mdf_ctx *c) {
+    if (c->ncand > 1 && (long long)c->nx * c->ny >= (1ll << 20)) {
+        cudaEvent_t e0, e1;
+        CK(c, cudaEventCreate(&e0));
+        CK(c, cudaEventCreate(&e1));
+        float best = 1e30f;
+        int best_i = 0;
+        // two rounds over the candidates, 8 timed launches each; keep the
+        // fastest time seen per candidate
+        for (int round = 0; round < 2; ++round)
+        for (int i = 0; i < c->ncand; ++i) {
+            c->plan = c->cand[i];
+            mdf_status s = encode_maps(c);
+            if (s != MDF_OK) return s;
+            StepArgs a = c->args;
+            a.W = c->plan.W;
+            a.H = c->plan.H;
+            a.fout = c->buf[1];
+            CK(c, step_launch(&c->tmap[0], a, c->kind, c->plan, 0));
+            CK(c, cudaEventRecord(e0, 0));
+            for (int r = 0; r < 8; ++r) CK(c, step_launch(&c->tmap[0], a, c->kind, c->plan, 0));
+            CK(c, cudaEventRecord(e1, 0));
+            CK(c, cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            CK(c, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_i = i;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->plan = c->cand[best_i];
+    }
+    c->args.W = c->plan.W;
+    c->args.H = c->plan.H;
+    return encode_maps(c);
+}
+
 extern "C" {
 
 mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc *bc, const mdf_params *params,
@@ -231,8 +277,19 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
     CKE(cudaGetDevice(&c->dev));
     CKE(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
     const int metric = grid->kind;
-    CKE(step_plan(metric, fluid->power_law ? 1 : 0, (xwall || ywall) ? 1 : 0, c->nx, c->ny, c->num_sms, &c->plan));
-    c->pitch = step_pitch(c->nx, c->plan.W);
+    {
+        cudaError_t pe = cudaSuccess;
+        c->ncand = step_candidates(metric, fluid->power_law ? 1 : 0, (xwall || ywall) ? 1 : 0, c->nx, c->ny,
+                                   c->num_sms, c->cand, mdf_ctx::kMaxCandidates, &pe);
+        CKE(pe);
+        if (c->ncand < 1) CKE(cudaErrorInvalidConfiguration);
+    }
+    c->plan = c->cand[0];
+    c->pitch = 0;
+    for (int i = 0; i < c->ncand; ++i) {
+        const int pt = step_pitch(c->nx, c->cand[i].W);
+        if (pt > c->pitch) c->pitch = pt;
+    }
     c->plane = (long long)c->pitch * c->ny;
     const size_t state_bytes = (size_t)NPLANES * c->plane * sizeof(float);
     for (int b = 0; b < 2; ++b) {
@@ -361,6 +418,7 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
     CKE(aux_init(x, c->scratch, c->scratch + N, c->scratch + 2 * N, c->buf[0], 0));
     CKE(aux_snapshot(x, c->buf[0], c->snap_u, c->snap_v, 0));
     CKE(cudaDeviceSynchronize());
+    CKC(autotune(c));
     c->cur = 0;
     *out = c;
     return MDF_OK;
@@ -596,6 +654,23 @@ mdf_status mdf_launch_info(const mdf_ctx *c, int info[8]) {
     info[6] = c->plan.occ;
     info[7] = c->pitch;
     return MDF_OK;
+}
+
+mdf_status mdf_set_launch(mdf_ctx *c, int threads, int rows_per_block) {
+    if (!c) return MDF_E_INVALID;
+    int found = -1;
+    for (int i = 0; i < c->ncand; ++i)
+        if (c->cand[i].NT == threads) { found = i; break; }
+    if (found < 0) return fail(c, MDF_E_INVALID, "no launch plan with %d threads for this problem", threads);
+    if (rows_per_block < 8) return fail(c, MDF_E_INVALID, "rows_per_block must be >= 8");
+    StepPlan p = c->cand[found];
+    p.H = rows_per_block;
+    p.gy = (c->ny + p.H - 1) / p.H;
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->plan = p;
+    c->args.W = p.W;
+    c->args.H = p.H;
+    return encode_maps(c);
 }
 
 double mdf_bytes_per_node(const mdf_ctx *c) {

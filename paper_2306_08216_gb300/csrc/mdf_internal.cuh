@@ -79,14 +79,17 @@ struct StepPlan {
     int occ;      // resident blocks per SM
 };
 
-cudaError_t step_plan(int metric, int power_law, int walls, int nx, int ny, int num_sms, StepPlan *plan);
+// Candidate launch plans of the fused step (the first one is the default);
+// returns how many were written to out[0..max).
+int step_candidates(int metric, int power_law, int walls, int nx, int ny, int num_sms, StepPlan *out, int max,
+                    cudaError_t *err);
 cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
                         cudaStream_t stream);
 int step_pitch(int nx, int W);
 
 // Periodic Newtonian fast path on uniform/separable grids (mdf_step_fast.cu).
 bool fast_path_applies(int metric, int power_law, int walls);
-cudaError_t fast_occupancy(int metric, int *nt, int *occ, int *smem);
+cudaError_t fast_occupancy(int metric, int nt, int *occ, int *smem);
 cudaError_t fast_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
                         cudaStream_t stream);
 

@@ -477,26 +477,43 @@ int step_pitch(int nx, int W) {
     return ((cols + 31) / 32) * 32;
 }
 
-cudaError_t step_plan(int metric, int power_law, int walls, int nx, int ny, int num_sms, StepPlan *plan) {
-    plan->NT = kNT;
-    int occ = 0, smem = 0;
-    cudaError_t e = fast_path_applies(metric, power_law, walls) ? fast_occupancy(metric, &plan->NT, &occ, &smem)
-                                                               : occupancy(metric, power_law, walls, &occ, &smem);
-    if (e != cudaSuccess) return e;
-    plan->W = plan->NT - 8;
+// Launch geometry for block size nt and `waves` blocks per resident slot:
+// a strip of nt - 8 output columns per block, bands sized so the grid fills
+// every SM at the measured occupancy (no band shorter than 8 rows: the
+// march recomputes 9 halo rows per band).
+static void fill_plan(int nt, int occ, int smem, int waves, int nx, int ny, int num_sms, StepPlan *plan) {
+    plan->NT = nt;
+    plan->W = nt - 8;
     plan->occ = occ;
     plan->smem = smem;
     plan->gx = (nx + plan->W - 1) / plan->W;
-    // Bands: enough blocks to fill every SM at the measured occupancy, but no
-    // band shorter than 8 rows (the march recomputes 9 halo rows per band).
-    const int slots = (occ > 0 ? occ : 1) * (num_sms > 0 ? num_sms : 1);
+    const int slots = waves * (occ > 0 ? occ : 1) * (num_sms > 0 ? num_sms : 1);
     int bands = slots / plan->gx;
     if (bands < 1) bands = 1;
     int H = (ny + bands - 1) / bands;
     if (H < 8) H = 8;
     plan->H = H;
     plan->gy = (ny + H - 1) / H;
-    return cudaSuccess;
+}
+
+int step_candidates(int metric, int power_law, int walls, int nx, int ny, int num_sms, StepPlan *out, int max,
+                    cudaError_t *err) {
+    int n = 0;
+    *err = cudaSuccess;
+    const bool fast = fast_path_applies(metric, power_law, walls);
+    const int nts[2] = {128, 256};
+    for (int i = 0; i < (fast ? 2 : 1); ++i) {
+        int occ = 0, smem = 0;
+        cudaError_t e = fast ? fast_occupancy(metric, nts[i], &occ, &smem)
+                             : occupancy(metric, power_law, walls, &occ, &smem);
+        if (e != cudaSuccess) {
+            *err = e;
+            return n;
+        }
+        if (occ < 1) continue;
+        for (int waves = 1; waves <= 2 && n < max; ++waves) fill_plan(nts[i], occ, smem, waves, nx, ny, num_sms, &out[n++]);
+    }
+    return n;
 }
 
 cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,

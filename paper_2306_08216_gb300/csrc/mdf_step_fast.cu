@@ -14,14 +14,15 @@
 //    row is formed).
 // The march is unrolled by five so every window index is a compile-time
 // constant.  Per row, with p the newest row:
-//   S1: x increments of pass 2 for row p-3 (exchange buffer of f) and the
-//       output fhat(t+dt) of row r = p-5;
+//   S0: output fhat(t+dt) of row r = p-5 (fhat^+ ring, register windows);
 //   S2: row p of fhat by TMA; fhat^+ -> ring, fbar^+ of pops 1,3 -> exchange
 //       buffer, of pops 2,4 -> register window;
-//   -- barrier --
+//   -- the one barrier of the row --
+//   S1: pass 2 x increments of row p-3 from the previous row's f exchange;
 //   S3: pass 1 x part of row p; pass 1 y part, fbar and f(t+h) of row q = p-2;
-//       f of pops 1,3 -> exchange buffer, of pops 2,4 -> register window;
-//   -- barrier --
+//       f of pops 1,3 -> exchange buffer, of pops 2,4 -> register window.
+// The exchange buffers are double-buffered by row parity, which is what lets
+// a single barrier per row order every shared-memory hand-off.
 #include "mdf_device.cuh"
 
 namespace mdf {
@@ -55,17 +56,17 @@ __device__ __forceinline__ F2 force_at(const StepArgs &a, int row, int X, F2 fac
     return factor * mk2(a.Fxp[fi], a.Fyp[fi]);
 }
 
-template <int NT, int MK>
-__global__ void __launch_bounds__(NT, 4) fast_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
+template <int NT, int MK, bool FORCED>
+__global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) fast_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
     constexpr int TROW = NPLANES * NT * 4;  // one TMA row: 10 planes x NT floats
     constexpr int PROW = 5 * NT * 8;        // one fhat^+ ring row: 5 pairs x NT
     constexpr int XROW = 2 * NT * 8;        // one exchange row: pops 1, 3 x NT
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *tma = smem;
     unsigned char *ringP = tma + TMA_SLOTS * TROW;
-    unsigned char *xB = ringP + RING * PROW;  // fbar^+ of pops 1, 3 of row p
-    unsigned char *xF = xB + XROW;            // f(t+h) of pops 1, 3 of row q
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(xF + XROW);
+    unsigned char *xB0 = ringP + RING * PROW;  // fbar^+ of pops 1, 3 of row p (two buffers)
+    unsigned char *xF0 = xB0 + 2 * XROW;       // f(t+h) of pops 1, 3 of row q (two buffers)
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(xF0 + 2 * XROW);
     __shared__ int s_abort;
 
     const int t = threadIdx.x;
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(NT, 4) fast_kernel(const __grid_constant__ CUt
     const int nIt = (y1 - y0) + 9;
     const int rowBase = y0 - 4;
     const float c = a.c, inv2c = a.inv2c;
-    const bool forced = a.force_mode != 0;
+    constexpr bool forced = FORCED;
 
     if (t == 0) {
         s_abort = 0;
@@ -126,18 +127,13 @@ __global__ void __launch_bounds__(NT, 4) fast_kernel(const __grid_constant__ CUt
             const int p = rowBase + it;
             // slots of rows p-1 .. p-4 (row p-5 shares slot k with row p)
             const int s1 = (k + 4) % 5, s2 = (k + 3) % 5, s3 = (k + 2) % 5, s4 = (k + 1) % 5;
-            // ---------------------------------------------- S1
-            if (it >= 5 && outc) {
-                // x increments of pass 2 for row p-3 (slot s3), from xF
-                const F2 f1p1 = lds2(xF, (t + 1) * 8), f1 = lds2(xF, t * 8);
-                const F2 f1m1 = lds2(xF, (t - 1) * 8), f1m2 = lds2(xF, (t - 2) * 8);
-                const F2 f3m1 = lds2(xF, (NT + t - 1) * 8), f3 = lds2(xF, (NT + t) * 8);
-                const F2 f3p1 = lds2(xF, (NT + t + 1) * 8), f3p2 = lds2(xF, (NT + t + 2) * 8);
-                XF[s3][0] = stream2<false>(zero, f1p1, f1, f1m1, f1m2, false, wxd.w1, wxd.w0, wxd.w2);
-                XF[s3][1] = stream2<false>(zero, f3m1, f3, f3p1, f3p2, false, wxd.w1, wxd.w0, wxd.w2);
-            }
+            // exchange buffers of this iteration (fbar^+) and of the previous one (f)
+            unsigned char *xB = xB0 + (it & 1) * XROW;
+            const unsigned char *xFp = xF0 + ((it & 1) ^ 1) * XROW;
+            unsigned char *xF = xF0 + (it & 1) * XROW;
+            // ---------------------------------------------- S0: output row r = p - 5
             if (it >= 9 && outc) {
-                // output row r = p - 5 (slot k of every window and of the ring)
+                // slot k of every window and of the ring holds row r
                 const int r = p - 5;
                 const unsigned char *Pr = ringP + k * PROW;
                 F2 out[5];
@@ -186,6 +182,9 @@ __global__ void __launch_bounds__(NT, 4) fast_kernel(const __grid_constant__ CUt
                 BY[k][1] = o[4];
                 D013[k][0] = o[0];
             }
+            // One barrier per row: the exchange rows are double-buffered, so
+            // the buffers written before this barrier are read only after it,
+            // and those read after it are rewritten only after the next one.
             if (__syncthreads_or(s_abort)) {
                 aborted = true;
                 break;
@@ -196,6 +195,15 @@ __global__ void __launch_bounds__(NT, 4) fast_kernel(const __grid_constant__ CUt
                 ++issued;
             }
             tslot = (tslot == TMA_SLOTS - 1) ? 0 : tslot + 1;
+            // ---------------------------------------------- S1: pass-2 x increments of row p-3
+            if (it >= 5 && outc) {
+                const F2 f1p1 = lds2(xFp, (t + 1) * 8), f1 = lds2(xFp, t * 8);
+                const F2 f1m1 = lds2(xFp, (t - 1) * 8), f1m2 = lds2(xFp, (t - 2) * 8);
+                const F2 f3m1 = lds2(xFp, (NT + t - 1) * 8), f3 = lds2(xFp, (NT + t) * 8);
+                const F2 f3p1 = lds2(xFp, (NT + t + 1) * 8), f3p2 = lds2(xFp, (NT + t + 2) * 8);
+                XF[s3][0] = stream2<false>(zero, f1p1, f1, f1m1, f1m2, false, wxd.w1, wxd.w0, wxd.w2);
+                XF[s3][1] = stream2<false>(zero, f3m1, f3, f3p1, f3p2, false, wxd.w1, wxd.w0, wxd.w2);
+            }
             // ---------------------------------------------- S3
             if (calc) {
                 // pass 1, x part of row p: fbar = fbar^+ - h c.grad fbar^+ + h w F
@@ -233,7 +241,6 @@ __global__ void __launch_bounds__(NT, 4) fast_kernel(const __grid_constant__ CUt
                     FY[s2][1] = f[4];
                 }
             }
-            __syncthreads();
         }
     }
     if (s_abort) {
@@ -249,12 +256,12 @@ __global__ void __launch_bounds__(NT, 4) fast_kernel(const __grid_constant__ CUt
 
 template <int NT>
 constexpr int fast_smem() {
-    return TMA_SLOTS * NPLANES * NT * 4 + RING * 5 * NT * 8 + 2 * (2 * NT * 8) + TMA_SLOTS * 8;
+    return TMA_SLOTS * NPLANES * NT * 4 + RING * 5 * NT * 8 + 4 * (2 * NT * 8) + TMA_SLOTS * 8;
 }
 
-template <int NT, int MK>
+template <int NT, int MK, bool FORCED>
 cudaError_t fast_launch_t(const CUtensorMap *tmap, const StepArgs &args, const StepPlan &plan, cudaStream_t stream) {
-    auto k = fast_kernel<NT, MK>;
+    auto k = fast_kernel<NT, MK, FORCED>;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem<NT>());
@@ -267,14 +274,23 @@ cudaError_t fast_launch_t(const CUtensorMap *tmap, const StepArgs &args, const S
 
 template <int NT, int MK>
 cudaError_t fast_occupancy_t(int *occ, int *smem) {
-    auto k = fast_kernel<NT, MK>;
+    // both force variants have the same shared memory; take the larger register count
+    int o1 = 0, o2 = 0;
     *smem = fast_smem<NT>();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, NT, *smem);
+    cudaError_t e = cudaFuncSetAttribute(fast_kernel<NT, MK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fast_kernel<NT, MK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, fast_kernel<NT, MK, false>, NT, *smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, fast_kernel<NT, MK, true>, NT, *smem);
+    *occ = o1 < o2 ? o1 : o2;
+    return e;
 }
 
-constexpr int kFastNT = 128;
+template <int NT, int MK>
+cudaError_t fast_launch_f(const CUtensorMap *tmap, const StepArgs &args, const StepPlan &plan, cudaStream_t stream) {
+    return args.force_mode ? fast_launch_t<NT, MK, true>(tmap, args, plan, stream)
+                           : fast_launch_t<NT, MK, false>(tmap, args, plan, stream);
+}
 
 }  // namespace
 
@@ -282,16 +298,21 @@ bool fast_path_applies(int metric, int power_law, int walls) {
     return !walls && !power_law && (metric == METRIC_UNIFORM || metric == METRIC_SEPARABLE);
 }
 
-cudaError_t fast_occupancy(int metric, int *nt, int *occ, int *smem) {
-    *nt = kFastNT;
-    return metric == METRIC_UNIFORM ? fast_occupancy_t<kFastNT, METRIC_UNIFORM>(occ, smem)
-                                    : fast_occupancy_t<kFastNT, METRIC_SEPARABLE>(occ, smem);
+cudaError_t fast_occupancy(int metric, int nt, int *occ, int *smem) {
+    if (nt == 256)
+        return metric == METRIC_UNIFORM ? fast_occupancy_t<256, METRIC_UNIFORM>(occ, smem)
+                                        : fast_occupancy_t<256, METRIC_SEPARABLE>(occ, smem);
+    return metric == METRIC_UNIFORM ? fast_occupancy_t<128, METRIC_UNIFORM>(occ, smem)
+                                    : fast_occupancy_t<128, METRIC_SEPARABLE>(occ, smem);
 }
 
 cudaError_t fast_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
                         cudaStream_t stream) {
-    return metric == METRIC_UNIFORM ? fast_launch_t<kFastNT, METRIC_UNIFORM>(tmap, args, plan, stream)
-                                    : fast_launch_t<kFastNT, METRIC_SEPARABLE>(tmap, args, plan, stream);
+    if (plan.NT == 256)
+        return metric == METRIC_UNIFORM ? fast_launch_f<256, METRIC_UNIFORM>(tmap, args, plan, stream)
+                                        : fast_launch_f<256, METRIC_SEPARABLE>(tmap, args, plan, stream);
+    return metric == METRIC_UNIFORM ? fast_launch_f<128, METRIC_UNIFORM>(tmap, args, plan, stream)
+                                    : fast_launch_f<128, METRIC_SEPARABLE>(tmap, args, plan, stream);
 }
 
 }  // namespace mdf

@@ -77,6 +77,7 @@ _SIGNATURES = [
     ("mdf_steps_done", ctypes.c_longlong, [ctypes.c_void_p]),
     ("mdf_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("mdf_launch_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    ("mdf_set_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     ("mdf_bytes_per_node", ctypes.c_double, [ctypes.c_void_p]),
     ("mdf_residual_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
@@ -280,6 +281,9 @@ class Solver:
         keys = ["threads", "cols_per_block", "rows_per_block", "grid_x", "grid_y", "smem_bytes",
                 "blocks_per_sm", "pitch"]
         return dict(zip(keys, list(info)))
+
+    def set_launch(self, threads, rows_per_block):
+        _check(lib().mdf_set_launch(self._h, int(threads), int(rows_per_block)), self._h)
 
     def bytes_per_node(self):
         return lib().mdf_bytes_per_node(self._h)

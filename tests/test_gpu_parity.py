@@ -87,6 +87,18 @@ def test_set_state_roundtrip_and_single_step():
     assert maxabs(g.state().astype(np.float64), o.state()) <= 2e-8
 
 
+@pytest.mark.parametrize("threads,rows", [(128, 8), (128, 37), (256, 8), (256, 64)])
+def test_launch_plans_agree_with_oracle(threads, rows):
+    """Every block size / band height the autotuner may pick (periodic fast
+    path): ragged strips and bands against the oracle."""
+    nx, ny = 300, 150
+    u, v, p = W.random_fields(nx, ny, 0.05, seed=17)
+    g, o = pair(nx, ny, nu=0.004, lx=1.0, ly=0.6)
+    g.set_launch(threads, rows)
+    sg, so = run_both(g, o, (u, v, p), 20)
+    assert maxabs(sg, so) <= 2e-6 * 0.05
+
+
 # ---------------------------------------------------------- walls and forces
 
 
