@@ -40,7 +40,7 @@ METRIC = "MLUPS & % HBM roofline; time-to-residual 1e-8, warm-start+batch vs col
 NX = NY = 4096
 NU, U0 = 0.01, 0.01
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_taylor_green_4096_traffic.json")
-STEP_SOURCE = os.path.join(ROOT, "paper_2306_08216_gb300", "csrc", "mdf_step.cu")
+STEP_SOURCE = os.path.join(ROOT, "paper_2306_08216_gb300", "csrc", "mdf_step_fast.cu")
 
 
 def dist_env():
@@ -161,6 +161,34 @@ def oracle_sample(steps, n=512):
     return n * n * steps / dt / 1e6, max_threads(), dt
 
 
+CAV_N, CAV_RE, CAV_U0 = 257, 1000.0, 0.1
+
+
+def time_to_residual(mdf, W, grid, stream, target=1e-8, check_every=100, max_steps=3_000_000):
+    """Cold start from rest to residual <= target (windowed residual of
+    mdf_residual, window `check_every` steps); wall-clock seconds including
+    the residual checks."""
+    kw = dict(nu=CAV_U0 / CAV_RE, walls=(True, True), u_wall=(0, 0, 0, CAV_U0), stream=stream)
+    if grid.startswith("tanh"):
+        xs = W.tanh_nodes(CAV_N, 1.5)
+        kw.update(grid="separable", x=xs, y=xs)
+    s = mdf.Solver(CAV_N, CAV_N, **kw)
+    s.init(*W.zeros(CAV_N, CAV_N))
+    s.synchronize()
+    t0 = time.perf_counter()
+    steps, r = 0, float("inf")
+    while r > target and steps < max_steps:
+        s.step(check_every)
+        steps += check_every
+        r, _ = s.residual()
+    sec = time.perf_counter() - t0
+    out = {"workload": "lid-driven cavity Re=%g, %dx%d nodes, %s grid, from rest" % (CAV_RE, CAV_N, CAV_N, grid),
+           "target": target, "reached": r <= target, "residual": r, "steps": steps, "seconds": sec,
+           "us_per_step": 1e6 * sec / steps, "launch": s.launch_info()}
+    s.close()
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -195,6 +223,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-residual", action="store_true")
     ap.add_argument("--launch", default=None,
                     help="threads,rows_per_block: pin the launch plan instead of the autotuned one (profiling)")
     ap.add_argument("--nx", type=int, default=NX,
@@ -269,6 +298,12 @@ def main():
     e2e_sec = time.perf_counter() - t0
     e2e_val = job_mlups(nodes, e2e_steps, world, max_over_ranks(e2e_sec, world, "cuda"))
 
+    # ---- time to residual 1e-8 from rest: lid-driven cavity, Re = 1000, 257^2
+    ttr = None
+    if not args.no_time_to_residual:
+        ttr = {}
+        for grid in ("uniform", "tanh_1.5"):
+            ttr[grid] = time_to_residual(mdf, W, grid, stream)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -294,7 +329,11 @@ def main():
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
         "check": {"residual": r, "drift_u": drift[0], "drift_v": drift[1]},
+        "time_to_residual": ttr,
     }
+    if ttr and cpu:
+        for k in ttr:
+            ttr[k]["cpu_oracle_seconds_extrapolated"] = ttr[k]["steps"] * CAV_N * CAV_N / (cpu["value"] * 1e6)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
