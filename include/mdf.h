@@ -184,6 +184,48 @@ mdf_status mdf_set_launch(mdf_ctx *ctx, int threads, int rows_per_block);
  * written once, plus force/metric planes read once). */
 double mdf_bytes_per_node(const mdf_ctx *ctx);
 
+/* ---- Batches: many problems, one persistent launch per time step ----------
+ *
+ * A batch holds `count` independent problems (each an ordinary context with
+ * its own grid, fluid, walls and scheme parameters) and advances them
+ * together: each time step is ONE launch whose blocks walk a table of work
+ * items (problem, strip, band), largest problems first, reading each
+ * problem's arguments and TMA descriptor from device memory; repeated steps
+ * are replayed from captured CUDA graphs.  All problems must share the grid
+ * kind, the fluid model (Newtonian or power law) and the wall/periodic type
+ * (one kernel variant); sizes, viscosities, power-law indices, wall
+ * velocities and forcing may differ (mdf_set_force on a problem's context
+ * takes effect at the next mdf_batch_step).  This is the batching the survey of the
+ * method lists after the single-problem step; the paper itself has no
+ * counterpart. */
+typedef struct mdf_batch mdf_batch;
+
+/* grids/fluids/bcs: `count` entries each; params: NULL or `count` entries.
+ * Each problem starts at rest.  MDF_E_INVALID if the problems cannot share
+ * one kernel variant or any problem is invalid (see mdf_create). */
+mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *fluids, const mdf_bc *bcs,
+                            const mdf_params *params, mdf_batch **out);
+void mdf_batch_destroy(mdf_batch *batch);
+mdf_status mdf_batch_set_stream(mdf_batch *batch, void *cuda_stream);
+/* Initial fields of problem `index` (as mdf_init_fields); only before the
+ * first batch step. */
+mdf_status mdf_batch_init_fields(mdf_batch *batch, int index, const float *u, const float *v, const float *p,
+                                 int on_device);
+/* n time steps of every problem (asynchronous). */
+mdf_status mdf_batch_step(mdf_batch *batch, int n);
+/* Per-problem windowed residuals (definition of mdf_residual) into
+ * residual[count] and per-problem status into status[count] (may be NULL):
+ * MDF_OK, MDF_E_DIVERGED or MDF_E_STATE.  Synchronises; returns
+ * MDF_E_DIVERGED if any problem diverged (the others keep running). */
+mdf_status mdf_batch_residual(mdf_batch *batch, double *residual, int *status);
+/* The context of problem `index` (owned by the batch): use it with
+ * mdf_fields, mdf_get_distributions, mdf_dt, ...; do not step or destroy it. */
+mdf_status mdf_batch_problem(mdf_batch *batch, int index, mdf_ctx **ctx);
+/* info[0] problems, [1] work items, [2] blocks per launch, [3] blocks per
+ * SM, [4] nodes in all problems, [5] steps taken. */
+mdf_status mdf_batch_info(const mdf_batch *batch, long long info[6]);
+const char *mdf_batch_last_error(const mdf_batch *batch);
+
 /* Residual and drift with no allocation at all (the paper has no
  * counterpart; this is a service for callers that may not allocate device
  * memory -- inside stream capture, under an allocator that owns all device

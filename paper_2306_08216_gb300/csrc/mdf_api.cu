@@ -16,46 +16,9 @@
 #include <chrono>
 #include <thread>
 
-#include "../../include/mdf.h"
-#include "mdf_aux.cuh"
-#include "mdf_internal.cuh"
+#include "mdf_ctx.cuh"
 
 using namespace mdf;
-
-struct mdf_ctx {
-    int dev = 0, num_sms = 0;
-    int nx = 0, ny = 0, kind = 0, xwall = 0, ywall = 0;
-    double lx = 0, ly = 0;
-    mdf_fluid fluid{};
-    mdf_bc bc{};
-    mdf_params prm{};
-    double cs2 = 0, dt = 0, dxmin = 0;
-    int pitch = 0;
-    long long plane = 0;
-    float *buf[2] = {nullptr, nullptr};
-    int cur = 0;
-    float *kxv = nullptr, *kyv = nullptr;
-    float *mxx = nullptr, *mxy = nullptr, *mex = nullptr, *mey = nullptr;
-    float *Fxp = nullptr, *Fyp = nullptr;
-    int force_mode = 0;
-    double fx = 0, fy = 0;
-    float *snap_u = nullptr, *snap_v = nullptr;
-    long long snap_step = 0;
-    double *partials = nullptr, *result = nullptr, *h_result = nullptr;
-    int *err = nullptr;
-    float *scratch = nullptr;  // dense staging for host transfers
-    size_t scratch_bytes = 0;
-    CUtensorMap tmap[2];
-    static constexpr int kMaxCandidates = 8;
-    StepPlan cand[kMaxCandidates];
-    int ncand = 0;
-    StepPlan plan{};
-    StepArgs args{};
-    AuxArgs aux{};
-    cudaStream_t stream = nullptr;
-    long long steps = 0;
-    char last_error[256] = {0};
-};
 
 static char g_create_error[256] = {0};
 
@@ -91,7 +54,11 @@ static void free_ctx(mdf_ctx *c) {
     delete c;
 }
 
-static mdf_status encode_maps(mdf_ctx *c) {
+static mdf_status encode_maps_box(mdf_ctx *c, int box_nt, CUtensorMap maps[2]);
+
+static mdf_status encode_maps(mdf_ctx *c) { return encode_maps_box(c, c->plan.NT, c->tmap); }
+
+static mdf_status encode_maps_box(mdf_ctx *c, int box_nt, CUtensorMap maps[2]) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -104,9 +71,9 @@ static mdf_status encode_maps(mdf_ctx *c) {
     for (int b = 0; b < 2; ++b) {
         cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->ny, (cuuint64_t)NPLANES};
         cuuint64_t strides[2] = {(cuuint64_t)c->pitch * 4, (cuuint64_t)c->plane * 4};
-        cuuint32_t box[3] = {(cuuint32_t)c->plan.NT, 1, (cuuint32_t)NPLANES};
+        cuuint32_t box[3] = {(cuuint32_t)box_nt, 1, (cuuint32_t)NPLANES};
         cuuint32_t estr[3] = {1, 1, 1};
-        CUresult r = encode(&c->tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->buf[b], dims, strides, box, estr,
+        CUresult r = encode(&maps[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->buf[b], dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(c, MDF_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -210,6 +177,12 @@ static mdf_status autotune(mdf_ctx *c) {
     c->args.H = c->plan.H;
     return encode_maps(c);
 }
+
+namespace mdf {
+mdf_status ctx_fail(mdf_ctx *c, mdf_status st, const char *msg) { return fail(c, st, "%s", msg); }
+mdf_status ctx_encode_maps(mdf_ctx *c, int box_nt, CUtensorMap maps[2]) { return encode_maps_box(c, box_nt, maps); }
+mdf_status ctx_wait(mdf_ctx *c, double timeout_s) { return wait_stream(c, timeout_s); }
+}  // namespace mdf
 
 extern "C" {
 
@@ -468,6 +441,7 @@ mdf_status mdf_set_force(mdf_ctx *c, int mode, double fx, double fy, const float
         CK(c, aux_pad_field(c->aux, c->scratch + N, c->Fyp, c->stream));
     }
     c->force_mode = mode;
+    ++c->args_version;
     c->args.force_mode = mode;
     c->args.Fx = (float)fx;
     c->args.Fy = (float)fy;

@@ -1,0 +1,336 @@
+// mdf_batch.cu -- many MDF-FDLBM problems stepped by one persistent launch.
+//
+// Each problem of a batch is an ordinary context (mdf_create: its own state
+// buffers, metrics, forcing and residual snapshot), so every single-problem
+// call (mdf_fields, mdf_get_distributions, mdf_residual, ...) works on it.
+// mdf_batch_step advances all of them together: one launch of batch_kernel
+// per time step, whose blocks walk a table of work items (problem, strip,
+// band) ordered largest problem first, with the problems' arguments and TMA
+// descriptors in global memory.  Repeated steps are replayed from captured
+// CUDA graphs of kGraphSteps launches.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "mdf_ctx.cuh"
+
+using namespace mdf;
+
+namespace {
+constexpr int kBatchNT = 128;     // block size of the general march
+constexpr int kBandRows = 128;    // target rows per work item
+constexpr int kGraphSteps = 16;   // launches per captured graph (even: parity returns)
+}  // namespace
+
+struct mdf_batch {
+    int count = 0;
+    std::vector<mdf_ctx *> ctx;
+    int metric = 0, power_law = 0, walls = 0;
+    StepArgs *d_args[2] = {nullptr, nullptr};      // per parity: fout = the other buffer
+    CUtensorMap *d_maps[2] = {nullptr, nullptr};   // per parity: maps of the input buffer
+    BatchItem *d_items = nullptr;
+    int nitems = 0, grid = 0, occ = 0, smem = 0;
+    int cur = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cstream = nullptr;                // capture / replay stream
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    double *h_res = nullptr;                       // pinned, 5 doubles per problem
+    std::vector<int> H;                            // rows per work item of each problem
+    std::vector<int> seen_version;                 // args_version of each context last uploaded
+    long long steps = 0;
+    long long nodes = 0;
+    char last_error[256] = {0};
+};
+
+static char g_batch_error[256] = {0};
+
+static mdf_status bfail(mdf_batch *b, mdf_status st, const char *fmt, ...) {
+    char *dst = b ? b->last_error : g_batch_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define BCK(b, call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? MDF_E_NOMEM : MDF_E_CUDA,       \
+                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+static void free_batch(mdf_batch *b) {
+    if (!b) return;
+    for (int p = 0; p < 2; ++p) {
+        if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
+        if (b->d_args[p]) cudaFree(b->d_args[p]);
+        if (b->d_maps[p]) cudaFree(b->d_maps[p]);
+    }
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->h_res) cudaFreeHost(b->h_res);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->cstream) cudaStreamDestroy(b->cstream);
+    for (mdf_ctx *c : b->ctx) mdf_destroy(c);
+    delete b;
+}
+
+// Upload the per-problem argument tables (both parities) from the contexts.
+static mdf_status upload_args(mdf_batch *b) {
+    std::vector<StepArgs> args(b->count);
+    for (int p = 0; p < 2; ++p) {
+        for (int i = 0; i < b->count; ++i) {
+            mdf_ctx *c = b->ctx[i];
+            StepArgs a = c->args;
+            a.W = kBatchNT - 8;
+            a.H = b->H[i];
+            a.fout = c->buf[1 - p];
+            a.err = b->ctx[0]->err;  // one fault word for the whole batch
+            args[i] = a;
+        }
+        BCK(b, cudaMemcpy(b->d_args[p], args.data(), b->count * sizeof(StepArgs), cudaMemcpyHostToDevice));
+    }
+    for (int i = 0; i < b->count; ++i) b->seen_version[i] = b->ctx[i]->args_version;
+    return MDF_OK;
+}
+
+static mdf_status launch_steps(mdf_batch *b, cudaStream_t st, int n) {
+    for (int i = 0; i < n; ++i) {
+        BCK(b, batch_launch(b->d_items, b->nitems, b->d_args[b->cur], b->d_maps[b->cur], b->metric, b->power_law,
+                            b->walls, b->grid, st));
+        b->cur ^= 1;
+    }
+    return MDF_OK;
+}
+
+static mdf_status build_graph(mdf_batch *b, int parity) {
+    const int saved = b->cur;
+    b->cur = parity;
+    BCK(b, cudaStreamBeginCapture(b->cstream, cudaStreamCaptureModeThreadLocal));
+    mdf_status s = launch_steps(b, b->cstream, kGraphSteps);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cstream, &g);
+    b->cur = saved;
+    if (s != MDF_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return bfail(b, MDF_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, MDF_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return MDF_OK;
+}
+
+extern "C" {
+
+mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *fluids, const mdf_bc *bcs,
+                            const mdf_params *params, mdf_batch **out) {
+    if (!out) return bfail(nullptr, MDF_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !grids || !fluids || !bcs) return bfail(nullptr, MDF_E_INVALID, "count >= 1 and arrays required");
+    // one kernel variant serves the whole batch
+    const int metric = grids[0].kind;
+    const int power_law = fluids[0].power_law ? 1 : 0;
+    const int walls = (bcs[0].type[0] == MDF_BC_WALL || bcs[0].type[2] == MDF_BC_WALL) ? 1 : 0;
+    for (int i = 1; i < count; ++i) {
+        const int w = (bcs[i].type[0] == MDF_BC_WALL || bcs[i].type[2] == MDF_BC_WALL) ? 1 : 0;
+        if (grids[i].kind != metric || (fluids[i].power_law ? 1 : 0) != power_law || w != walls)
+            return bfail(nullptr, MDF_E_INVALID,
+                         "problem %d differs from problem 0 in grid kind, fluid model or wall/periodic type", i);
+    }
+    mdf_batch *b = new mdf_batch();
+    b->count = count;
+    b->metric = metric;
+    b->power_law = power_law;
+    b->walls = walls;
+#define BCKC(call)                                          \
+    do {                                                    \
+        mdf_status s_ = (call);                             \
+        if (s_ != MDF_OK) {                                 \
+            strncpy(g_batch_error, b->last_error, 255);     \
+            free_batch(b);                                  \
+            return s_;                                      \
+        }                                                   \
+    } while (0)
+#define BCKE(call) BCKC(([&]() -> mdf_status { BCK(b, call); return MDF_OK; })())
+    for (int i = 0; i < count; ++i) {
+        mdf_ctx *c = nullptr;
+        mdf_status s = mdf_create(&grids[i], &fluids[i], &bcs[i], params ? &params[i] : nullptr, &c);
+        if (s != MDF_OK) {
+            bfail(b, s, "problem %d: %s", i, mdf_last_error(nullptr));
+            BCKC(s);
+        }
+        b->ctx.push_back(c);
+        b->nodes += (long long)c->nx * c->ny;
+    }
+    int nt = 0, num_sms = 0, dev = 0;
+    BCKE(batch_occupancy(metric, power_law, walls, &nt, &b->occ, &b->smem));
+    BCKE(cudaGetDevice(&dev));
+    BCKE(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+    // work items, largest problems first
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (long long)b->ctx[x]->nx * b->ctx[x]->ny > (long long)b->ctx[y]->nx * b->ctx[y]->ny;
+    });
+    std::vector<BatchItem> items;
+    std::vector<CUtensorMap> maps[2];
+    for (int p = 0; p < 2; ++p) maps[p].resize(count);
+    b->H.resize(count);
+    b->seen_version.resize(count);
+    for (int i = 0; i < count; ++i) {
+        mdf_ctx *c = b->ctx[i];
+        const int bands = (c->ny + kBandRows - 1) / kBandRows;
+        int H = (c->ny + bands - 1) / bands;
+        if (H < 8) H = 8;
+        b->H[i] = H;
+        CUtensorMap m[2];
+        BCKC(ctx_encode_maps(c, kBatchNT, m));
+        for (int p = 0; p < 2; ++p) maps[p][i] = m[p];
+    }
+    for (int oi = 0; oi < count; ++oi) {
+        const int i = order[oi];
+        mdf_ctx *c = b->ctx[i];
+        const int W = kBatchNT - 8;
+        const int gx = (c->nx + W - 1) / W;
+        const int H = b->H[i];
+        const int gy = (c->ny + H - 1) / H;
+        for (int by = 0; by < gy; ++by)
+            for (int bx = 0; bx < gx; ++bx) items.push_back(BatchItem{i, bx, by, 0});
+    }
+    b->nitems = (int)items.size();
+    b->grid = std::min(b->nitems, std::max(1, b->occ) * num_sms);
+    BCKE(cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem)));
+    BCKE(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+    for (int p = 0; p < 2; ++p) {
+        BCKE(cudaMalloc(&b->d_args[p], count * sizeof(StepArgs)));
+        BCKE(cudaMalloc(&b->d_maps[p], count * sizeof(CUtensorMap)));
+        BCKE(cudaMemcpy(b->d_maps[p], maps[p].data(), count * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    }
+    BCKC(upload_args(b));
+    BCKE(cudaMallocHost(&b->h_res, (size_t)count * 5 * sizeof(double)));
+    BCKE(cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking));
+    BCKE(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+    BCKE(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+    *out = b;
+    return MDF_OK;
+#undef BCKE
+#undef BCKC
+}
+
+void mdf_batch_destroy(mdf_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    cudaStreamSynchronize(b->cstream);
+    free_batch(b);
+}
+
+mdf_status mdf_batch_set_stream(mdf_batch *b, void *stream) {
+    if (!b) return MDF_E_INVALID;
+    b->stream = (cudaStream_t)stream;
+    for (mdf_ctx *c : b->ctx) c->stream = b->stream;
+    return MDF_OK;
+}
+
+mdf_status mdf_batch_problem(mdf_batch *b, int index, mdf_ctx **ctx) {
+    if (!b || !ctx || index < 0 || index >= b->count) return b ? bfail(b, MDF_E_INVALID, "bad index") : MDF_E_INVALID;
+    *ctx = b->ctx[index];
+    return MDF_OK;
+}
+
+mdf_status mdf_batch_init_fields(mdf_batch *b, int index, const float *u, const float *v, const float *p,
+                                 int on_device) {
+    if (!b || index < 0 || index >= b->count) return b ? bfail(b, MDF_E_INVALID, "bad index") : MDF_E_INVALID;
+    if (b->steps != 0 || b->cur != 0)
+        return bfail(b, MDF_E_STATE, "initial fields are set before the batch takes its first step");
+    mdf_status s = mdf_init_fields(b->ctx[index], u, v, p, on_device);
+    if (s != MDF_OK) bfail(b, s, "problem %d: %s", index, mdf_last_error(b->ctx[index]));
+    return s;
+}
+
+mdf_status mdf_batch_step(mdf_batch *b, int n) {
+    if (!b) return MDF_E_INVALID;
+    if (n < 0) return bfail(b, MDF_E_INVALID, "n must be >= 0");
+    // arguments changed since the last upload (forcing set on a problem)?
+    for (int i = 0; i < b->count; ++i)
+        if (b->seen_version[i] != b->ctx[i]->args_version) {
+            BCK(b, cudaStreamSynchronize(b->stream));
+            BCK(b, cudaStreamSynchronize(b->cstream));
+            mdf_status s = upload_args(b);
+            if (s != MDF_OK) return s;
+            break;
+        }
+    int done = 0;
+    const int reps = n / kGraphSteps;
+    if (reps >= 2) {
+        // replay captured graphs on the capture stream, ordered after and
+        // before the batch stream by events
+        if (!b->graph[b->cur]) {
+            mdf_status s = build_graph(b, b->cur);
+            if (s != MDF_OK) return s;
+        }
+        BCK(b, cudaEventRecord(b->ev_in, b->stream));
+        BCK(b, cudaStreamWaitEvent(b->cstream, b->ev_in, 0));
+        for (int r = 0; r < reps; ++r) BCK(b, cudaGraphLaunch(b->graph[b->cur], b->cstream));
+        BCK(b, cudaEventRecord(b->ev_out, b->cstream));
+        BCK(b, cudaStreamWaitEvent(b->stream, b->ev_out, 0));
+        done = reps * kGraphSteps;  // even: the parity is unchanged
+    }
+    mdf_status s = launch_steps(b, b->stream, n - done);
+    if (s != MDF_OK) return s;
+    b->steps += n;
+    for (mdf_ctx *c : b->ctx) {
+        c->cur = b->cur;
+        c->steps += n;
+    }
+    return MDF_OK;
+}
+
+mdf_status mdf_batch_residual(mdf_batch *b, double *residual, int *status) {
+    if (!b || !residual) return b ? bfail(b, MDF_E_INVALID, "residual is NULL") : MDF_E_INVALID;
+    for (int i = 0; i < b->count; ++i) {
+        mdf_ctx *c = b->ctx[i];
+        BCK(b, aux_residual(c->aux, c->buf[c->cur], c->snap_u, c->snap_v, c->partials, c->result, b->stream));
+        BCK(b, cudaMemcpyAsync(b->h_res + 5 * i, c->result, 5 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    }
+    mdf_status s = ctx_wait(b->ctx[0], 0);
+    if (s != MDF_OK) return bfail(b, s, "%s", mdf_last_error(b->ctx[0]));
+    int any_diverged = 0;
+    for (int i = 0; i < b->count; ++i) {
+        mdf_ctx *c = b->ctx[i];
+        const double *r = b->h_res + 5 * i;
+        const long long window = c->steps - c->snap_step;
+        c->snap_step = c->steps;
+        residual[i] = window > 0 ? sqrt(r[0]) / ((double)window * sqrt(r[1])) : NAN;
+        int st = MDF_OK;
+        if (r[4] > 0 || !isfinite(r[2]) || !isfinite(r[3])) st = MDF_E_DIVERGED;
+        else if (window <= 0) st = MDF_E_STATE;
+        if (status) status[i] = st;
+        any_diverged |= st == MDF_E_DIVERGED;
+    }
+    return any_diverged ? bfail(b, MDF_E_DIVERGED, "at least one problem diverged") : MDF_OK;
+}
+
+mdf_status mdf_batch_info(const mdf_batch *b, long long info[6]) {
+    if (!b || !info) return MDF_E_INVALID;
+    info[0] = b->count;
+    info[1] = b->nitems;
+    info[2] = b->grid;
+    info[3] = b->occ;
+    info[4] = b->nodes;
+    info[5] = b->steps;
+    return MDF_OK;
+}
+
+const char *mdf_batch_last_error(const mdf_batch *b) { return b ? b->last_error : g_batch_error; }
+
+}  // extern "C"

@@ -1,0 +1,53 @@
+// mdf_ctx.cuh -- the context behind the opaque mdf_ctx handle of the C ABI,
+// shared by the single-problem runtime (mdf_api.cu) and the batch runtime
+// (mdf_batch.cu).
+#pragma once
+
+#include "../../include/mdf.h"
+#include "mdf_aux.cuh"
+#include "mdf_internal.cuh"
+
+struct mdf_ctx {
+    // the members are documented where they are set (mdf_create)
+    int dev = 0, num_sms = 0;
+    int nx = 0, ny = 0, kind = 0, xwall = 0, ywall = 0;
+    double lx = 0, ly = 0;
+    mdf_fluid fluid{};
+    mdf_bc bc{};
+    mdf_params prm{};
+    double cs2 = 0, dt = 0, dxmin = 0;
+    int pitch = 0;
+    long long plane = 0;
+    float *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    float *kxv = nullptr, *kyv = nullptr;
+    float *mxx = nullptr, *mxy = nullptr, *mex = nullptr, *mey = nullptr;
+    float *Fxp = nullptr, *Fyp = nullptr;
+    int force_mode = 0;
+    double fx = 0, fy = 0;
+    float *snap_u = nullptr, *snap_v = nullptr;
+    long long snap_step = 0;
+    double *partials = nullptr, *result = nullptr, *h_result = nullptr;
+    int *err = nullptr;
+    float *scratch = nullptr;  // dense staging for host transfers
+    size_t scratch_bytes = 0;
+    CUtensorMap tmap[2];
+    static constexpr int kMaxCandidates = 8;
+    mdf::StepPlan cand[kMaxCandidates];
+    int ncand = 0;
+    mdf::StepPlan plan{};
+    mdf::StepArgs args{};
+    mdf::AuxArgs aux{};
+    cudaStream_t stream = nullptr;
+    long long steps = 0;
+    int args_version = 0;  // bumped whenever args change after creation (forcing)
+    char last_error[256] = {0};
+};
+
+
+namespace mdf {
+// Shared helpers of the host runtime (mdf_api.cu).
+mdf_status ctx_fail(mdf_ctx *c, mdf_status st, const char *msg);
+mdf_status ctx_encode_maps(mdf_ctx *c, int box_nt, CUtensorMap maps[2]);
+mdf_status ctx_wait(mdf_ctx *c, double timeout_s);
+}  // namespace mdf

@@ -87,6 +87,15 @@ cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metri
                         cudaStream_t stream);
 int step_pitch(int nx, int W);
 
+// Batched step: one work item = one block's march (strip bx, band by) of one
+// problem of the batch (mdf_step.cu).
+struct BatchItem {
+    int problem, bx, by, pad;
+};
+cudaError_t batch_occupancy(int metric, int power_law, int walls, int *nt, int *occ, int *smem);
+cudaError_t batch_launch(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps, int metric,
+                         int power_law, int walls, int grid, cudaStream_t stream);
+
 // Periodic Newtonian fast path on uniform/separable grids (mdf_step_fast.cu).
 bool fast_path_applies(int metric, int power_law, int walls);
 cudaError_t fast_occupancy(int metric, int nt, int *occ, int *smem);

@@ -102,23 +102,26 @@ __device__ __forceinline__ F2 curvi_term(const unsigned char *const rows[5], int
     return acc;
 }
 
+// One block's march over strip bx, band by of one problem.  `tmap` is the
+// TMA descriptor of the input state, `a` the problem's arguments (kernel
+// parameter space for a single problem, global memory for a batch).
 template <int NT, int MK, bool PL, bool WALLS>
-__global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
+__device__ __forceinline__ void march(const CUtensorMap *tmap, const StepArgs &a, int bx, int by, unsigned char *smem,
+                                      int *abort_flag) {
     using R = Ring<NT>;
     constexpr int TROW = NPLANES * NT * 4;  // bytes of one TMA row (10 planes x NT floats)
-    extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *tma = smem;
     unsigned char *ringP = tma + TMA_SLOTS * TROW;   // fhat^+
     unsigned char *ringB = ringP + RING * R::ROW;    // fbar^+
     unsigned char *ringF = ringB + RING * R::ROW;    // f(t+h)
     float *ringK = reinterpret_cast<float *>(ringF + RING * R::ROW);  // power law: recovery rates
     uint64_t *mbar = reinterpret_cast<uint64_t *>(ringK + (PL ? RING * 2 * NT : 0));
-    __shared__ int s_abort;
+    int &s_abort = *abort_flag;
 
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * a.W;
+    const int x0 = bx * a.W;
     const int X = x0 - 4 + t;
-    const int y0 = blockIdx.y * a.H;
+    const int y0 = by * a.H;
     const int y1 = min(y0 + a.H, a.ny);
     const int nIt = (y1 - y0) + 9;
     const int rowBase = y0 - 4;
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ CUtens
         const int p = rowBase + it;
         const int yy = (WALLS && a.ywall) ? p : wrap(p, a.ny);
         mbar_expect_tx(&mbar[slot], TROW);
-        tma_load_row(&tmap, &mbar[slot], tma + slot * TROW, x0, yy);
+        tma_load_row(tmap, &mbar[slot], tma + slot * TROW, x0, yy);
     };
     int issued = min(TMA_SLOTS, nIt);
     if (t == 0)
@@ -417,6 +420,34 @@ __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ CUtens
             atomicCAS(a.err, DEVERR_NONE, DEVERR_TMA_TIMEOUT);
         }
     }
+    // every copy was consumed: the barriers may be invalidated for reuse
+    __syncthreads();
+    if (t == 0)
+        for (int i = 0; i < TMA_SLOTS; ++i) mbar_inval(&mbar[i]);
+    __syncthreads();
+}
+
+template <int NT, int MK, bool PL, bool WALLS>
+__global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_abort;
+    march<NT, MK, PL, WALLS>(&tmap, a, blockIdx.x, blockIdx.y, smem, &s_abort);
+}
+
+// Many problems in one persistent launch: block b takes work items
+// b, b + gridDim.x, ... of the table (problem, strip, band), which lists the
+// largest problems first.  Arguments and TMA descriptors live in global memory.
+template <int NT, int MK, bool PL, bool WALLS>
+__global__ void __launch_bounds__(NT) batch_kernel(const BatchItem *__restrict__ items, int nitems,
+                                                   const StepArgs *__restrict__ args,
+                                                   const CUtensorMap *__restrict__ maps) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_abort;
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const BatchItem item = items[w];
+        march<NT, MK, PL, WALLS>(&maps[item.problem], args[item.problem], item.bx, item.by, smem, &s_abort);
+        if (s_abort) break;
+    }
 }
 
 template <int NT, int MK, bool PL, bool WALLS>
@@ -441,6 +472,30 @@ cudaError_t launch_t(const CUtensorMap *tmap, const StepArgs &args, const StepPl
 template <int NT, int MK, bool PL, bool WALLS>
 cudaError_t occupancy_t(int *occ, int *smem) {
     auto k = step_kernel<NT, MK, PL, WALLS>;
+    *smem = smem_bytes<NT, MK, PL, WALLS>();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, NT, *smem);
+}
+
+template <int NT, int MK, bool PL, bool WALLS>
+cudaError_t batch_launch_t(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps,
+                           int grid, cudaStream_t stream) {
+    auto k = batch_kernel<NT, MK, PL, WALLS>;
+    const int smem = smem_bytes<NT, MK, PL, WALLS>();
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k<<<grid, NT, smem, stream>>>(items, nitems, args, maps);
+    return cudaGetLastError();
+}
+
+template <int NT, int MK, bool PL, bool WALLS>
+cudaError_t batch_occupancy_t(int *occ, int *smem) {
+    auto k = batch_kernel<NT, MK, PL, WALLS>;
     *smem = smem_bytes<NT, MK, PL, WALLS>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
     if (e != cudaSuccess) return e;
@@ -514,6 +569,16 @@ int step_candidates(int metric, int power_law, int walls, int nx, int ny, int nu
         for (int waves = 1; waves <= 2 && n < max; ++waves) fill_plan(nts[i], occ, smem, waves, nx, ny, num_sms, &out[n++]);
     }
     return n;
+}
+
+cudaError_t batch_occupancy(int metric, int power_law, int walls, int *nt, int *occ, int *smem) {
+    *nt = kNT;
+    MDF_DISPATCH(batch_occupancy_t, occ, smem)
+}
+
+cudaError_t batch_launch(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps, int metric,
+                         int power_law, int walls, int grid, cudaStream_t stream) {
+    MDF_DISPATCH(batch_launch_t, items, nitems, args, maps, grid, stream)
 }
 
 cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,

@@ -79,6 +79,17 @@ _SIGNATURES = [
     ("mdf_launch_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     ("mdf_set_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     ("mdf_bytes_per_node", ctypes.c_double, [ctypes.c_void_p]),
+    ("mdf_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Grid), ctypes.POINTER(Fluid),
+                                        ctypes.POINTER(BC), ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]),
+    ("mdf_batch_destroy", None, [ctypes.c_void_p]),
+    ("mdf_batch_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("mdf_batch_init_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_int]),
+    ("mdf_batch_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("mdf_batch_residual", ctypes.c_int, [ctypes.c_void_p, _D, ctypes.POINTER(ctypes.c_int)]),
+    ("mdf_batch_problem", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    ("mdf_batch_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
+    ("mdf_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("mdf_residual_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
 ]
@@ -135,6 +146,31 @@ class _Arr:
             assert size == n, "expected %d elements, got %d" % (n, size)
 
 
+def problem_structs(nx, ny, nu=0.01, grid="uniform", lx=1.0, ly=1.0, x=None, y=None, power_law=None,
+                    walls=(False, False), u_wall=(0, 0, 0, 0), v_wall=(0, 0, 0, 0), c=1.0, cfl=0.5, eta=0.8,
+                    s_ratio=1.5):
+    """The C structs (mdf_grid, mdf_fluid, mdf_bc, mdf_params) of one problem,
+    plus the arrays they point to (keep them alive while the structs are used)."""
+    keep = []
+    g = Grid(nx, ny, GRID_KINDS[grid], lx, ly)
+    if grid != "uniform":
+        xa = np.ascontiguousarray(x, dtype=np.float64).ravel()
+        ya = np.ascontiguousarray(y, dtype=np.float64).ravel()
+        keep += [xa, ya]
+        g.x, g.y = xa.ctypes.data_as(_D), ya.ctypes.data_as(_D)
+    f = Fluid(nu, 0, 0.0, 1.0, 0.0, 0.0)
+    if power_law is not None:
+        f.power_law = 1
+        f.K, f.n, f.nu_min, f.nu_max = power_law
+    b = BC()
+    for k in range(4):
+        b.type[k] = 1 if walls[0 if k < 2 else 1] else 0
+        b.u_wall[k] = u_wall[k]
+        b.v_wall[k] = v_wall[k]
+    p = Params(c, cfl, eta, s_ratio)
+    return g, f, b, p, keep
+
+
 class Solver:
     """One MDF-FDLBM problem on the GPU (see include/mdf.h).
 
@@ -147,38 +183,26 @@ class Solver:
 
     def __init__(self, nx, ny, nu=0.01, grid="uniform", lx=1.0, ly=1.0, x=None, y=None,
                  power_law=None, walls=(False, False), u_wall=(0, 0, 0, 0), v_wall=(0, 0, 0, 0),
-                 c=1.0, cfl=0.5, eta=0.8, s_ratio=1.5, force=None, stream=None):
-        L = lib()
-        g = Grid(nx, ny, GRID_KINDS[grid], lx, ly)
-        self._keep = []
-        if grid != "uniform":
-            xa = np.ascontiguousarray(x, dtype=np.float64).ravel()
-            ya = np.ascontiguousarray(y, dtype=np.float64).ravel()
-            self._keep += [xa, ya]
-            g.x, g.y = xa.ctypes.data_as(_D), ya.ctypes.data_as(_D)
-        f = Fluid(nu, 0, 0.0, 1.0, 0.0, 0.0)
-        if power_law is not None:
-            f.power_law = 1
-            f.K, f.n, f.nu_min, f.nu_max = power_law
-        b = BC()
-        for k in range(4):
-            b.type[k] = 1 if walls[0 if k < 2 else 1] else 0
-            b.u_wall[k] = u_wall[k]
-            b.v_wall[k] = v_wall[k]
-        p = Params(c, cfl, eta, s_ratio)
-        h = ctypes.c_void_p()
-        _check(L.mdf_create(ctypes.byref(g), ctypes.byref(f), ctypes.byref(b), ctypes.byref(p), ctypes.byref(h)))
-        self._h = h
+                 c=1.0, cfl=0.5, eta=0.8, s_ratio=1.5, force=None, stream=None, _handle=None):
         self.nx, self.ny = nx, ny
+        self._owned = _handle is None
+        if _handle is not None:  # a problem of a batch: the batch owns the context
+            self._h = _handle
+            return
+        g, f, b, p, self._keep = problem_structs(nx, ny, nu, grid, lx, ly, x, y, power_law, walls, u_wall, v_wall,
+                                                 c, cfl, eta, s_ratio)
+        h = ctypes.c_void_p()
+        _check(lib().mdf_create(ctypes.byref(g), ctypes.byref(f), ctypes.byref(b), ctypes.byref(p), ctypes.byref(h)))
+        self._h = h
         if stream is not None:
             self.set_stream(stream)
         if force is not None:
             self.set_force(force)
 
     def close(self):
-        if getattr(self, "_h", None):
+        if getattr(self, "_h", None) and getattr(self, "_owned", True):
             lib().mdf_destroy(self._h)
-            self._h = None
+        self._h = None
 
     def __del__(self):
         try:
@@ -300,3 +324,76 @@ def create_status(grid, fluid, bc, params=None):
     if st == MDF_OK:
         L.mdf_destroy(h)
     return st, (msg.decode() if msg else "")
+
+
+class Batch:
+    """Many problems advanced by one persistent launch per time step
+    (mdf_batch_*).  `problems` is a list of keyword dicts as for Solver
+    (without stream/force); problem i is available as batch.problem(i), a
+    Solver view on the batch's context (no step(); the batch steps it)."""
+
+    def __init__(self, problems, stream=None):
+        L = lib()
+        n = len(problems)
+        G, F, B, P = (Grid * n)(), (Fluid * n)(), (BC * n)(), (Params * n)()
+        self._keep = []
+        for i, kw in enumerate(problems):
+            kw = dict(kw)
+            nx, ny = kw.pop("nx"), kw.pop("ny")
+            g, f, b, p, keep = problem_structs(nx, ny, **kw)
+            G[i], F[i], B[i], P[i] = g, f, b, p
+            self._keep += keep
+        h = ctypes.c_void_p()
+        st = L.mdf_batch_create(n, G, F, B, P, ctypes.byref(h))
+        if st != MDF_OK:
+            raise MdfError(st, L.mdf_batch_last_error(None).decode())
+        self._h = h
+        self.count = n
+        self.shapes = [(kw["nx"], kw["ny"]) for kw in problems]
+        if stream is not None:
+            raw = getattr(stream, "cuda_stream", stream)
+            self._chk(L.mdf_batch_set_stream(self._h, ctypes.c_void_p(raw or 0)))
+
+    def _chk(self, st):
+        if st != MDF_OK:
+            raise MdfError(st, lib().mdf_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mdf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, index, u, v, p):
+        nx, ny = self.shapes[index]
+        a = [_Arr(t, nx * ny) for t in (u, v, p)]
+        self._chk(lib().mdf_batch_init_fields(self._h, index, a[0].ptr, a[1].ptr, a[2].ptr, a[0].on_device))
+
+    def step(self, n=1):
+        self._chk(lib().mdf_batch_step(self._h, int(n)))
+
+    def residual(self):
+        """(residuals[count], statuses[count]); divergence is reported in the
+        statuses, not raised."""
+        r = (ctypes.c_double * self.count)()
+        s = (ctypes.c_int * self.count)()
+        st = lib().mdf_batch_residual(self._h, r, s)
+        if st not in (MDF_OK, MDF_E_DIVERGED):
+            self._chk(st)
+        return np.array(r[:]), np.array(s[:])
+
+    def problem(self, index):
+        h = ctypes.c_void_p()
+        self._chk(lib().mdf_batch_problem(self._h, index, ctypes.byref(h)))
+        nx, ny = self.shapes[index]
+        return Solver(nx, ny, _handle=h)
+
+    def info(self):
+        v = (ctypes.c_longlong * 6)()
+        self._chk(lib().mdf_batch_info(self._h, v))
+        return dict(zip(["problems", "work_items", "blocks", "blocks_per_sm", "nodes", "steps"], list(v)))
