@@ -189,6 +189,72 @@ def time_to_residual(mdf, W, grid, stream, target=1e-8, check_every=100, max_ste
     return out
 
 
+BATCH_COUNT, BATCH_SEED = 512, 2306
+
+
+def batch_problems(count=BATCH_COUNT, seed=BATCH_SEED, u0=0.1):
+    """Seeded sweep of power-law lid-driven cavities: Re log-uniform in
+    [100, 5000], n uniform in [0.5, 1.5], side in {65, 129, 257, 513};
+    K = u0^(2-n) L^n / Re with L = 1, nu clamped to [nu_ref/20, 20 nu_ref],
+    nu_ref = K (u0/L)^(n-1)."""
+    from paper_2306_08216_gb300 import workloads as W
+    re, nn, sides = W.cavity_batch_draws(count, seed)
+    probs = []
+    for Re, n, side in zip(re, nn, sides):
+        K = u0 ** (2 - n) / Re
+        nu_ref = K * u0 ** (n - 1)
+        probs.append(dict(nx=int(side), ny=int(side), nu=nu_ref, walls=(True, True), u_wall=(0, 0, 0, u0),
+                          power_law=(K, float(n), nu_ref / 20, nu_ref * 20)))
+    return probs
+
+
+def batch_benchmark(mdf, torch, stream, steps=200, solo_sample=16):
+    """Throughput of the batched step over the seeded 512-cavity sweep, against
+    the same cavities stepped one problem per launch (timed on a sample of
+    `solo_sample` cavities and scaled by node count)."""
+    probs = batch_problems()
+    t0 = time.perf_counter()
+    batch = mdf.Batch(probs, stream=stream)
+    create_s = time.perf_counter() - t0
+    batch.step(2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    info = batch.info()
+    r, status = batch.residual()
+    nodes = info["nodes"]
+    batch_mlups = nodes * steps / (ms / 1e3) / 1e6
+    batch.close()
+    # one-problem-per-launch reference on a sample, largest and smallest mixed
+    idx = list(range(0, len(probs), max(1, len(probs) // solo_sample)))[:solo_sample]
+    solo_nodes, solo_ms = 0, 0.0
+    for i in idx:
+        kw = dict(probs[i])
+        nx, ny = kw.pop("nx"), kw.pop("ny")
+        sv = mdf.Solver(nx, ny, stream=stream, **kw)
+        sv.step(2)
+        sv.synchronize()
+        e0.record(stream)
+        sv.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        solo_ms += e0.elapsed_time(e1)
+        solo_nodes += nx * ny
+        sv.close()
+    solo_mlups = solo_nodes * steps / (solo_ms / 1e3) / 1e6
+    return {"workload": "%d power-law cavities, sides {65,129,257,513}, Re log-uniform [100,5000], "
+                        "n uniform [0.5,1.5], seed %d" % (BATCH_COUNT, BATCH_SEED),
+            "steps": steps, "nodes": nodes, "ms_per_step": ms / steps, "value": batch_mlups, "unit": "MLUPS",
+            "launches_per_step": 1, "work_items": info["work_items"], "blocks": info["blocks"],
+            "diverged": int((status == mdf.MDF_E_DIVERGED).sum()), "create_seconds": create_s,
+            "one_launch_per_problem_mlups": solo_mlups, "solo_sample": len(idx),
+            "speedup_vs_one_launch_per_problem": batch_mlups / solo_mlups}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -224,6 +290,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-residual", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--launch", default=None,
                     help="threads,rows_per_block: pin the launch plan instead of the autotuned one (profiling)")
     ap.add_argument("--nx", type=int, default=NX,
@@ -298,6 +365,9 @@ def main():
     e2e_sec = time.perf_counter() - t0
     e2e_val = job_mlups(nodes, e2e_steps, world, max_over_ranks(e2e_sec, world, "cuda"))
 
+    # ---- batched sweep: many cavities, one launch per step
+    batch = None if args.no_batch else batch_benchmark(mdf, torch, stream)
+
     # ---- time to residual 1e-8 from rest: lid-driven cavity, Re = 1000, 257^2
     ttr = None
     if not args.no_time_to_residual:
@@ -330,6 +400,7 @@ def main():
         "cpu_baseline": cpu,
         "check": {"residual": r, "drift_u": drift[0], "drift_v": drift[1]},
         "time_to_residual": ttr,
+        "batch": batch,
     }
     if ttr and cpu:
         for k in ttr:
