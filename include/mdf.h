@@ -90,14 +90,35 @@ typedef struct {
 /* Scheme parameters: lattice speed c (= |c_j|, Eq. 3.1.0), CFL number
  * (Eq. 3.1, 0 < cfl < 1), mixed-scheme weight eta (Eq. 2.2.12, 0..1) and the
  * ratio s'/s of the free rates (Sec. 4 uses 1.5).  A NULL params pointer
- * selects c = 1, cfl = 0.5, eta = 0.8, s_ratio = 1.5. */
+ * selects c = 1, cfl = 0.5, eta = 0.8, s_ratio = 1.5, FP32 storage.
+ *
+ * storage selects how the state is kept in device memory between steps (the
+ * arithmetic is FP32 in every mode; the paper stores fhat in full
+ * precision, the 16-bit modes have no counterpart there):
+ *   MDF_STORAGE_FP32  the 10 distributions fhat_{alpha,j} in FP32 (40 B/node)
+ *   MDF_STORAGE_FP16  u, v, P (Eqs. 2.3.5-2.3.7) in FP32 and the
+ *   MDF_STORAGE_BF16  non-equilibrium parts fhat_{alpha,j} - feq_{alpha,j}
+ *                     of j = 1..4 in FP16 / BF16 (j = 0 follows, since the
+ *                     non-equilibrium part carries no zeroth moment),
+ *                     scaled by the power of two 2^(12 - floor(log2 c)):
+ *                     28 B/node.  Only periodic Newtonian problems on uniform
+ *                     or separable grids (MDF_E_INVALID otherwise); rounding
+ *                     the non-equilibrium part perturbs each step by at most
+ *                     2^-11 (FP16) or 2^-8 (BF16) of |fhat - feq|; in FP16
+ *                     a non-equilibrium part above about 16 c overflows and
+ *                     the next residual reports MDF_E_DIVERGED.
+ * The distribution and field calls convert, so their layouts do not depend
+ * on the storage mode; checkpoints of the 16-bit modes hold the raw device
+ * buffer (see mdf_save). */
+enum { MDF_STORAGE_FP32 = 0, MDF_STORAGE_FP16 = 1, MDF_STORAGE_BF16 = 2 };
 typedef struct {
     double c, cfl, eta, s_ratio;
+    int storage;
 } mdf_params;
 
 /* Create a solver: validates the arguments (MDF_E_INVALID before any CUDA
- * call), allocates two FP32 state buffers of 10 planes each on the current
- * device, forms the grid metrics and dt = cfl * dx_min / c (Eq. 3.1), and
+ * call), allocates two state buffers (layout chosen by params->storage) on
+ * the current device, forms the grid metrics and dt = cfl * dx_min / c (Eq. 3.1), and
  * sets the state to rest (u = v = p = 0).  *out receives the context. */
 mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc *bc,
                       const mdf_params *params, mdf_ctx **out);
@@ -157,8 +178,13 @@ mdf_status mdf_set_distributions(mdf_ctx *ctx, const float *in, int on_device);
  * Returns MDF_E_TIMEOUT if the wait ran out or a bounded device wait gave up. */
 mdf_status mdf_synchronize(mdf_ctx *ctx, double timeout_s);
 
-/* Checkpoint: raw little-endian FP32 state plus a text header (grid size,
- * step count, dt).  mdf_load requires a context of the same grid size. */
+/* Checkpoint: a 256-byte text header (grid size, step count, dt, plane
+ * count) followed by the state.  FP32 storage: the 10 planes of
+ * mdf_get_distributions, little-endian FP32; mdf_load requires a context of
+ * the same grid size.  16-bit storage: the raw padded device buffer (header
+ * adds the storage mode and row pitch), so a restart continues bitwise;
+ * mdf_load then requires a context with the same grid, storage mode and
+ * pitch, else MDF_E_INVALID. */
 mdf_status mdf_save(mdf_ctx *ctx, const char *path);
 mdf_status mdf_load(mdf_ctx *ctx, const char *path);
 
@@ -195,14 +221,14 @@ double mdf_bytes_per_node(const mdf_ctx *ctx);
  * kind, the fluid model (Newtonian or power law) and the wall/periodic type
  * (one kernel variant); sizes, viscosities, power-law indices, wall
  * velocities and forcing may differ (mdf_set_force on a problem's context
- * takes effect at the next mdf_batch_step).  This is the batching the survey of the
- * method lists after the single-problem step; the paper itself has no
- * counterpart. */
+ * takes effect at the next mdf_batch_step).  The paper itself has no
+ * counterpart: it solves one problem at a time. */
 typedef struct mdf_batch mdf_batch;
 
 /* grids/fluids/bcs: `count` entries each; params: NULL or `count` entries.
  * Each problem starts at rest.  MDF_E_INVALID if the problems cannot share
- * one kernel variant or any problem is invalid (see mdf_create). */
+ * one kernel variant, any problem is invalid (see mdf_create) or asks for
+ * 16-bit storage (batches keep FP32 storage). */
 mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *fluids, const mdf_bc *bcs,
                             const mdf_params *params, mdf_batch **out);
 void mdf_batch_destroy(mdf_batch *batch);

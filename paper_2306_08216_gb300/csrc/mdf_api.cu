@@ -1,6 +1,7 @@
 // mdf_api.cu -- host runtime behind the C ABI of include/mdf.h.
 //
-// Owns the device state (two FP32 buffers of 10 padded planes), the TMA
+// Owns the device state (two buffers of padded 32-bit planes: 10 FP32
+// distributions, or u, v, P and 4 planes of 16-bit pairs), the TMA
 // descriptors of both buffers, the launch plan of the fused step, the grid
 // metrics and force planes, and the FP64 residual machinery.  Argument
 // validation happens before any CUDA call, so MDF_E_INVALID never touches
@@ -58,6 +59,9 @@ static mdf_status encode_maps_box(mdf_ctx *c, int box_nt, CUtensorMap maps[2]);
 
 static mdf_status encode_maps(mdf_ctx *c) { return encode_maps_box(c, c->plan.NT, c->tmap); }
 
+// Tensor maps of both state buffers for boxes of box_nt columns x 1 row x
+// all planes (32-bit elements; the 16-bit pair words move as opaque 32-bit
+// values).
 static mdf_status encode_maps_box(mdf_ctx *c, int box_nt, CUtensorMap maps[2]) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -68,10 +72,11 @@ static mdf_status encode_maps_box(mdf_ctx *c, int box_nt, CUtensorMap maps[2]) {
             return fail(c, MDF_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
+    const int planes = state_planes(c->prm.storage);
     for (int b = 0; b < 2; ++b) {
-        cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->ny, (cuuint64_t)NPLANES};
+        cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->ny, (cuuint64_t)planes};
         cuuint64_t strides[2] = {(cuuint64_t)c->pitch * 4, (cuuint64_t)c->plane * 4};
-        cuuint32_t box[3] = {(cuuint32_t)box_nt, 1, (cuuint32_t)NPLANES};
+        cuuint32_t box[3] = {(cuuint32_t)box_nt, 1, (cuuint32_t)planes};
         cuuint32_t estr[3] = {1, 1, 1};
         CUresult r = encode(&maps[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->buf[b], dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -214,7 +219,7 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
             !finite_pos(fluid->nu_max) || fluid->nu_min > fluid->nu_max)
             return fail(nullptr, MDF_E_INVALID, "power law needs K, n > 0 and 0 < nu_min <= nu_max");
     }
-    mdf_params prm = params ? *params : mdf_params{1.0, 0.5, 0.8, 1.5};
+    mdf_params prm = params ? *params : mdf_params{1.0, 0.5, 0.8, 1.5, MDF_STORAGE_FP32};
     if (!finite_pos(prm.c)) return fail(nullptr, MDF_E_INVALID, "c must be > 0");
     if (!(prm.cfl > 0 && prm.cfl < 1)) return fail(nullptr, MDF_E_INVALID, "cfl must be in (0, 1)");
     if (!(prm.eta >= 0 && prm.eta <= 1)) return fail(nullptr, MDF_E_INVALID, "eta must be in [0, 1]");
@@ -222,6 +227,12 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
     for (int s = 0; s < 4; ++s)
         if (!isfinite(bc->u_wall[s]) || !isfinite(bc->v_wall[s]))
             return fail(nullptr, MDF_E_INVALID, "wall velocities must be finite");
+    if (prm.storage < MDF_STORAGE_FP32 || prm.storage > MDF_STORAGE_BF16)
+        return fail(nullptr, MDF_E_INVALID, "unknown storage mode %d", prm.storage);
+    if (prm.storage != MDF_STORAGE_FP32 &&
+        !fast_path_applies(grid->kind, fluid->power_law ? 1 : 0, (xwall || ywall) ? 1 : 0))
+        return fail(nullptr, MDF_E_INVALID,
+                    "16-bit storage needs a periodic Newtonian problem on a uniform or separable grid");
 
     mdf_ctx *c = new mdf_ctx();
     c->nx = grid->nx;
@@ -252,8 +263,8 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
     const int metric = grid->kind;
     {
         cudaError_t pe = cudaSuccess;
-        c->ncand = step_candidates(metric, fluid->power_law ? 1 : 0, (xwall || ywall) ? 1 : 0, c->nx, c->ny,
-                                   c->num_sms, c->cand, mdf_ctx::kMaxCandidates, &pe);
+        c->ncand = step_candidates(metric, fluid->power_law ? 1 : 0, (xwall || ywall) ? 1 : 0, prm.storage, c->nx,
+                                   c->ny, c->num_sms, c->cand, mdf_ctx::kMaxCandidates, &pe);
         CKE(pe);
         if (c->ncand < 1) CKE(cudaErrorInvalidConfiguration);
     }
@@ -264,7 +275,7 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
         if (pt > c->pitch) c->pitch = pt;
     }
     c->plane = (long long)c->pitch * c->ny;
-    const size_t state_bytes = (size_t)NPLANES * c->plane * sizeof(float);
+    const size_t state_bytes = state_buffer_bytes(prm.storage, c->plane);
     for (int b = 0; b < 2; ++b) {
         CKE(cudaMalloc(&c->buf[b], state_bytes));
         CKE(cudaMemset(c->buf[b], 0, state_bytes));
@@ -285,6 +296,9 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
     x.power_law = fluid->power_law ? 1 : 0;
     x.nu = (float)fluid->nu; x.K = (float)fluid->K; x.n_index = (float)fluid->n;
     x.nu_min = (float)fluid->nu_min; x.nu_max = (float)fluid->nu_max;
+    x.storage = prm.storage;
+    x.nscale = (float)ldexp(1.0, NSCALE_EXP - ilogb(prm.c));
+    x.ninv = (float)ldexp(1.0, ilogb(prm.c) - NSCALE_EXP);
     CKE(cudaMalloc(&c->partials, (size_t)aux_residual_blocks(x) * 5 * sizeof(double)));
 
     // Grid metrics (FP64 on the GPU) and the time step of Eq. 3.1.
@@ -344,6 +358,9 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
     c->dt = prm.cfl * c->dxmin / prm.c;  // Eq. 3.1
 
     StepArgs &a = c->args;
+    a.storage = prm.storage;
+    a.nscale = x.nscale;
+    a.ninv = x.ninv;
     a.nx = c->nx; a.ny = c->ny; a.pitch = c->pitch; a.plane = c->plane;
     a.W = c->plan.W; a.H = c->plan.H;
     a.xwall = xwall; a.ywall = ywall;
@@ -567,8 +584,30 @@ mdf_status mdf_synchronize(mdf_ctx *c, double timeout_s) {
     return wait_stream(c, timeout_s);
 }
 
+// 16-bit storage: the checkpoint holds the raw device buffer (padded planes
+// u, v, P and the 16-bit non-equilibrium planes), so a restart is bitwise.
+static mdf_status save_raw(mdf_ctx *c, const char *path) {
+    const size_t bytes = state_buffer_bytes(c->prm.storage, c->plane);
+    unsigned char *h = (unsigned char *)malloc(bytes);
+    if (!h) return fail(c, MDF_E_NOMEM, "host buffer");
+    CK(c, cudaMemcpyAsync(h, c->buf[c->cur], bytes, cudaMemcpyDeviceToHost, c->stream));
+    mdf_status s = wait_stream(c, 0);
+    if (s != MDF_OK) { free(h); return s; }
+    FILE *fp = fopen(path, "wb");
+    if (!fp) { free(h); return fail(c, MDF_E_INVALID, "cannot open %s", path); }
+    char hdr[256];
+    memset(hdr, 0, sizeof(hdr));
+    snprintf(hdr, sizeof(hdr), "MDFCKPT1 nx=%d ny=%d steps=%lld dt=%.17g planes=%d storage=%d pitch=%d\n", c->nx,
+             c->ny, c->steps, c->dt, DEV_PLANES, c->prm.storage, c->pitch);
+    const bool ok = fwrite(hdr, 1, sizeof(hdr), fp) == sizeof(hdr) && fwrite(h, 1, bytes, fp) == bytes;
+    fclose(fp);
+    free(h);
+    return ok ? MDF_OK : fail(c, MDF_E_INVALID, "short write to %s", path);
+}
+
 mdf_status mdf_save(mdf_ctx *c, const char *path) {
     if (!c || !path) return c ? fail(c, MDF_E_INVALID, "path is NULL") : MDF_E_INVALID;
+    if (c->prm.storage != MDF_STORAGE_FP32) return save_raw(c, path);
     const size_t n = (size_t)NPLANES * c->nx * c->ny;
     float *h = (float *)malloc(n * sizeof(float));
     if (!h) return fail(c, MDF_E_NOMEM, "host buffer");
@@ -593,11 +632,36 @@ mdf_status mdf_load(mdf_ctx *c, const char *path) {
     char hdr[256];
     if (fread(hdr, 1, sizeof(hdr), fp) != sizeof(hdr)) { fclose(fp); return fail(c, MDF_E_INVALID, "bad header"); }
     hdr[255] = 0;
-    int nx = 0, ny = 0, planes = 0;
+    int nx = 0, ny = 0, planes = 0, storage = 0, pitch = 0;
     long long steps = 0;
     double dt = 0;
-    if (sscanf(hdr, "MDFCKPT1 nx=%d ny=%d steps=%lld dt=%lg planes=%d", &nx, &ny, &steps, &dt, &planes) != 5 ||
-        nx != c->nx || ny != c->ny || planes != NPLANES) {
+    const int got = sscanf(hdr, "MDFCKPT1 nx=%d ny=%d steps=%lld dt=%lg planes=%d storage=%d pitch=%d", &nx, &ny,
+                           &steps, &dt, &planes, &storage, &pitch);
+    if (got < 5 || nx != c->nx || ny != c->ny) {
+        fclose(fp);
+        return fail(c, MDF_E_INVALID, "checkpoint does not match this grid");
+    }
+    if (c->prm.storage != MDF_STORAGE_FP32 || got == 7) {
+        // raw 16-bit checkpoint: same storage mode and padded layout only
+        if (got != 7 || storage != c->prm.storage || pitch != c->pitch || planes != DEV_PLANES) {
+            fclose(fp);
+            return fail(c, MDF_E_INVALID, "checkpoint storage mode or layout does not match this solver");
+        }
+        const size_t bytes = state_buffer_bytes(storage, c->plane);
+        unsigned char *h = (unsigned char *)malloc(bytes);
+        if (!h) { fclose(fp); return fail(c, MDF_E_NOMEM, "host buffer"); }
+        const bool ok = fread(h, 1, bytes, fp) == bytes;
+        fclose(fp);
+        if (!ok) { free(h); return fail(c, MDF_E_INVALID, "short read from %s", path); }
+        cudaError_t e = cudaMemcpyAsync(c->buf[c->cur], h, bytes, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = aux_snapshot(c->aux, c->buf[c->cur], c->snap_u, c->snap_v, c->stream);
+        mdf_status s = e == cudaSuccess ? wait_stream(c, 0)
+                                         : fail(c, MDF_E_CUDA, "checkpoint upload: %s", cudaGetErrorString(e));
+        free(h);
+        if (s == MDF_OK) { c->steps = steps; c->snap_step = steps; }
+        return s;
+    }
+    if (planes != NPLANES) {
         fclose(fp);
         return fail(c, MDF_E_INVALID, "checkpoint does not match this grid");
     }
@@ -649,7 +713,7 @@ mdf_status mdf_set_launch(mdf_ctx *c, int threads, int rows_per_block) {
 
 double mdf_bytes_per_node(const mdf_ctx *c) {
     if (!c) return NAN;
-    double b = 2.0 * NPLANES * 4.0;
+    double b = 2.0 * 4.0 * state_planes(c->prm.storage);
     if (c->force_mode == MDF_FORCE_FIELD) b += 8.0;
     if (c->kind == MDF_GRID_CURVILINEAR) b += 16.0;
     return b;

@@ -1,10 +1,13 @@
 // mdf_aux.cu -- auxiliary kernels of libmdf.so: initial state (Sec. 4,
 // fhat = feq), grid metrics in FP64 (coordinate transformation), derived
 // fields (Sec. 2.4), the FP64 residual/drift reduction, and the packing
-// between the padded plane layout and dense caller arrays.
+// between the padded plane layout and dense caller arrays.  Every kernel
+// reads and writes both state layouts (10 FP32 planes, or u, v, P in FP32
+// plus 8 16-bit non-equilibrium planes).
 #include <math.h>
 
 #include "mdf_aux.cuh"
+#include "mdf_device.cuh"
 
 namespace mdf {
 
@@ -26,6 +29,78 @@ __device__ __forceinline__ void equilibrium(float u, float v, float P, float inv
     out[5] = v5; out[6] = v5 + F1y; out[8] = v5 - F1y; out[7] = v5 + F2y; out[9] = v5 - F2y;
 }
 
+// ---- access to one node of either state layout ------------------------------
+
+// Non-equilibrium pair n_j = (n_{u,j}, n_{v,j}), j = 1..4, of a 16-bit
+// layout at storage element s (unscaled).
+__device__ __forceinline__ dev::F2 pair_at(const AuxArgs &a, const float *f, int j, long long s) {
+    const unsigned w = reinterpret_cast<const unsigned *>(f)[(DEV_FPLANES + j - 1) * a.plane + s];
+    const dev::F2 p = a.storage == STORAGE_FP16 ? dev::unpack16<STORAGE_FP16>(w) : dev::unpack16<STORAGE_BF16>(w);
+    return p * dev::splat(a.ninv);
+}
+
+// Velocity (u, v) = sum_j fhat_{alpha,j} (Eq. 2.3.5) at storage element s.
+__device__ __forceinline__ void node_uv(const AuxArgs &a, const float *f, long long s, float &u, float &v) {
+    if (a.storage == STORAGE_FP32) {
+        u = 0.0f;
+        v = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            u += f[j * a.plane + s];
+            v += f[(5 + j) * a.plane + s];
+        }
+    } else {
+        u = f[s];
+        v = f[a.plane + s];
+    }
+}
+
+// The 10 distributions fhat_{alpha,j} (plane order k = 5 alpha + j).  In the
+// 16-bit layouts fhat = feq(u, v, P) + n, formed exactly as the step does.
+__device__ __forceinline__ void node_full(const AuxArgs &a, const float *f, long long s, float g[10]) {
+    if (a.storage == STORAGE_FP32) {
+#pragma unroll
+        for (int k = 0; k < NPLANES; ++k) g[k] = f[k * a.plane + s];
+        return;
+    }
+    dev::F2 nn[4], gp[5], np[5];
+#pragma unroll
+    for (int j = 1; j < 5; ++j) nn[j - 1] = pair_at(a, f, j, s);
+    dev::dev_build(f[s], f[a.plane + s], f[2 * a.plane + s], nn, a.inv2c, gp, np);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) dev::split2(gp[j], g[j], g[5 + j]);
+}
+
+// Write node (u, v, P, n_1..n_4) of a 16-bit layout at storage element s.
+__device__ __forceinline__ void node_store16(const AuxArgs &a, float *f, long long s, float u, float v, float P,
+                                             const dev::F2 n[4]) {
+    f[s] = u;
+    f[a.plane + s] = v;
+    f[2 * a.plane + s] = P;
+    unsigned *w = reinterpret_cast<unsigned *>(f);
+    const dev::F2 S = dev::splat(a.nscale);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        w[(DEV_FPLANES + j) * a.plane + s] = a.storage == STORAGE_FP16 ? dev::pack16<STORAGE_FP16>(n[j] * S)
+                                                                        : dev::pack16<STORAGE_BF16>(n[j] * S);
+}
+
+// Split 10 distributions into (u, v, P, n_1..n_4) with the moments and
+// non-equilibrium part the step uses.
+__device__ __forceinline__ void node_split(const AuxArgs &a, const float g[10], float &u, float &v, float &P,
+                                           dev::F2 n[4]) {
+    dev::F2 gp[5], np[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) gp[j] = dev::mk2(g[j], g[5 + j]);
+    const dev::Mom2 m = dev::moments2(gp, a.c);
+    dev::noneq2(gp, m, a.inv2c, np);
+    u = m.u;
+    v = m.v;
+    P = m.P;
+#pragma unroll
+    for (int j = 1; j < 5; ++j) n[j - 1] = np[j];
+}
+
 }  // namespace
 
 // One thread per stored column slot (including ghosts) and row.
@@ -34,11 +109,17 @@ __global__ void init_kernel(AuxArgs a, const float *u, const float *v, const flo
     const int y = blockIdx.y;
     if (col >= a.pitch || y >= a.ny) return;
     const int X = col - GHOST;
+    const long long s = (long long)y * a.pitch + col;
+    const dev::F2 zero4[4] = {dev::splat(0.0f), dev::splat(0.0f), dev::splat(0.0f), dev::splat(0.0f)};
     int xs = X;
     if (!a.xwall) xs = wrapi(X, a.nx);
     else if (X < 0 || X >= a.nx) {
+        if (a.storage != STORAGE_FP32) {
+            node_store16(a, f, s, 0.0f, 0.0f, 0.0f, zero4);
+            return;
+        }
 #pragma unroll
-        for (int k = 0; k < NPLANES; ++k) f[k * a.plane + (long long)y * a.pitch + col] = 0.0f;
+        for (int k = 0; k < NPLANES; ++k) f[k * a.plane + s] = 0.0f;
         return;
     }
     const long long n = (long long)y * a.nx + xs;
@@ -50,10 +131,14 @@ __global__ void init_kernel(AuxArgs a, const float *u, const float *v, const flo
         const int side = y == 0 ? 2 : 3;
         uu = a.uw[side]; vv = a.vw[side];
     }
+    if (a.storage != STORAGE_FP32) {  // fhat = feq: no non-equilibrium part
+        node_store16(a, f, s, uu, vv, p[n], zero4);
+        return;
+    }
     float e[10];
     equilibrium(uu, vv, p[n], a.inv2c, e);
 #pragma unroll
-    for (int k = 0; k < NPLANES; ++k) f[k * a.plane + (long long)y * a.pitch + col] = e[k];
+    for (int k = 0; k < NPLANES; ++k) f[k * a.plane + s] = e[k];
 }
 
 // Dense [2][5][ny][nx] <-> padded planes.  On unpack, ghost columns of a
@@ -64,6 +149,35 @@ __global__ void pack_kernel(AuxArgs a, const float *f, float *dense) {
     const int k = blockIdx.z;
     if (x >= a.nx) return;
     dense[((long long)k * a.ny + y) * a.nx + x] = f[k * a.plane + (long long)y * a.pitch + GHOST + x];
+}
+
+// 16-bit layouts: one thread per node and all planes.
+__global__ void pack16_kernel(AuxArgs a, const float *f, float *dense) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= a.nx) return;
+    float g[10];
+    node_full(a, f, (long long)y * a.pitch + GHOST + x, g);
+#pragma unroll
+    for (int k = 0; k < NPLANES; ++k) dense[((long long)k * a.ny + y) * a.nx + x] = g[k];
+}
+
+__global__ void unpack16_kernel(AuxArgs a, const float *dense, float *f) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (col >= a.pitch) return;
+    const int X = col - GHOST;
+    float g[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int xs = -1;
+    if (!a.xwall) xs = wrapi(X, a.nx);
+    else if (X >= 0 && X < a.nx) xs = X;
+    if (xs >= 0)
+#pragma unroll
+        for (int k = 0; k < NPLANES; ++k) g[k] = dense[((long long)k * a.ny + y) * a.nx + xs];
+    float u, v, P;
+    dev::F2 nn[4];
+    node_split(a, g, u, v, P, nn);
+    node_store16(a, f, (long long)y * a.pitch + col, u, v, P, nn);
 }
 
 __global__ void unpack_kernel(AuxArgs a, const float *dense, float *f) {
@@ -243,17 +357,37 @@ __global__ void fields_kernel(AuxArgs a, const float *f, FieldPtrs dst) {
     const int y = blockIdx.y;
     if (x >= a.nx) return;
     const long long s = (long long)y * a.pitch + GHOST + x;
-    float g[10];
-#pragma unroll
-    for (int k = 0; k < NPLANES; ++k) g[k] = f[k * a.plane + s];
     const float c = a.c;
-    const float u = g[0] + g[1] + g[2] + g[3] + g[4];
-    const float v = g[5] + g[6] + g[7] + g[8] + g[9];
-    const float d1x = g[1] - g[3], d1y = g[2] - g[4], d2x = g[6] - g[8], d2y = g[7] - g[9];
-    const float P = 0.5f * (c * (d1x + d2y) - u * u - v * v);  // Eq. 2.3.23, R = 0
-    // first moment of fhat - feq (Eq. 2.2.5 fluxes ub u + P E)
-    const float gx1 = c * d1x - (u * u + P), gy1 = c * d1y - u * v;
-    const float gx2 = c * d2x - u * v, gy2 = c * d2y - (v * v + P);
+    float u, v, P, gx1, gy1, gx2, gy2;
+    if (a.storage == STORAGE_FP32) {
+        float g[10];
+#pragma unroll
+        for (int k = 0; k < NPLANES; ++k) g[k] = f[k * a.plane + s];
+        u = g[0] + g[1] + g[2] + g[3] + g[4];
+        v = g[5] + g[6] + g[7] + g[8] + g[9];
+        const float d1x = g[1] - g[3], d1y = g[2] - g[4], d2x = g[6] - g[8], d2y = g[7] - g[9];
+        P = 0.5f * (c * (d1x + d2y) - u * u - v * v);  // Eq. 2.3.23, R = 0
+        // first moment of fhat - feq (Eq. 2.2.5 fluxes ub u + P E)
+        gx1 = c * d1x - (u * u + P);
+        gy1 = c * d1y - u * v;
+        gx2 = c * d2x - u * v;
+        gy2 = c * d2y - (v * v + P);
+    } else {
+        // stored u, v, P; the first moment of fhat - feq is c (n_1 - n_3),
+        // c (n_2 - n_4) per component
+        u = f[s];
+        v = f[a.plane + s];
+        P = f[2 * a.plane + s];
+        float n1u, n1v, n2u, n2v, n3u, n3v, n4u, n4v;
+        dev::split2(pair_at(a, f, 1, s), n1u, n1v);
+        dev::split2(pair_at(a, f, 2, s), n2u, n2v);
+        dev::split2(pair_at(a, f, 3, s), n3u, n3v);
+        dev::split2(pair_at(a, f, 4, s), n4u, n4v);
+        gx1 = c * (n1u - n3u);
+        gy1 = c * (n2u - n4u);
+        gx2 = c * (n1v - n3v);
+        gy2 = c * (n2v - n4v);
+    }
     float nu = a.nu;
     if (a.power_law) {
         const float sxy = 0.5f * (gy1 + gx2);
@@ -282,12 +416,8 @@ __global__ void residual_partial_kernel(AuxArgs a, const float *f, float *su, fl
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(n / a.nx), x = (int)(n % a.nx);
         const long long s = (long long)y * a.pitch + GHOST + x;
-        float u = 0.0f, v = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            u += f[j * a.plane + s];
-            v += f[(5 + j) * a.plane + s];
-        }
+        float u, v;
+        node_uv(a, f, s, u, v);
         if (!isfinite(u) || !isfinite(v)) bad += 1.0;
         const double du = (double)u - su[n], dv = (double)v - sv[n];
         d2 += du * du + dv * dv;
@@ -349,12 +479,8 @@ __global__ void snapshot_kernel(AuxArgs a, const float *f, float *su, float *sv)
     const int y = blockIdx.y;
     if (x >= a.nx) return;
     const long long s = (long long)y * a.pitch + GHOST + x;
-    float u = 0.0f, v = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 5; ++j) {
-        u += f[j * a.plane + s];
-        v += f[(5 + j) * a.plane + s];
-    }
+    float u, v;
+    node_uv(a, f, s, u, v);
     su[(long long)y * a.nx + x] = u;
     sv[(long long)y * a.nx + x] = v;
 }
@@ -372,11 +498,19 @@ cudaError_t aux_init(const AuxArgs &a, const float *u, const float *v, const flo
 }
 
 cudaError_t aux_pack(const AuxArgs &a, const float *f, float *dense, cudaStream_t st) {
+    if (a.storage != STORAGE_FP32) {
+        pack16_kernel<<<rows_grid(a.nx, a.ny, 128), 128, 0, st>>>(a, f, dense);
+        return cudaGetLastError();
+    }
     pack_kernel<<<rows_grid(a.nx, a.ny, 128, NPLANES), 128, 0, st>>>(a, f, dense);
     return cudaGetLastError();
 }
 
 cudaError_t aux_unpack(const AuxArgs &a, const float *dense, float *f, cudaStream_t st) {
+    if (a.storage != STORAGE_FP32) {
+        unpack16_kernel<<<rows_grid(a.pitch, a.ny, 128), 128, 0, st>>>(a, dense, f);
+        return cudaGetLastError();
+    }
     unpack_kernel<<<rows_grid(a.pitch, a.ny, 128, NPLANES), 128, 0, st>>>(a, dense, f);
     return cudaGetLastError();
 }

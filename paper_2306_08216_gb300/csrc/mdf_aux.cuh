@@ -15,6 +15,8 @@ struct AuxArgs {
     float uw[4], vw[4];
     int power_law;
     float nu, K, n_index, nu_min, nu_max, a_pl;  // a_pl = cs2 dt / 2
+    int storage;                                 // StorageKind of the state buffers
+    float nscale, ninv;                          // 16-bit storage: S and 1/S
 };
 
 struct FieldPtrs {

@@ -4,6 +4,9 @@
 // non-equilibrium extrapolation, mixed-scheme streaming increment).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "mdf_internal.cuh"
 
 namespace mdf {
@@ -270,6 +273,89 @@ __device__ __forceinline__ void store_node(const StepArgs &a, int row, int X, co
     }
 }
 
+
+// ------------------------------------------------------------ 16-bit storage
+
+// 16-bit pair word (low half: alpha = u, high half: alpha = v) <-> pair.
+template <int ST>
+__device__ __forceinline__ F2 unpack16(unsigned w) {
+    float2 f;
+    if (ST == STORAGE_FP16) {
+        __half2 h;
+        memcpy(&h, &w, 4);
+        f = __half22float2(h);
+    } else {
+        __nv_bfloat162 h;
+        memcpy(&h, &w, 4);
+        f = __bfloat1622float2(h);
+    }
+    return mk2(f.x, f.y);
+}
+template <int ST>
+__device__ __forceinline__ unsigned pack16(F2 a) {
+    float x, y;
+    split2(a, x, y);
+    unsigned w;
+    if (ST == STORAGE_FP16) {
+        const __half2 h = __floats2half2_rn(x, y);
+        memcpy(&w, &h, 4);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+        memcpy(&w, &h, 4);
+    }
+    return w;
+}
+
+// Node of the 16-bit layouts: fhat = feq(u, v, P) + n with
+// n_0 = -(n_1 + n_2 + n_3 + n_4); nn[j - 1] = n_j (j = 1..4, unscaled).
+// Returns the pairs g = fhat and n.
+__device__ __forceinline__ void dev_build(float u, float v, float P, const F2 nn[4], float inv2c, F2 g[5],
+                                          F2 n[5]) {
+#pragma unroll
+    for (int j = 1; j < 5; ++j) n[j] = nn[j - 1];
+    n[0] = splat(0.0f) - ((n[1] + n[2]) + (n[3] + n[4]));
+    const F2 uv = mk2(u, v);
+    const F2 u5 = splat(0.2f) * uv;
+    const float uu = fmaf(u, u, P) * inv2c, uvv = u * v * inv2c, vv = fmaf(v, v, P) * inv2c;
+    const F2 fx = mk2(uu, uvv), fy = mk2(uvv, vv);
+    g[0] = fma2(splat(-4.0f), u5, uv) + n[0];
+    g[1] = (u5 + fx) + n[1];
+    g[3] = (u5 - fx) + n[3];
+    g[2] = (u5 + fy) + n[2];
+    g[4] = (u5 - fy) + n[4];
+}
+
+// Store one node in a 16-bit layout at element e of every plane.
+__device__ __forceinline__ void dev_store_at(const StepArgs &a, long long e, float u, float v, float P,
+                                             const unsigned w[4]) {
+    float *fp = a.fout;
+    unsigned *wp = reinterpret_cast<unsigned *>(fp);
+    fp[e] = u;
+    fp[a.plane + e] = v;
+    fp[2 * a.plane + e] = P;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) wp[(DEV_FPLANES + j) * a.plane + e] = w[j];
+}
+
+// Output of one node (5 pairs of fhat) in a 16-bit layout: moments and
+// non-equilibrium part as the FP32 path forms them on load, n scaled by S
+// and rounded to 16 bits.
+template <int ST, bool XPER>
+__device__ __forceinline__ void store_node_dev(const StepArgs &a, int row, int X, const F2 v[5]) {
+    const Mom2 m = moments2(v, a.c);
+    F2 n[5];
+    noneq2(v, m, a.inv2c, n);
+    const F2 S = splat(a.nscale);
+    unsigned w[4];
+#pragma unroll
+    for (int j = 1; j < 5; ++j) w[j - 1] = pack16<ST>(n[j] * S);
+    const long long base = (long long)row * a.pitch + GHOST + X;
+    dev_store_at(a, base, m.u, m.v, m.P, w);
+    if (XPER) {
+        if (X < GHOST) dev_store_at(a, base + a.nx, m.u, m.v, m.P, w);
+        if (X >= a.nx - GHOST) dev_store_at(a, base - a.nx, m.u, m.v, m.P, w);
+    }
+}
 
 }  // namespace dev
 }  // namespace mdf

@@ -18,11 +18,33 @@ constexpr int NPLANES = 10;
 
 enum MetricKind { METRIC_UNIFORM = 0, METRIC_SEPARABLE = 1, METRIC_CURVILINEAR = 2 };
 
+// State storage.  STORAGE_FP32: 10 FP32 planes fhat_{alpha,j}.  The 16-bit
+// modes keep the macroscopic fields exact and round only the small
+// non-equilibrium part n = fhat - feq(u, v, P): 7 planes of 32-bit words,
+// u, v, P in FP32 followed by, for j = 1..4, the pair word of S n_{u,j}
+// (low half) and S n_{v,j} (high half) in FP16 or BF16;
+// n_{alpha,0} = -(n_1 + n_2 + n_3 + n_4).  The scale S = 2^(12 - floor(log2
+// c)) is a power of two (exact both ways) that lifts n, a few orders of
+// magnitude below c, out of the FP16 subnormal range while keeping
+// |S n| < 65504 for |n| up to about 16 c.
+enum StorageKind { STORAGE_FP32 = 0, STORAGE_FP16 = 1, STORAGE_BF16 = 2 };
+constexpr int DEV_FPLANES = 3;  // u, v, P
+constexpr int DEV_PLANES = 7;   // plus 4 pair planes
+constexpr int NSCALE_EXP = 12;
+
+// 32-bit planes of one state buffer.
+inline int state_planes(int storage) { return storage == STORAGE_FP32 ? NPLANES : DEV_PLANES; }
+inline size_t state_buffer_bytes(int storage, long long plane) {
+    return (size_t)state_planes(storage) * plane * 4;
+}
+
 // Error codes the kernels raise in StepArgs::err (first one wins).
 enum DeviceError { DEVERR_NONE = 0, DEVERR_TMA_TIMEOUT = 1 };
 
 struct StepArgs {
     float *fout;            // output state (same layout as the input)
+    int storage;            // StorageKind of both state buffers
+    float nscale, ninv;     // 16-bit storage: S and 1/S
     int nx, ny, pitch;      // nodes, row pitch in floats
     long long plane;        // floats per plane (pitch * ny)
     int W, H;               // output columns / rows per block
@@ -81,8 +103,8 @@ struct StepPlan {
 
 // Candidate launch plans of the fused step (the first one is the default);
 // returns how many were written to out[0..max).
-int step_candidates(int metric, int power_law, int walls, int nx, int ny, int num_sms, StepPlan *out, int max,
-                    cudaError_t *err);
+int step_candidates(int metric, int power_law, int walls, int storage, int nx, int ny, int num_sms, StepPlan *out,
+                    int max, cudaError_t *err);
 cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
                         cudaStream_t stream);
 int step_pitch(int nx, int W);
@@ -98,7 +120,7 @@ cudaError_t batch_launch(const BatchItem *items, int nitems, const StepArgs *arg
 
 // Periodic Newtonian fast path on uniform/separable grids (mdf_step_fast.cu).
 bool fast_path_applies(int metric, int power_law, int walls);
-cudaError_t fast_occupancy(int metric, int nt, int *occ, int *smem);
+cudaError_t fast_occupancy(int metric, int storage, int nt, int *occ, int *smem);
 cudaError_t fast_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
                         cudaStream_t stream);
 

@@ -551,15 +551,15 @@ static void fill_plan(int nt, int occ, int smem, int waves, int nx, int ny, int 
     plan->gy = (ny + H - 1) / H;
 }
 
-int step_candidates(int metric, int power_law, int walls, int nx, int ny, int num_sms, StepPlan *out, int max,
-                    cudaError_t *err) {
+int step_candidates(int metric, int power_law, int walls, int storage, int nx, int ny, int num_sms, StepPlan *out,
+                    int max, cudaError_t *err) {
     int n = 0;
     *err = cudaSuccess;
     const bool fast = fast_path_applies(metric, power_law, walls);
     const int nts[2] = {128, 256};
     for (int i = 0; i < (fast ? 2 : 1); ++i) {
         int occ = 0, smem = 0;
-        cudaError_t e = fast ? fast_occupancy(metric, nts[i], &occ, &smem)
+        cudaError_t e = fast ? fast_occupancy(metric, storage, nts[i], &occ, &smem)
                              : occupancy(metric, power_law, walls, &occ, &smem);
         if (e != cudaSuccess) {
             *err = e;

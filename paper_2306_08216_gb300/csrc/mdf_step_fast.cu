@@ -56,9 +56,11 @@ __device__ __forceinline__ F2 force_at(const StepArgs &a, int row, int X, F2 fac
     return factor * mk2(a.Fxp[fi], a.Fyp[fi]);
 }
 
-template <int NT, int MK, bool FORCED>
-__global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) fast_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
-    constexpr int TROW = NPLANES * NT * 4;  // one TMA row: 10 planes x NT floats
+template <int NT, int MK, bool FORCED, int ST>
+__global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
+    fast_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
+    // one TMA row: 10 FP32 planes, or u, v, P and 4 planes of 16-bit pairs
+    constexpr int TROW = (ST == STORAGE_FP32 ? NPLANES : DEV_PLANES) * NT * 4;
     constexpr int PROW = 5 * NT * 8;        // one fhat^+ ring row: 5 pairs x NT
     constexpr int XROW = 2 * NT * 8;        // one exchange row: pops 1, 3 x NT
     extern __shared__ __align__(128) unsigned char smem[];
@@ -154,7 +156,8 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) fast_kernel(const __gri
                                         wy.w2);
                 out[4] = stream2<false>(out[4], FY[s1][1], FY[k][1], FY[s4][1], FY[s3][1], false, wy.w1, wy.w0,
                                         wy.w2);
-                store_node<true>(a, r, X, out);
+                if (ST == STORAGE_FP32) store_node<true>(a, r, X, out);
+                else store_node_dev<ST, true>(a, r, X, out);
             }
             // ---------------------------------------------- S2: row p
             F2 own1, own3;
@@ -162,12 +165,22 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) fast_kernel(const __gri
                 const bool ok = mbar_wait_bounded(&mbar[tslot], (uint32_t)((it / TMA_SLOTS) & 1));
                 if (!ok) atomicExch(&s_abort, 1);
                 const float *src = reinterpret_cast<const float *>(tma + tslot * TROW);
-                F2 g[5];
+                F2 g[5], n[5], o[5];
+                if (ST == STORAGE_FP32) {
 #pragma unroll
-                for (int j = 0; j < 5; ++j) g[j] = mk2(src[j * NT + t], src[(5 + j) * NT + t]);
-                const Mom2 m = moments2(g, c);
-                F2 n[5], o[5];
-                noneq2(g, m, inv2c, n);
+                    for (int j = 0; j < 5; ++j) g[j] = mk2(src[j * NT + t], src[(5 + j) * NT + t]);
+                    const Mom2 m = moments2(g, c);
+                    noneq2(g, m, inv2c, n);
+                } else {
+                    // fhat = feq(u, v, P) + n: the stored macroscopic fields
+                    // give the equilibrium directly
+                    const unsigned *w = reinterpret_cast<const unsigned *>(src + DEV_FPLANES * NT);
+                    const F2 inv = splat(a.ninv);
+                    F2 nn[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) nn[j] = unpack16<ST>(w[j * NT + t]) * inv;
+                    dev_build(src[t], src[NT + t], src[2 * NT + t], nn, inv2c, g, n);
+                }
                 const F2 n13 = n[1] - n[3], n24 = n[2] - n[4];
                 relax2(g, n, n13, n24, pair_of(a.pmKp), pair_of(a.pDp), o);
                 unsigned char *dP = ringP + k * PROW;
@@ -254,42 +267,67 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) fast_kernel(const __gri
     }
 }
 
-template <int NT>
+template <int NT, int ST>
 constexpr int fast_smem() {
-    return TMA_SLOTS * NPLANES * NT * 4 + RING * 5 * NT * 8 + 4 * (2 * NT * 8) + TMA_SLOTS * 8;
+    return TMA_SLOTS * (ST == STORAGE_FP32 ? NPLANES : DEV_PLANES) * NT * 4 +
+           RING * 5 * NT * 8 + 4 * (2 * NT * 8) + TMA_SLOTS * 8;
 }
 
-template <int NT, int MK, bool FORCED>
-cudaError_t fast_launch_t(const CUtensorMap *tmap, const StepArgs &args, const StepPlan &plan, cudaStream_t stream) {
-    auto k = fast_kernel<NT, MK, FORCED>;
+template <int NT, int MK, bool FORCED, int ST>
+cudaError_t fast_launch_t(const CUtensorMap *tmap, const StepArgs &args,
+                          const StepPlan &plan, cudaStream_t stream) {
+    auto k = fast_kernel<NT, MK, FORCED, ST>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem<NT>());
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem<NT, ST>());
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k<<<dim3(plan.gx, plan.gy), NT, fast_smem<NT>(), stream>>>(*tmap, args);
+    k<<<dim3(plan.gx, plan.gy), NT, fast_smem<NT, ST>(), stream>>>(*tmap, args);
     return cudaGetLastError();
 }
 
-template <int NT, int MK>
+template <int NT, int MK, int ST>
 cudaError_t fast_occupancy_t(int *occ, int *smem) {
-    // both force variants have the same shared memory; take the larger register count
+    // both force variants have the same shared memory; take the smaller occupancy
     int o1 = 0, o2 = 0;
-    *smem = fast_smem<NT>();
-    cudaError_t e = cudaFuncSetAttribute(fast_kernel<NT, MK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
+    *smem = fast_smem<NT, ST>();
+    cudaError_t e =
+        cudaFuncSetAttribute(fast_kernel<NT, MK, false, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fast_kernel<NT, MK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, fast_kernel<NT, MK, false>, NT, *smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, fast_kernel<NT, MK, true>, NT, *smem);
+        e = cudaFuncSetAttribute(fast_kernel<NT, MK, true, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, fast_kernel<NT, MK, false, ST>, NT, *smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, fast_kernel<NT, MK, true, ST>, NT, *smem);
     *occ = o1 < o2 ? o1 : o2;
     return e;
 }
 
+template <int NT, int MK, int ST>
+cudaError_t fast_launch_f(const CUtensorMap *tmap, const StepArgs &args,
+                          const StepPlan &plan, cudaStream_t stream) {
+    return args.force_mode ? fast_launch_t<NT, MK, true, ST>(tmap, args, plan, stream)
+                           : fast_launch_t<NT, MK, false, ST>(tmap, args, plan, stream);
+}
+
 template <int NT, int MK>
-cudaError_t fast_launch_f(const CUtensorMap *tmap, const StepArgs &args, const StepPlan &plan, cudaStream_t stream) {
-    return args.force_mode ? fast_launch_t<NT, MK, true>(tmap, args, plan, stream)
-                           : fast_launch_t<NT, MK, false>(tmap, args, plan, stream);
+cudaError_t fast_occupancy_s(int storage, int *occ, int *smem) {
+    switch (storage) {
+        case STORAGE_FP16: return fast_occupancy_t<NT, MK, STORAGE_FP16>(occ, smem);
+        case STORAGE_BF16: return fast_occupancy_t<NT, MK, STORAGE_BF16>(occ, smem);
+        default: return fast_occupancy_t<NT, MK, STORAGE_FP32>(occ, smem);
+    }
+}
+
+template <int NT, int MK>
+cudaError_t fast_launch_s(const CUtensorMap *tmap, const StepArgs &args,
+                          const StepPlan &plan, cudaStream_t stream) {
+    switch (args.storage) {
+        case STORAGE_FP16: return fast_launch_f<NT, MK, STORAGE_FP16>(tmap, args, plan, stream);
+        case STORAGE_BF16: return fast_launch_f<NT, MK, STORAGE_BF16>(tmap, args, plan, stream);
+        default: return fast_launch_f<NT, MK, STORAGE_FP32>(tmap, args, plan, stream);
+    }
 }
 
 }  // namespace
@@ -298,21 +336,21 @@ bool fast_path_applies(int metric, int power_law, int walls) {
     return !walls && !power_law && (metric == METRIC_UNIFORM || metric == METRIC_SEPARABLE);
 }
 
-cudaError_t fast_occupancy(int metric, int nt, int *occ, int *smem) {
+cudaError_t fast_occupancy(int metric, int storage, int nt, int *occ, int *smem) {
     if (nt == 256)
-        return metric == METRIC_UNIFORM ? fast_occupancy_t<256, METRIC_UNIFORM>(occ, smem)
-                                        : fast_occupancy_t<256, METRIC_SEPARABLE>(occ, smem);
-    return metric == METRIC_UNIFORM ? fast_occupancy_t<128, METRIC_UNIFORM>(occ, smem)
-                                    : fast_occupancy_t<128, METRIC_SEPARABLE>(occ, smem);
+        return metric == METRIC_UNIFORM ? fast_occupancy_s<256, METRIC_UNIFORM>(storage, occ, smem)
+                                        : fast_occupancy_s<256, METRIC_SEPARABLE>(storage, occ, smem);
+    return metric == METRIC_UNIFORM ? fast_occupancy_s<128, METRIC_UNIFORM>(storage, occ, smem)
+                                    : fast_occupancy_s<128, METRIC_SEPARABLE>(storage, occ, smem);
 }
 
-cudaError_t fast_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
-                        cudaStream_t stream) {
+cudaError_t fast_launch(const CUtensorMap *tmap, const StepArgs &args, int metric,
+                        const StepPlan &plan, cudaStream_t stream) {
     if (plan.NT == 256)
-        return metric == METRIC_UNIFORM ? fast_launch_f<256, METRIC_UNIFORM>(tmap, args, plan, stream)
-                                        : fast_launch_f<256, METRIC_SEPARABLE>(tmap, args, plan, stream);
-    return metric == METRIC_UNIFORM ? fast_launch_f<128, METRIC_UNIFORM>(tmap, args, plan, stream)
-                                    : fast_launch_f<128, METRIC_SEPARABLE>(tmap, args, plan, stream);
+        return metric == METRIC_UNIFORM ? fast_launch_s<256, METRIC_UNIFORM>(tmap, args, plan, stream)
+                                        : fast_launch_s<256, METRIC_SEPARABLE>(tmap, args, plan, stream);
+    return metric == METRIC_UNIFORM ? fast_launch_s<128, METRIC_UNIFORM>(tmap, args, plan, stream)
+                                    : fast_launch_s<128, METRIC_SEPARABLE>(tmap, args, plan, stream);
 }
 
 }  // namespace mdf

@@ -52,7 +52,11 @@ class BC(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("cfl", ctypes.c_double), ("eta", ctypes.c_double),
-                ("s_ratio", ctypes.c_double)]
+                ("s_ratio", ctypes.c_double), ("storage", ctypes.c_int)]
+
+
+# mdf_params.storage: how the state is kept between steps (arithmetic is FP32)
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 
 
 # (name, restype, argtypes) of every entry point declared in include/mdf.h
@@ -148,7 +152,7 @@ class _Arr:
 
 def problem_structs(nx, ny, nu=0.01, grid="uniform", lx=1.0, ly=1.0, x=None, y=None, power_law=None,
                     walls=(False, False), u_wall=(0, 0, 0, 0), v_wall=(0, 0, 0, 0), c=1.0, cfl=0.5, eta=0.8,
-                    s_ratio=1.5):
+                    s_ratio=1.5, storage="fp32"):
     """The C structs (mdf_grid, mdf_fluid, mdf_bc, mdf_params) of one problem,
     plus the arrays they point to (keep them alive while the structs are used)."""
     keep = []
@@ -167,7 +171,9 @@ def problem_structs(nx, ny, nu=0.01, grid="uniform", lx=1.0, ly=1.0, x=None, y=N
         b.type[k] = 1 if walls[0 if k < 2 else 1] else 0
         b.u_wall[k] = u_wall[k]
         b.v_wall[k] = v_wall[k]
-    p = Params(c, cfl, eta, s_ratio)
+    if storage not in STORAGE:
+        raise ValueError("storage must be one of %s" % sorted(STORAGE))
+    p = Params(c, cfl, eta, s_ratio, STORAGE[storage])
     return g, f, b, p, keep
 
 
@@ -178,19 +184,21 @@ class Solver:
     ("uniform" | "separable" | "curvilinear"), lx, ly, x, y, power_law
     (K, n, nu_min, nu_max), walls (x_walls, y_walls), u_wall, v_wall
     (west, east, south, north), c, cfl, eta, s_ratio, force (None, (fx, fy)
-    constants or (Fx, Fy) fields).
+    constants or (Fx, Fy) fields), and storage ("fp32", or "fp16" / "bf16":
+    u, v, P in FP32 plus the non-equilibrium part in 16 bits; periodic
+    Newtonian problems on uniform or separable grids only).
     """
 
     def __init__(self, nx, ny, nu=0.01, grid="uniform", lx=1.0, ly=1.0, x=None, y=None,
                  power_law=None, walls=(False, False), u_wall=(0, 0, 0, 0), v_wall=(0, 0, 0, 0),
-                 c=1.0, cfl=0.5, eta=0.8, s_ratio=1.5, force=None, stream=None, _handle=None):
+                 c=1.0, cfl=0.5, eta=0.8, s_ratio=1.5, force=None, stream=None, storage="fp32", _handle=None):
         self.nx, self.ny = nx, ny
         self._owned = _handle is None
         if _handle is not None:  # a problem of a batch: the batch owns the context
             self._h = _handle
             return
         g, f, b, p, self._keep = problem_structs(nx, ny, nu, grid, lx, ly, x, y, power_law, walls, u_wall, v_wall,
-                                                 c, cfl, eta, s_ratio)
+                                                 c, cfl, eta, s_ratio, storage)
         h = ctypes.c_void_p()
         _check(lib().mdf_create(ctypes.byref(g), ctypes.byref(f), ctypes.byref(b), ctypes.byref(p), ctypes.byref(h)))
         self._h = h

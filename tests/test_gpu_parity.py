@@ -163,6 +163,19 @@ def test_separable_periodic_channel():
     assert maxabs(sg, so) <= 1e-5 * (1e-4 / (8 * 0.01))
 
 
+def test_separable_periodic_stretched_axis_with_force_field():
+    """Both axes periodic, y nodes smoothly stretched (periodic metric
+    continuation across the seam), forcing-field variant of the fast path."""
+    nx, ny, nu, u0 = 48, 40, 0.01, 0.05
+    j = np.arange(ny)
+    y = j / ny + 0.02 * np.sin(2 * np.pi * j / ny) / (2 * np.pi)
+    _, _, _, Fx, Fy, _ = W.periodic_flow(nx, ny, u0=u0, nu=nu)
+    kw = dict(nu=nu, grid="separable", x=W.periodic_nodes(nx, 1.0), y=y, lx=1.0, ly=1.0, force=(Fx, Fy))
+    g, o = pair(nx, ny, **kw)
+    sg, so = run_both(g, o, W.zeros(nx, ny), 500)
+    assert maxabs(sg, so) <= 1e-5 * u0
+
+
 # ---------------------------------------------------------------- power law
 
 
