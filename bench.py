@@ -255,6 +255,38 @@ def batch_benchmark(mdf, torch, stream, steps=200, solo_sample=16):
             "speedup_vs_one_launch_per_problem": batch_mlups / solo_mlups}
 
 
+def storage_benchmark(mdf, W, torch, stream, ref_solver, nx, steps=500, warmup=20):
+    """The same Taylor-Green workload with 16-bit deviation storage (FP32
+    u, v, P plus the non-equilibrium part in FP16 / BF16): device-timed
+    MLUPS, achieved bandwidth of the algorithmic bytes, and the largest
+    velocity deviation from the FP32 run after the same steps."""
+    u, v, p = W.taylor_green(nx, U0)
+    ref_solver.init(u, v, p)
+    ref_solver.step(warmup + steps)
+    u32 = ref_solver.fields(["u"])["u"]
+    peak, _ = measured_peaks()
+    out = {}
+    for mode in ("fp16", "bf16"):
+        s = mdf.Solver(nx, nx, nu=NU, lx=2 * math.pi, ly=2 * math.pi, stream=stream, storage=mode)
+        s.init(u, v, p)
+        s.step(warmup)
+        s.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        bpn = s.bytes_per_node()
+        gbs = bpn * nx * nx / (ms / 1e3) / 1e9
+        du = float(abs(s.fields(["u"])["u"].astype("float64") - u32).max())
+        out[mode] = {"mlups": nx * nx / (ms / 1e3) / 1e6, "ms_per_step": ms, "bytes_per_node": bpn,
+                     "achieved_gbs": gbs, "frac": gbs / peak, "max_du_vs_fp32_over_U0": du / U0,
+                     "steps": warmup + steps, "launch": s.launch_info()}
+        del s
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -291,6 +323,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-residual", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-storage", action="store_true", help="skip the 16-bit storage runs")
     ap.add_argument("--launch", default=None,
                     help="threads,rows_per_block: pin the launch plan instead of the autotuned one (profiling)")
     ap.add_argument("--nx", type=int, default=NX,
@@ -365,6 +398,9 @@ def main():
     e2e_sec = time.perf_counter() - t0
     e2e_val = job_mlups(nodes, e2e_steps, world, max_over_ranks(e2e_sec, world, "cuda"))
 
+    # ---- 16-bit deviation storage on the same workload
+    storage = None if args.no_storage else storage_benchmark(mdf, W, torch, stream, solver, nx)
+
     # ---- batched sweep: many cavities, one launch per step
     batch = None if args.no_batch else batch_benchmark(mdf, torch, stream)
 
@@ -401,6 +437,7 @@ def main():
         "check": {"residual": r, "drift_u": drift[0], "drift_v": drift[1]},
         "time_to_residual": ttr,
         "batch": batch,
+        "storage": storage,
     }
     if ttr and cpu:
         for k in ttr:
