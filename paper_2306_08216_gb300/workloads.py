@@ -13,6 +13,10 @@ Problems (arXiv:2306.08216 Sec. 4 unless noted):
   cavity         Sec. 4.4, lid-driven square cavity, lid speed u0
 Grids: uniform, tanh-stretched (separable) and a trapezoid mapped from the
 unit square (curvilinear).
+
+Warm-start network inputs (the network is the project's extension, not the
+paper's): seeded initial parameters, the four input planes of a cavity
+(Re, power-law index, node coordinates) and seeded (Re, n) draws.
 """
 import math
 
@@ -151,3 +155,51 @@ def cavity_batch_draws(count, seed=2306):
     n = rng.uniform(0.5, 1.5, size=count)
     sides = rng.choice(np.array([65, 129, 257, 513]), size=count)
     return re, n, sides
+
+
+# ---------------------------------------------------------------- warm start
+
+WARM_RE_RANGE = (100.0, 1000.0)
+WARM_N_RANGE = (0.5, 1.5)
+
+
+def warm_start_draws(count, seed):
+    """Seeded power-law cavity parameters: Re log-uniform in [100, 1000],
+    index n uniform in [0.5, 1.5]."""
+    rng = np.random.default_rng(seed)
+    re = np.exp(rng.uniform(math.log(WARM_RE_RANGE[0]), math.log(WARM_RE_RANGE[1]), size=count))
+    n = rng.uniform(WARM_N_RANGE[0], WARM_N_RANGE[1], size=count)
+    return re, n
+
+
+def warm_start_inputs(re, n_index, R):
+    """Input planes [B][4][R][R] (float32) of the warm-start network: the
+    scaled log Reynolds number and power-law index (each mapped to [-1, 1]
+    over the training ranges) and the node coordinates x_i = i/(R-1),
+    y_j = j/(R-1) of the square cavity."""
+    re = np.atleast_1d(np.asarray(re, dtype=np.float64))
+    n_index = np.atleast_1d(np.asarray(n_index, dtype=np.float64))
+    lo, hi = math.log(WARM_RE_RANGE[0]), math.log(WARM_RE_RANGE[1])
+    a = 2.0 * (np.log(re) - lo) / (hi - lo) - 1.0
+    b = 2.0 * (n_index - WARM_N_RANGE[0]) / (WARM_N_RANGE[1] - WARM_N_RANGE[0]) - 1.0
+    X, Y = np.meshgrid(np.arange(R) / (R - 1.0), np.arange(R) / (R - 1.0))
+    out = np.empty((re.size, 4, R, R), dtype=np.float32)
+    out[:, 0] = a[:, None, None]
+    out[:, 1] = b[:, None, None]
+    out[:, 2] = X
+    out[:, 3] = Y
+    return out
+
+
+def net_init_params(shapes, seed, out_gain=0.1):
+    """Seeded initial parameters of a stack of 3 x 3 convolutions, flat
+    float32 in the order of `shapes` = [(name, cout, cin), ...]: weights
+    [cout][3][3][cin] normal with std sqrt(2 / (9 cin)) (He), scaled by
+    out_gain on the last layer, then zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i, (_, co, ci) in enumerate(shapes):
+        std = math.sqrt(2.0 / (9.0 * ci)) * (out_gain if i == len(shapes) - 1 else 1.0)
+        parts.append((std * rng.standard_normal(co * 9 * ci)).astype(np.float32))
+        parts.append(np.zeros(co, dtype=np.float32))
+    return np.concatenate(parts)
