@@ -59,7 +59,7 @@ class Params(ctypes.Structure):
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 
 
-# (name, restype, argtypes) of every entry point declared in include/mdf.h
+# (name, restype, argtypes) of every entry point declared in include/*.h
 _SIGNATURES = [
     ("mdf_create", ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Fluid), ctypes.POINTER(BC),
                                   ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]),
@@ -96,6 +96,22 @@ _SIGNATURES = [
     ("mdf_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("mdf_residual_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
+    # include/mdf_net.h (warm-start network)
+    ("mdf_net_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    ("mdf_net_destroy", None, [ctypes.c_void_p]),
+    ("mdf_net_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("mdf_net_param_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("mdf_net_layer_count", ctypes.c_int, [ctypes.c_void_p]),
+    ("mdf_net_layer_shape", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("mdf_net_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("mdf_net_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("mdf_net_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int]),
+    ("mdf_net_gradient", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, _D,
+                                        ctypes.c_void_p, ctypes.c_int]),
+    ("mdf_net_train_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_double, _D, ctypes.c_int]),
+    ("mdf_net_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
 
 _lib = None

@@ -21,7 +21,8 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(os.path.join(ROOT, "include", h)).read() for h in sorted(os.listdir(os.path.join(ROOT, "include")))
+                   if h.endswith(".h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = re.findall(r"\b(mdf_[a-z0-9_]+)\s*\(", text)
     return sorted(set(names))
@@ -122,3 +123,12 @@ def test_storage_names():
     assert mdf.STORAGE == {"fp32": 0, "fp16": 1, "bf16": 2}
     with pytest.raises(ValueError):
         mdf.problem_structs(8, 8, storage="fp8")
+
+
+def test_net_create_rejects_bad_arguments_before_any_cuda_call(lib):
+    h = ctypes.c_void_p()
+    assert lib.mdf_net_create(12, 1, ctypes.byref(h)) == mdf.MDF_E_INVALID   # R % 8 != 0
+    assert lib.mdf_net_create(8, 0, ctypes.byref(h)) == mdf.MDF_E_INVALID    # empty batch
+    assert lib.mdf_net_create(16, 1, None) == mdf.MDF_E_INVALID
+    assert lib.mdf_net_last_error(None)
+    assert lib.mdf_net_param_count(None) == -1
