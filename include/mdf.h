@@ -244,6 +244,13 @@ mdf_status mdf_batch_step(mdf_batch *batch, int n);
  * MDF_OK, MDF_E_DIVERGED or MDF_E_STATE.  Synchronises; returns
  * MDF_E_DIVERGED if any problem diverged (the others keep running). */
 mdf_status mdf_batch_residual(mdf_batch *batch, double *residual, int *status);
+/* Retire (active = 0) or re-admit (active = 1) problem `index`: a retired
+ * problem keeps its state and step count, takes no work in later batch
+ * steps and reports MDF_E_STATE with a NaN residual from
+ * mdf_batch_residual; the work items (and band heights) are rebuilt over the
+ * remaining problems.  Lets a sweep stop paying for problems that have
+ * converged or diverged.  Waits for the batch's streams. */
+mdf_status mdf_batch_set_active(mdf_batch *batch, int index, int active);
 /* The context of problem `index` (owned by the batch): use it with
  * mdf_fields, mdf_get_distributions, mdf_dt, ...; do not step or destroy it. */
 mdf_status mdf_batch_problem(mdf_batch *batch, int index, mdf_ctx **ctx);

@@ -23,7 +23,7 @@ using namespace mdf;
 
 namespace {
 constexpr int kBatchNT = 128;     // block size of the general march
-constexpr int kBandRows = 128;    // target rows per work item
+constexpr int kBandRows = 128;    // longest band (rows per work item)
 constexpr int kGraphSteps = 16;   // launches per captured graph (even: parity returns)
 }  // namespace
 
@@ -43,6 +43,9 @@ struct mdf_batch {
     double *h_res = nullptr;                       // pinned, 5 doubles per problem
     std::vector<int> H;                            // rows per work item of each problem
     std::vector<int> seen_version;                 // args_version of each context last uploaded
+    std::vector<char> active;                      // problems that step (mdf_batch_set_active)
+    std::vector<CUtensorMap> h_maps[2];            // host copies of d_maps
+    int num_sms = 0, items_cap = 0;
     long long steps = 0;
     long long nodes = 0;
     char last_error[256] = {0};
@@ -130,6 +133,58 @@ static mdf_status build_graph(mdf_batch *b, int parity) {
     return MDF_OK;
 }
 
+// Work items of the active problems, largest problems first, with band
+// heights sized to the active work: a band of H rows costs H + 9 row
+// iterations (halo), so long bands are cheapest when there is enough work to
+// fill every resident block; a small batch instead gets bands short enough
+// that its items cover the grid (one item per block, at least 8 rows).
+static mdf_status build_items(mdf_batch *b) {
+    const int count = b->count;
+    const int W = kBatchNT - 8;
+    long long strip_rows = 0;
+    for (int i = 0; i < count; ++i)
+        if (b->active[i]) strip_rows += (long long)((b->ctx[i]->nx + W - 1) / W) * b->ctx[i]->ny;
+    const long long slots = (long long)std::max(1, b->occ) * b->num_sms;
+    const int band_target = (int)std::max(8ll, std::min((long long)kBandRows, (strip_rows + slots - 1) / slots));
+    for (int i = 0; i < count; ++i) {
+        const int ny = b->ctx[i]->ny;
+        const int bands = (ny + band_target - 1) / band_target;
+        int H = (ny + bands - 1) / bands;
+        if (H < 8) H = 8;
+        b->H[i] = H;
+    }
+    std::vector<int> order;
+    for (int i = 0; i < count; ++i)
+        if (b->active[i]) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (long long)b->ctx[x]->nx * b->ctx[x]->ny > (long long)b->ctx[y]->nx * b->ctx[y]->ny;
+    });
+    std::vector<BatchItem> items;
+    for (int i : order) {
+        mdf_ctx *c = b->ctx[i];
+        const int gx = (c->nx + W - 1) / W;
+        const int gy = (c->ny + b->H[i] - 1) / b->H[i];
+        for (int by = 0; by < gy; ++by)
+            for (int bx = 0; bx < gx; ++bx) items.push_back(BatchItem{i, bx, by, 0});
+    }
+    b->nitems = (int)items.size();
+    b->grid = std::min(b->nitems, std::max(1, b->occ) * b->num_sms);
+    if (b->nitems > b->items_cap) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        b->items_cap = 0;
+        BCK(b, cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem)));
+        b->items_cap = b->nitems;
+    }
+    if (b->nitems)
+        BCK(b, cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+    for (int p = 0; p < 2; ++p) {
+        if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
+        b->graph[p] = nullptr;
+    }
+    return MDF_OK;
+}
+
 extern "C" {
 
 mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *fluids, const mdf_bc *bcs,
@@ -179,45 +234,21 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
     BCKE(batch_occupancy(metric, power_law, walls, &nt, &b->occ, &b->smem));
     BCKE(cudaGetDevice(&dev));
     BCKE(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
-    // work items, largest problems first
-    std::vector<int> order(count);
-    for (int i = 0; i < count; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        return (long long)b->ctx[x]->nx * b->ctx[x]->ny > (long long)b->ctx[y]->nx * b->ctx[y]->ny;
-    });
-    std::vector<BatchItem> items;
-    std::vector<CUtensorMap> maps[2];
-    for (int p = 0; p < 2; ++p) maps[p].resize(count);
+    b->num_sms = num_sms;
     b->H.resize(count);
     b->seen_version.resize(count);
+    b->active.assign(count, 1);
+    for (int p = 0; p < 2; ++p) b->h_maps[p].resize(count);
     for (int i = 0; i < count; ++i) {
-        mdf_ctx *c = b->ctx[i];
-        const int bands = (c->ny + kBandRows - 1) / kBandRows;
-        int H = (c->ny + bands - 1) / bands;
-        if (H < 8) H = 8;
-        b->H[i] = H;
         CUtensorMap m[2];
-        BCKC(ctx_encode_maps(c, kBatchNT, m));
-        for (int p = 0; p < 2; ++p) maps[p][i] = m[p];
+        BCKC(ctx_encode_maps(b->ctx[i], kBatchNT, m));
+        for (int p = 0; p < 2; ++p) b->h_maps[p][i] = m[p];
     }
-    for (int oi = 0; oi < count; ++oi) {
-        const int i = order[oi];
-        mdf_ctx *c = b->ctx[i];
-        const int W = kBatchNT - 8;
-        const int gx = (c->nx + W - 1) / W;
-        const int H = b->H[i];
-        const int gy = (c->ny + H - 1) / H;
-        for (int by = 0; by < gy; ++by)
-            for (int bx = 0; bx < gx; ++bx) items.push_back(BatchItem{i, bx, by, 0});
-    }
-    b->nitems = (int)items.size();
-    b->grid = std::min(b->nitems, std::max(1, b->occ) * num_sms);
-    BCKE(cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem)));
-    BCKE(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+    BCKC(build_items(b));
     for (int p = 0; p < 2; ++p) {
         BCKE(cudaMalloc(&b->d_args[p], count * sizeof(StepArgs)));
         BCKE(cudaMalloc(&b->d_maps[p], count * sizeof(CUtensorMap)));
-        BCKE(cudaMemcpy(b->d_maps[p], maps[p].data(), count * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+        BCKE(cudaMemcpy(b->d_maps[p], b->h_maps[p].data(), count * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
     }
     BCKC(upload_args(b));
     BCKE(cudaMallocHost(&b->h_res, (size_t)count * 5 * sizeof(double)));
@@ -272,6 +303,7 @@ mdf_status mdf_batch_step(mdf_batch *b, int n) {
             if (s != MDF_OK) return s;
             break;
         }
+    if (b->nitems == 0) return MDF_OK;  // every problem retired
     int done = 0;
     const int reps = n / kGraphSteps;
     if (reps >= 2) {
@@ -291,16 +323,42 @@ mdf_status mdf_batch_step(mdf_batch *b, int n) {
     mdf_status s = launch_steps(b, b->stream, n - done);
     if (s != MDF_OK) return s;
     b->steps += n;
-    for (mdf_ctx *c : b->ctx) {
-        c->cur = b->cur;
-        c->steps += n;
-    }
+    for (int i = 0; i < b->count; ++i)
+        if (b->active[i]) {
+            b->ctx[i]->cur = b->cur;
+            b->ctx[i]->steps += n;
+        }
     return MDF_OK;
+}
+
+mdf_status mdf_batch_set_active(mdf_batch *b, int index, int active) {
+    if (!b || index < 0 || index >= b->count) return b ? bfail(b, MDF_E_INVALID, "bad index") : MDF_E_INVALID;
+    active = active ? 1 : 0;
+    if (b->active[index] == active) return MDF_OK;
+    BCK(b, cudaStreamSynchronize(b->stream));
+    BCK(b, cudaStreamSynchronize(b->cstream));
+    mdf_ctx *c = b->ctx[index];
+    if (active && c->cur != b->cur) {
+        // the batch reads buffer `cur` of every problem: give this problem's
+        // current state that role by exchanging its two buffers
+        std::swap(c->buf[0], c->buf[1]);
+        std::swap(c->tmap[0], c->tmap[1]);
+        std::swap(b->h_maps[0][index], b->h_maps[1][index]);
+        c->cur = b->cur;
+        for (int p = 0; p < 2; ++p)
+            BCK(b, cudaMemcpy(b->d_maps[p] + index, &b->h_maps[p][index], sizeof(CUtensorMap),
+                              cudaMemcpyHostToDevice));
+    }
+    b->active[index] = (char)active;
+    mdf_status s = build_items(b);
+    if (s != MDF_OK) return s;
+    return upload_args(b);
 }
 
 mdf_status mdf_batch_residual(mdf_batch *b, double *residual, int *status) {
     if (!b || !residual) return b ? bfail(b, MDF_E_INVALID, "residual is NULL") : MDF_E_INVALID;
     for (int i = 0; i < b->count; ++i) {
+        if (!b->active[i]) continue;
         mdf_ctx *c = b->ctx[i];
         BCK(b, aux_residual(c->aux, c->buf[c->cur], c->snap_u, c->snap_v, c->partials, c->result, b->stream));
         BCK(b, cudaMemcpyAsync(b->h_res + 5 * i, c->result, 5 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
@@ -309,6 +367,11 @@ mdf_status mdf_batch_residual(mdf_batch *b, double *residual, int *status) {
     if (s != MDF_OK) return bfail(b, s, "%s", mdf_last_error(b->ctx[0]));
     int any_diverged = 0;
     for (int i = 0; i < b->count; ++i) {
+        if (!b->active[i]) {
+            residual[i] = NAN;
+            if (status) status[i] = MDF_E_STATE;
+            continue;
+        }
         mdf_ctx *c = b->ctx[i];
         const double *r = b->h_res + 5 * i;
         const long long window = c->steps - c->snap_step;

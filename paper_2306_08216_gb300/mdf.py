@@ -92,6 +92,7 @@ _SIGNATURES = [
     ("mdf_batch_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("mdf_batch_residual", ctypes.c_int, [ctypes.c_void_p, _D, ctypes.POINTER(ctypes.c_int)]),
     ("mdf_batch_problem", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    ("mdf_batch_set_active", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     ("mdf_batch_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
     ("mdf_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("mdf_residual_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
@@ -410,6 +411,10 @@ class Batch:
         if st not in (MDF_OK, MDF_E_DIVERGED):
             self._chk(st)
         return np.array(r[:]), np.array(s[:])
+
+    def set_active(self, index, active):
+        """Retire (False) or re-admit (True) problem `index`."""
+        self._chk(lib().mdf_batch_set_active(self._h, int(index), 1 if active else 0))
 
     def problem(self, index):
         h = ctypes.c_void_p()

@@ -100,3 +100,37 @@ def test_batch_rejects_mixed_kernel_variants():
     with pytest.raises(mdf.MdfError) as e:
         mdf.Batch([cavity(33, 100), cavity(33, 100, 0.7)])
     assert e.value.status == mdf.MDF_E_INVALID
+
+
+def _solo_state(kw, steps):
+    kw = dict(kw)
+    nx, ny = kw.pop("nx"), kw.pop("ny")
+    solo = mdf.Solver(nx, ny, **kw)
+    solo.init(*W.zeros(nx, ny))
+    solo.step(steps)
+    return solo.state()
+
+
+def test_retired_problems_freeze_and_resume_bitwise():
+    """A retired problem keeps its state while the others advance; re-admitted
+    after an odd number of batch steps (its buffers swap roles), it continues
+    exactly as if it had been stepped alone."""
+    probs = [cavity(65, 400, 0.8), cavity(40, 100, 1.2), cavity(33, 250, 1.0)]
+    batch = mdf.Batch(probs)
+    batch.step(20)
+    batch.set_active(1, False)
+    batch.step(37)  # odd: the batch parity now differs from problem 1's
+    r, st = batch.residual()
+    assert st[1] == mdf.MDF_E_STATE and np.isnan(r[1])
+    assert st[0] == mdf.MDF_OK and st[2] == mdf.MDF_OK
+    np.testing.assert_array_equal(batch.problem(1).state(), _solo_state(probs[1], 20))
+    np.testing.assert_array_equal(batch.problem(0).state(), _solo_state(probs[0], 57))
+    batch.set_active(1, True)
+    batch.step(35)
+    np.testing.assert_array_equal(batch.problem(1).state(), _solo_state(probs[1], 55))
+    np.testing.assert_array_equal(batch.problem(2).state(), _solo_state(probs[2], 92))
+    assert batch.problem(1).steps == 55 and batch.problem(2).steps == 92
+    for i in range(3):
+        batch.set_active(i, False)
+    batch.step(10)  # nothing left to step
+    np.testing.assert_array_equal(batch.problem(2).state(), _solo_state(probs[2], 92))
