@@ -106,6 +106,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def finite_json(x):
+    """The bench line as strict JSON: non-finite floats (a residual never
+    reached, a diverged problem) become null."""
+    if isinstance(x, float):
+        return x if math.isfinite(x) else None
+    if isinstance(x, dict):
+        return {k: finite_json(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [finite_json(v) for v in x]
+    return x
+
+
 def max_over_ranks(x, world, device="cpu"):
     """Max of a per-rank scalar over all ranks (identity for one rank)."""
     if world <= 1:
@@ -287,6 +299,29 @@ def storage_benchmark(mdf, W, torch, stream, ref_solver, nx, steps=500, warmup=2
     return out
 
 
+def warm_start_benchmark(stream, count=16, target=1e-8, max_steps=130_000):
+    """Learned warm start + batching against cold starts: `count` held-out
+    power-law cavities (128 x 128 nodes, the draws the shipped network was
+    not trained on) marched to residual `target` from rest and from the
+    network's prediction, each set as one batch that retires problems as
+    they converge, plus the cold march one launch per problem extrapolated
+    from the single-cavity step time."""
+    import os
+
+    from paper_2306_08216_gb300 import warmstart as WS
+    from paper_2306_08216_gb300 import workloads as W
+    R = 128
+    net = WS.Net(R, count)
+    net.load(os.path.join(WS.WEIGHTS_DIR, "warmstart_cavity_R128.npy"))
+    re, nn = W.warm_start_draws(64, 2)
+    out = WS.warm_vs_cold(net, re[:count], nn[:count], R, target=target, max_steps=max_steps, stream=stream,
+                          log=None)
+    net.close()
+    out["workload"] = ("%d held-out power-law lid-driven cavities, 128x128 nodes, Re log-uniform [100,1000], "
+                       "n uniform [0.5,1.5], seed 2" % count)
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -324,6 +359,7 @@ def main():
     ap.add_argument("--no-time-to-residual", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-storage", action="store_true", help="skip the 16-bit storage runs")
+    ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start comparison")
     ap.add_argument("--launch", default=None,
                     help="threads,rows_per_block: pin the launch plan instead of the autotuned one (profiling)")
     ap.add_argument("--nx", type=int, default=NX,
@@ -404,6 +440,9 @@ def main():
     # ---- batched sweep: many cavities, one launch per step
     batch = None if args.no_batch else batch_benchmark(mdf, torch, stream)
 
+    # ---- learned warm start + batching against cold starts
+    warm = None if args.no_warm_start else warm_start_benchmark(stream)
+
     # ---- time to residual 1e-8 from rest: lid-driven cavity, Re = 1000, 257^2
     ttr = None
     if not args.no_time_to_residual:
@@ -438,11 +477,12 @@ def main():
         "time_to_residual": ttr,
         "batch": batch,
         "storage": storage,
+        "warm_start": warm,
     }
     if ttr and cpu:
         for k in ttr:
             ttr[k]["cpu_oracle_seconds_extrapolated"] = ttr[k]["steps"] * CAV_N * CAV_N / (cpu["value"] * 1e6)
-    print(json.dumps(line), flush=True)
+    print(json.dumps(finite_json(line), allow_nan=False), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -122,7 +122,7 @@ def loss_and_grad(params, x, target):
     y = forward_tensors(P, torch.as_tensor(np.asarray(x, dtype=np.float64)))
     loss = ((y - torch.as_tensor(np.asarray(target, dtype=np.float64))) ** 2).mean()
     loss.backward()
-    return float(loss), p.grad.numpy().copy()
+    return float(loss.detach()), p.grad.numpy().copy()
 
 
 def unpack_tensor(p):
