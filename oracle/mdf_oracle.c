@@ -46,7 +46,18 @@
  *     gdot = sqrt(2 S:S), S from the non-equilibrium first moment
  *     (Eqs. 2.4.1, 2.4.3), solved per node from fhat(t) and clamped to
  *     [nu_min, nu_max]; the rates so found serve the whole step at that node.
- *   - Source R = 0 and dF/dt = 0 for every workload.
+ *   - Source R of the continuity equation (Eq. 2.1.1) enters only the
+ *     pressure, P = (sum c f + (cs^2/s_1) R - |u|^2)/d (Eq. 2.3.23), with
+ *     s_1 = s = cs^2/nu.  Eq. 2.3.23 is stated for f; computed from fhat or
+ *     fbar, whose non-equilibrium first moments are (1 + dt s/2) and
+ *     (1 + h s/2) times that of f, the R term takes the same factor
+ *     (see moments_rk).  Newtonian fluids only (with a power-law viscosity
+ *     nu would depend on P through the trace of the non-equilibrium moment).  The alpha = 0 equation is not evolved
+ *     (Remark 1: it influences neither u nor P), and the G source is
+ *     dropped (Remark 2).
+ *   - dF/dt enters Step 4 as dt^2/2 w_j dF/dt (Eq. 2.3.24); the h^2/2 term
+ *     of the fbar update is dropped (Remark 2).  R, F and dF/dt are set by
+ *     the caller (constants or fields) and may change between steps.
  * Parity unpinned: the curvilinear path for non-affine maps (trapezoid) has
  * no closed form to pin it; it is checked only through its affine and
  * separable special cases and grid refinement.
@@ -88,6 +99,8 @@ typedef struct {
     double *X, *Y;        /* node coordinates (kinds 1-2) */
     double *xi_x, *xi_y, *eta_x, *eta_y;
     double *Fx, *Fy;      /* body force per node */
+    double *dFx, *dFy;    /* its time derivative per node */
+    double *Rs;           /* source R of Eq. 2.1.1 per node */
     double *fh, *fhp, *fbp, *fb, *f, *fn;  /* 10 planes each */
     double *s_node;       /* per-node first-moment rate s */
     double Minv[Q][Q], M[Q][Q];
@@ -218,10 +231,15 @@ static inline long idx(const orc_ctx *o, int a, int j, int x, int y) {
     return ((long)(a * Q + j) * o->ny + y) * o->nx + x;
 }
 
-/* Zeroth moments ubar_alpha and pressure P of Eq. 2.3.23 (R = 0) from a
- * distribution g (fhat, fbar or f give the same values). */
-static void moments(const orc_ctx *o, const double *g, int x, int y,
-                    double *u, double *v, double *P) {
+/* Zeroth moments ubar_alpha and pressure P of Eq. 2.3.23 from a
+ * distribution g.  Eq. 2.3.23 holds for f, whose non-equilibrium first
+ * moment has trace -(cs^2/s) R (Eq. 2.3.22).  fhat and fbar carry that
+ * moment scaled by 1 + dt s/2 and 1 + h s/2 (Eqs. 2.2.2 and 2.2.16: Lt acts
+ * on the first moments with rate s), so the R term takes the same factor:
+ * rk = (cs^2/s)(1 + k s/2) = nu + cs^2 k/2 with k = dt (fhat), h (fbar) or
+ * 0 (f). */
+static void moments_rk(const orc_ctx *o, const double *g, int x, int y, double rk,
+                       double *u, double *v, double *P) {
     double ub[NA] = { 0, 0 };
     double first = 0.0;  /* sum_alpha sum_i c_{i,alpha} g_{i,alpha} */
     for (int a = 0; a < NA; ++a)
@@ -232,7 +250,12 @@ static void moments(const orc_ctx *o, const double *g, int x, int y,
         }
     *u = ub[0];
     *v = ub[1];
-    *P = (first - ub[0] * ub[0] - ub[1] * ub[1]) / 2.0;  /* d = 2 */
+    *P = (first + rk * o->Rs[(long)y * o->nx + x] - ub[0] * ub[0] - ub[1] * ub[1]) / 2.0;  /* d = 2 */
+}
+
+/* Moments of fhat (the stored state). */
+static void moments(const orc_ctx *o, const double *g, int x, int y, double *u, double *v, double *P) {
+    moments_rk(o, g, x, y, o->p.nu + o->cs2 * o->dt / 2.0, u, v, P);
 }
 
 /* Eq. 2.2.5: feq_{j,alpha} = w_j [ubar_alpha + c_j.(ubar_alpha u + P E_alpha)/cs2]. */
@@ -523,6 +546,9 @@ orc_ctx *orc_create(const orc_params *p) {
 
     o->Fx = alloc0(N);
     o->Fy = alloc0(N);
+    o->dFx = alloc0(N);
+    o->dFy = alloc0(N);
+    o->Rs = alloc0(N);
     for (long n = 0; n < N; ++n) {
         if (p->force_mode == 1) { o->Fx[n] = p->fx; o->Fy[n] = p->fy; }
         else if (p->force_mode == 2) { o->Fx[n] = p->force_x[n]; o->Fy[n] = p->force_y[n]; }
@@ -538,10 +564,31 @@ orc_ctx *orc_create(const orc_params *p) {
 void orc_destroy(orc_ctx *o) {
     if (!o) return;
     free(o->X); free(o->Y); free(o->xi_x); free(o->xi_y); free(o->eta_x); free(o->eta_y);
-    free(o->Fx); free(o->Fy);
+    free(o->Fx); free(o->Fy); free(o->dFx); free(o->dFy); free(o->Rs);
     free(o->fh); free(o->fhp); free(o->fbp); free(o->fb); free(o->f); free(o->fn);
     free(o->s_node);
     free(o);
+}
+
+/* Body force (mode 0 none, 1 constant, 2 field), its time derivative, and
+ * the source R (Newtonian only: returns -1 for a power-law fluid). */
+static void fill_pair(const orc_ctx *o, int mode, double cx, double cy, const double *Fx, const double *Fy,
+                      double *outx, double *outy) {
+    for (long n = 0; n < o->N; ++n) {
+        outx[n] = mode == 1 ? cx : mode == 2 ? Fx[n] : 0.0;
+        outy[n] = mode == 1 ? cy : mode == 2 ? Fy[n] : 0.0;
+    }
+}
+void orc_set_force(orc_ctx *o, int mode, double fx, double fy, const double *Fx, const double *Fy) {
+    fill_pair(o, mode, fx, fy, Fx, Fy, o->Fx, o->Fy);
+}
+void orc_set_force_rate(orc_ctx *o, int mode, double dfx, double dfy, const double *dFx, const double *dFy) {
+    fill_pair(o, mode, dfx, dfy, dFx, dFy, o->dFx, o->dFy);
+}
+int orc_set_source(orc_ctx *o, int mode, double r, const double *R) {
+    if (o->p.power_law && mode != 0) return -1;
+    for (long n = 0; n < o->N; ++n) o->Rs[n] = mode == 1 ? r : mode == 2 ? R[n] : 0.0;
+    return 0;
 }
 
 int orc_last_status(void) { return g_last_status; }
@@ -646,7 +693,7 @@ static void one_step(orc_ctx *o) {
                 step_matrices(o, o->s_node[n], A, Ab, L, L34, Ri, RL);
             } else { memcpy(Ri, o->Rinv, sizeof(Ri)); memcpy(RL, o->RL, sizeof(RL)); }
             double u, v, P, feq[NA][Q];
-            moments(o, o->fb, x, y, &u, &v, &P);
+            moments_rk(o, o->fb, x, y, o->p.nu + o->cs2 * h / 2.0, &u, &v, &P);
             equilibrium(o, u, v, P, feq);
             for (int a = 0; a < NA; ++a) {
                 double g[Q], t1[Q], t2[Q];
@@ -665,11 +712,13 @@ static void one_step(orc_ctx *o) {
             if (is_wall(o, x, y)) continue;
             long n = (long)y * nx + x;
             double Fa[NA] = { o->Fx[n], o->Fy[n] };
+            double dFa[NA] = { o->dFx[n], o->dFy[n] };
             for (int a = 0; a < NA; ++a)
                 for (int j = 0; j < Q; ++j) {
                     const double *plane = o->f + (long)(a * Q + j) * N;
                     double cg = (j == 0) ? 0.0 : c_dot_grad(o, plane, j, x, y);
-                    o->fn[idx(o, a, j, x, y)] = o->fhp[idx(o, a, j, x, y)] - dt * cg + dt * o->w[j] * Fa[a];
+                    o->fn[idx(o, a, j, x, y)] = o->fhp[idx(o, a, j, x, y)] - dt * cg + dt * o->w[j] * Fa[a] +
+                                                0.5 * dt * dt * o->w[j] * dFa[a];
                 }
         }
     apply_nee(o, o->fn);

@@ -80,6 +80,10 @@ def lib():
         L.orc_collision_matrix.argtypes = [ctypes.c_void_p, ctypes.c_double, _D]
         L.orc_lambda_matrix.argtypes = [ctypes.c_void_p, _D]
         L.orc_max_threads.restype = ctypes.c_int
+        L.orc_set_force.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]
+        L.orc_set_force_rate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]
+        L.orc_set_source.restype = ctypes.c_int
+        L.orc_set_source.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _D]
         _lib = L
     return _lib
 
@@ -102,12 +106,14 @@ class Oracle:
       u_wall, v_wall    4-tuples, west/east/south/north
       c, cfl, eta, s_ratio  lattice speed, CFL number, mixed-scheme weight, s'/s
       force             None, (fx, fy) constants, or (Fx[ny,nx], Fy[ny,nx])
+      force_rate        dF/dt in the same forms (Eq. 2.3.24)
+      source            R of Eq. 2.1.1: None, a constant or R[ny,nx]
     """
 
     def __init__(self, nx, ny, nu=0.01, grid="uniform", lx=1.0, ly=1.0, x=None, y=None,
                  power_law=None, walls=(False, False), u_wall=(0, 0, 0, 0),
                  v_wall=(0, 0, 0, 0), c=1.0, cfl=0.5, eta=0.8, s_ratio=1.5,
-                 force=None, threads=0):
+                 force=None, force_rate=None, source=None, threads=0):
         L = lib()
         p = OrcParams()
         p.nx, p.ny = nx, ny
@@ -147,6 +153,42 @@ class Oracle:
             raise ValueError("oracle rejected the parameters (status %d)" % L.orc_last_status())
         self._h = h
         self.nx, self.ny = nx, ny
+        if force_rate is not None:
+            self.set_force_rate(force_rate)
+        if source is not None:
+            self.set_source(source)
+
+    @staticmethod
+    def _pair(pair):
+        if pair is None:
+            return 0, 0.0, 0.0, None, None, []
+        if np.isscalar(pair[0]):
+            return 1, float(pair[0]), float(pair[1]), None, None, []
+        a = np.ascontiguousarray(pair[0], dtype=np.float64).ravel()
+        b = np.ascontiguousarray(pair[1], dtype=np.float64).ravel()
+        return 2, 0.0, 0.0, _ptr(a), _ptr(b), [a, b]
+
+    def set_force(self, force):
+        """Replace the body force (None, (fx, fy) or fields) before the next step."""
+        m, a, b, pa, pb, keep = self._pair(force)
+        lib().orc_set_force(self._h, m, a, b, pa, pb)
+
+    def set_force_rate(self, rate):
+        """dF/dt (None, (dfx, dfy) or fields) used by the next steps."""
+        m, a, b, pa, pb, keep = self._pair(rate)
+        lib().orc_set_force_rate(self._h, m, a, b, pa, pb)
+
+    def set_source(self, R):
+        """Source R of the continuity equation (None, a constant or a field)."""
+        if R is None:
+            st = lib().orc_set_source(self._h, 0, 0.0, None)
+        elif np.isscalar(R):
+            st = lib().orc_set_source(self._h, 1, float(R), None)
+        else:
+            a = np.ascontiguousarray(R, dtype=np.float64).ravel()
+            st = lib().orc_set_source(self._h, 2, 0.0, _ptr(a))
+        if st != 0:
+            raise ValueError("the source term needs a Newtonian fluid")
 
     def __del__(self):
         h = getattr(self, "_h", None)

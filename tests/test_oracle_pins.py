@@ -422,3 +422,70 @@ def test_power_law_poiseuille(n_index, K, G, c):
     y = W.wall_nodes(ny, 1.0)
     ue = W.power_law_poiseuille_exact(y, G, K, n_index)
     assert gre(o.fields()["u"][:, 0], ue) < 5e-3
+
+
+# ------------------------------------------------- source R and dF/dt terms
+
+
+def _manufactured_source_flow(nx, nu, c, with_source):
+    """Steady periodic flow u = U0 + a sin(kx), v = 0 with div u = R = u_x and
+    F_x = d(u^2)/dx - nu u_xx (then P is uniform); the oracle marched to
+    t = 25 (ten viscous times) from that state."""
+    ny, U0, a, k = 8, 0.05, 0.02, 2 * math.pi
+    X = np.tile(np.arange(nx) / nx, (ny, 1))
+    u = U0 + a * np.sin(k * X)
+    ux, uxx = a * k * np.cos(k * X), -a * k * k * np.sin(k * X)
+    o = Oracle(nx, ny, nu=nu, lx=1.0, ly=ny / nx, c=c, force=(2 * u * ux - nu * uxx, 0 * X),
+               source=ux if with_source else None)
+    o.init(u, 0 * u, 0 * u)
+    o.step(int(25.0 / o.dt))
+    f = o.fields()
+    return np.abs(f["u"] - u).max() / a, np.abs(f["div"] - ux).max() / (a * k)
+
+
+def test_source_term_sets_the_divergence():
+    """Eq. 2.3.23 with R: the steady state of a flow with div u = R matches
+    the manufactured solution up to the D2Q5 kinetic error, which falls as
+    1/c^2 and does not depend on the grid; without R the pressure enforces
+    div u = 0 and the flow misses the solution entirely."""
+    e1, d1 = _manufactured_source_flow(32, 0.01, 1.0, True)
+    e2, d2 = _manufactured_source_flow(32, 0.01, 2.0, True)
+    e2f, _ = _manufactured_source_flow(64, 0.01, 2.0, True)
+    e0, d0 = _manufactured_source_flow(32, 0.01, 1.0, False)
+    assert d1 < 1e-12 and d2 < 1e-12   # the first-moment divergence equals R
+    assert e1 < 0.03 and e2 < 0.01
+    assert 3.0 < e1 / e2 < 5.0          # kinetic error ~ 1/c^2
+    assert abs(e2f - e2) < 0.2 * e2     # not a grid error
+    assert e0 > 0.9 and d0 > 0.99       # without R: div u = 0, u far off
+
+
+def test_force_rate_term_gives_second_order_time_accuracy():
+    """Uniform flow under F_x = F0 cos(w t): u' = F(t) exactly (no gradients),
+    so the update is a Taylor step.  With the dt^2/2 dF/dt term of Eq. 2.3.24
+    the error at a fixed time falls 4x per halving of dt; without it 2x."""
+    n, F0, T = 8, 1e-3, 2.0
+    w = 2 * math.pi / T
+
+    def error(cfl, rate):
+        o = Oracle(n, n, nu=0.01, lx=1.0, ly=1.0, cfl=cfl)
+        o.init(*W.zeros(n, n))
+        steps = int(round(0.75 * T / o.dt))
+        for k in range(steps):
+            t = k * o.dt
+            o.set_force((F0 * math.cos(w * t), 0.0))
+            o.set_force_rate((-F0 * w * math.sin(w * t), 0.0) if rate else None)
+            o.step(1)
+        return float(np.abs(o.fields()["u"] - F0 / w * math.sin(w * steps * o.dt)).max())
+
+    with_rate = [error(c, True) for c in (0.4, 0.2, 0.1)]
+    without = [error(c, False) for c in (0.4, 0.2, 0.1)]
+    for e in (with_rate, without):
+        assert e[0] > e[1] > e[2]
+    assert all(3.6 < with_rate[i] / with_rate[i + 1] < 4.4 for i in range(2))
+    assert all(1.8 < without[i] / without[i + 1] < 2.2 for i in range(2))
+
+
+def test_source_needs_a_newtonian_fluid():
+    o = Oracle(16, 16, nu=0.01, power_law=(0.01, 0.8, 1e-4, 1.0), walls=(True, True))
+    with pytest.raises(ValueError):
+        o.set_source(0.1)
