@@ -131,9 +131,31 @@ mdf_status mdf_set_stream(mdf_ctx *ctx, void *cuda_stream);
 
 /* Body force F_alpha of Eq. 2.2.6 (F_{j,alpha} = w_j F_alpha).  mode:
  * MDF_FORCE_NONE, MDF_FORCE_CONSTANT (fx, fy) or MDF_FORCE_FIELD (arrays
- * Fx, Fy of nx*ny FP32, copied).  dF/dt is taken as zero. */
+ * Fx, Fy of nx*ny FP32, copied).  May change between steps (a time-dependent
+ * force is set before every step); its time derivative is given by
+ * mdf_set_force_rate. */
 mdf_status mdf_set_force(mdf_ctx *ctx, int mode, double fx, double fy,
                          const float *Fx, const float *Fy, int on_device);
+
+/* Time derivative dF_alpha/dt of the body force (same modes and layouts as
+ * mdf_set_force; MDF_FORCE_NONE = 0, the default).  It enters the fhat
+ * update as dt^2/2 w_j dF/dt (Eq. 2.2.1 with G dropped, Eq. 2.3.24); the
+ * h^2/2 term of the fbar update is dropped (Remark 2).  The dt step then
+ * reads F + dt/2 dF/dt (one extra pair of planes when either is a field). */
+mdf_status mdf_set_force_rate(mdf_ctx *ctx, int mode, double dfx, double dfy,
+                              const float *dFx, const float *dFy, int on_device);
+
+/* Source R of the continuity equation div u = R (Eq. 2.1.1): mode
+ * MDF_FORCE_NONE (R = 0, the default), MDF_FORCE_CONSTANT (r) or
+ * MDF_FORCE_FIELD (array R of nx*ny FP32, copied).  R enters the pressure of
+ * Eq. 2.3.23, P = (sum c f + (cs^2/s) R - |u|^2)/2, which is stated for f;
+ * computed from fhat (Step 1) and fbar (Step 3), whose non-equilibrium
+ * first moments are (1 + dt s/2) and (1 + h s/2) times that of f
+ * (Eqs. 2.2.2, 2.2.16), the term becomes (nu + cs^2 dt/2) R / 2 and
+ * (nu + cs^2 h/2) R / 2.  Newtonian fluids and FP32 storage only
+ * (MDF_E_INVALID otherwise).  The alpha = 0 distribution (rho_0, Remark 1)
+ * is not evolved: it influences neither u nor P. */
+mdf_status mdf_set_source(mdf_ctx *ctx, int mode, double r, const float *R, int on_device);
 
 /* Initial state fhat = feq(u, v, p) (Sec. 4: distributions start at
  * equilibrium); wall nodes take the wall velocity.  Resets the step count

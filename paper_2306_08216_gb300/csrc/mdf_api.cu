@@ -44,8 +44,8 @@ static bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
 
 static void free_ctx(mdf_ctx *c) {
     if (!c) return;
-    float *fp[] = {c->buf[0], c->buf[1], c->kxv, c->kyv, c->mxx, c->mxy, c->mex, c->mey,
-                   c->Fxp, c->Fyp, c->snap_u, c->snap_v, c->scratch};
+    float *fp[] = {c->buf[0], c->buf[1], c->kxv, c->kyv, c->mxx, c->mxy, c->mex, c->mey, c->Fxp, c->Fyp,
+                   c->dFxp, c->dFyp, c->Fxdp, c->Fydp, c->Rp, c->snap_u, c->snap_v, c->scratch};
     for (float *p : fp)
         if (p) cudaFree(p);
     if (c->partials) cudaFree(c->partials);
@@ -392,6 +392,9 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
             a.pwyd[i] = pack_pair(-a.dt * kys * w[i]);
         }
     }
+    a.rk_hat = (float)(0.5 * (fluid->nu + c->cs2 * c->dt / 2.0));  // Eq. 2.3.23 from fhat
+    a.rk_bar = (float)(0.5 * (fluid->nu + c->cs2 * c->dt / 4.0));  // ... from fbar (h = dt/2)
+    x.rk_hat = a.rk_hat;
     a.pmKp = pack_pair(-(1.0f - a.rpp));
     a.pDp = pack_pair(0.5f * (a.rp - a.rpp));
     a.pmKb = pack_pair(-(1.0f - a.rbp));
@@ -439,6 +442,40 @@ static mdf_status stage_in(mdf_ctx *c, const float *const *src, int count, int o
     return MDF_OK;
 }
 
+// The dt step's force F + dt/2 dF/dt (Eq. 2.3.24) from the force and its rate.
+static mdf_status update_force_d(mdf_ctx *c) {
+    StepArgs &a = c->args;
+    const double k = 0.5 * c->dt;
+    if (c->rate_mode == 0) {
+        a.force_mode_d = a.force_mode;
+        a.Fxd = a.Fx;
+        a.Fyd = a.Fy;
+        a.Fxdp = a.Fxp;
+        a.Fydp = a.Fyp;
+    } else if (c->rate_mode == 1 && c->force_mode != MDF_FORCE_FIELD) {
+        const double fx = c->force_mode ? c->fx : 0.0, fy = c->force_mode ? c->fy : 0.0;
+        a.force_mode_d = 1;
+        a.Fxd = (float)(fx + k * c->drx);
+        a.Fyd = (float)(fy + k * c->dry);
+    } else {
+        const size_t pb = (size_t)c->pitch * c->ny * sizeof(float);
+        if (!c->Fxdp) CK(c, cudaMalloc(&c->Fxdp, pb));
+        if (!c->Fydp) CK(c, cudaMalloc(&c->Fydp, pb));
+        const bool ff = c->force_mode == MDF_FORCE_FIELD, rf = c->rate_mode == MDF_FORCE_FIELD;
+        const float fx = c->force_mode == MDF_FORCE_CONSTANT ? (float)c->fx : 0.0f;
+        const float fy = c->force_mode == MDF_FORCE_CONSTANT ? (float)c->fy : 0.0f;
+        CK(c, aux_axpy_field(c->aux, ff ? c->Fxp : nullptr, fx, rf ? c->dFxp : nullptr, (float)c->drx, (float)k,
+                             c->Fxdp, c->stream));
+        CK(c, aux_axpy_field(c->aux, ff ? c->Fyp : nullptr, fy, rf ? c->dFyp : nullptr, (float)c->dry, (float)k,
+                             c->Fydp, c->stream));
+        a.force_mode_d = 2;
+        a.Fxdp = c->Fxdp;
+        a.Fydp = c->Fydp;
+    }
+    ++c->args_version;
+    return MDF_OK;
+}
+
 mdf_status mdf_set_force(mdf_ctx *c, int mode, double fx, double fy, const float *Fx, const float *Fy,
                          int on_device) {
     if (!c) return MDF_E_INVALID;
@@ -458,12 +495,65 @@ mdf_status mdf_set_force(mdf_ctx *c, int mode, double fx, double fy, const float
         CK(c, aux_pad_field(c->aux, c->scratch + N, c->Fyp, c->stream));
     }
     c->force_mode = mode;
+    c->fx = fx;
+    c->fy = fy;
     ++c->args_version;
     c->args.force_mode = mode;
     c->args.Fx = (float)fx;
     c->args.Fy = (float)fy;
     c->args.Fxp = c->Fxp;
     c->args.Fyp = c->Fyp;
+    return update_force_d(c);
+}
+
+mdf_status mdf_set_force_rate(mdf_ctx *c, int mode, double dfx, double dfy, const float *dFx, const float *dFy,
+                              int on_device) {
+    if (!c) return MDF_E_INVALID;
+    if (mode < MDF_FORCE_NONE || mode > MDF_FORCE_FIELD) return fail(c, MDF_E_INVALID, "unknown force-rate mode");
+    if (mode == MDF_FORCE_CONSTANT && (!isfinite(dfx) || !isfinite(dfy)))
+        return fail(c, MDF_E_INVALID, "force rate must be finite");
+    if (mode == MDF_FORCE_FIELD) {
+        if (!dFx || !dFy) return fail(c, MDF_E_INVALID, "force-rate field arrays are required");
+        const size_t pb = (size_t)c->pitch * c->ny * sizeof(float);
+        if (!c->dFxp) CK(c, cudaMalloc(&c->dFxp, pb));
+        if (!c->dFyp) CK(c, cudaMalloc(&c->dFyp, pb));
+        const float *src[2] = {dFx, dFy};
+        mdf_status s = stage_in(c, src, 2, on_device);
+        if (s != MDF_OK) return s;
+        const size_t N = (size_t)c->nx * c->ny;
+        CK(c, aux_pad_field(c->aux, c->scratch, c->dFxp, c->stream));
+        CK(c, aux_pad_field(c->aux, c->scratch + N, c->dFyp, c->stream));
+    }
+    c->rate_mode = mode;
+    c->drx = mode == MDF_FORCE_CONSTANT ? dfx : 0.0;
+    c->dry = mode == MDF_FORCE_CONSTANT ? dfy : 0.0;
+    return update_force_d(c);
+}
+
+mdf_status mdf_set_source(mdf_ctx *c, int mode, double r, const float *R, int on_device) {
+    if (!c) return MDF_E_INVALID;
+    if (mode < MDF_FORCE_NONE || mode > MDF_FORCE_FIELD) return fail(c, MDF_E_INVALID, "unknown source mode");
+    if (mode != MDF_FORCE_NONE && c->fluid.power_law)
+        return fail(c, MDF_E_INVALID, "the source term needs a Newtonian fluid");
+    if (mode != MDF_FORCE_NONE && c->prm.storage != MDF_STORAGE_FP32)
+        return fail(c, MDF_E_INVALID, "the source term needs FP32 storage");
+    if (mode == MDF_FORCE_CONSTANT && !isfinite(r)) return fail(c, MDF_E_INVALID, "source must be finite");
+    if (mode == MDF_FORCE_FIELD) {
+        if (!R) return fail(c, MDF_E_INVALID, "source field array is required");
+        if (!c->Rp) CK(c, cudaMalloc(&c->Rp, (size_t)c->pitch * c->ny * sizeof(float)));
+        const float *src[1] = {R};
+        mdf_status s = stage_in(c, src, 1, on_device);
+        if (s != MDF_OK) return s;
+        CK(c, aux_pad_field(c->aux, c->scratch, c->Rp, c->stream));
+    }
+    StepArgs &a = c->args;
+    a.r_mode = mode;
+    a.Rc = mode == MDF_FORCE_CONSTANT ? (float)r : 0.0f;
+    a.Rp = c->Rp;
+    c->aux.r_mode = a.r_mode;
+    c->aux.Rc = a.Rc;
+    c->aux.Rp = a.Rp;
+    ++c->args_version;
     return MDF_OK;
 }
 
@@ -715,6 +805,8 @@ double mdf_bytes_per_node(const mdf_ctx *c) {
     if (!c) return NAN;
     double b = 2.0 * 4.0 * state_planes(c->prm.storage);
     if (c->force_mode == MDF_FORCE_FIELD) b += 8.0;
+    if (c->args.force_mode_d == MDF_FORCE_FIELD && c->args.Fxdp != c->args.Fxp) b += 8.0;
+    if (c->args.r_mode == MDF_FORCE_FIELD) b += 4.0;
     if (c->kind == MDF_GRID_CURVILINEAR) b += 16.0;
     return b;
 }

@@ -204,6 +204,13 @@ __global__ void pad_field_kernel(AuxArgs a, const float *src, float *dst) {
     dst[(long long)y * a.pitch + col] = val;
 }
 
+__global__ void axpy_field_kernel(AuxArgs a, const float *F, float f0, const float *dF, float d0, float k,
+                                  float *dst) {
+    const long long n = a.plane;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (F ? F[i] : f0) + k * (dF ? dF[i] : d0);
+}
+
 // ---- grid metrics (FP64) ----------------------------------------------
 
 // Coordinates with periodic continuation: crossing a periodic boundary shifts
@@ -366,7 +373,8 @@ __global__ void fields_kernel(AuxArgs a, const float *f, FieldPtrs dst) {
         u = g[0] + g[1] + g[2] + g[3] + g[4];
         v = g[5] + g[6] + g[7] + g[8] + g[9];
         const float d1x = g[1] - g[3], d1y = g[2] - g[4], d2x = g[6] - g[8], d2y = g[7] - g[9];
-        P = 0.5f * (c * (d1x + d2y) - u * u - v * v);  // Eq. 2.3.23, R = 0
+        P = 0.5f * (c * (d1x + d2y) - u * u - v * v);  // Eq. 2.3.23
+        if (a.r_mode) P += a.rk_hat * (a.r_mode == 1 ? a.Rc : a.Rp[s]);
         // first moment of fhat - feq (Eq. 2.2.5 fluxes ub u + P E)
         gx1 = c * d1x - (u * u + P);
         gy1 = c * d1y - u * v;
@@ -517,6 +525,14 @@ cudaError_t aux_unpack(const AuxArgs &a, const float *dense, float *f, cudaStrea
 
 cudaError_t aux_pad_field(const AuxArgs &a, const float *src, float *dst, cudaStream_t st) {
     pad_field_kernel<<<rows_grid(a.pitch, a.ny, 128), 128, 0, st>>>(a, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t aux_axpy_field(const AuxArgs &a, const float *F, float f0, const float *dF, float d0, float k, float *dst,
+                           cudaStream_t st) {
+    long long b = (a.plane + 255) / 256;
+    if (b > 65535) b = 65535;
+    axpy_field_kernel<<<(unsigned)b, 256, 0, st>>>(a, F, f0, dF, d0, k, dst);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,9 @@ struct AuxArgs {
     float nu, K, n_index, nu_min, nu_max, a_pl;  // a_pl = cs2 dt / 2
     int storage;                                 // StorageKind of the state buffers
     float nscale, ninv;                          // 16-bit storage: S and 1/S
+    int r_mode;                                  // source R: 0 none, 1 constant, 2 padded field
+    float Rc, rk_hat;                            // constant R; P factor for fhat (Eq. 2.3.23)
+    const float *Rp;
 };
 
 struct FieldPtrs {
@@ -27,6 +30,10 @@ cudaError_t aux_init(const AuxArgs &a, const float *u, const float *v, const flo
 cudaError_t aux_pack(const AuxArgs &a, const float *f, float *dense, cudaStream_t st);
 cudaError_t aux_unpack(const AuxArgs &a, const float *dense, float *f, cudaStream_t st);
 cudaError_t aux_pad_field(const AuxArgs &a, const float *src, float *dst, cudaStream_t st);
+// dst = F + k dF per element of two padded planes; F, dF may be null (read
+// as the constants f0, d0)
+cudaError_t aux_axpy_field(const AuxArgs &a, const float *F, float f0, const float *dF, float d0, float k, float *dst,
+                           cudaStream_t st);
 cudaError_t aux_metrics2d(const AuxArgs &a, const double *X, const double *Y, double c, float *mxx, float *mxy,
                           float *mex, float *mey, double *edge_min, cudaStream_t st);
 cudaError_t aux_metrics1d(const AuxArgs &a, const double *xc, const double *yc, double c, float *kxv, float *kyv,

@@ -24,6 +24,12 @@ struct mdf_ctx {
     float *mxx = nullptr, *mxy = nullptr, *mex = nullptr, *mey = nullptr;
     float *Fxp = nullptr, *Fyp = nullptr;
     int force_mode = 0;
+    // dF/dt (mode 0 none, 1 constant, 2 field) and the dt step's force planes
+    int rate_mode = 0;
+    double drx = 0, dry = 0;
+    float *dFxp = nullptr, *dFyp = nullptr, *Fxdp = nullptr, *Fydp = nullptr;
+    // source R of Eq. 2.1.1
+    float *Rp = nullptr;
     double fx = 0, fy = 0;
     float *snap_u = nullptr, *snap_v = nullptr;
     long long snap_step = 0;

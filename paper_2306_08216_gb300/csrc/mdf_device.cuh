@@ -131,6 +131,20 @@ __device__ __forceinline__ Mom2 moments2(const F2 g[5], float c) {
     return m;
 }
 
+// As moments2, with the source term of Eq. 2.3.23 added to P: pr =
+// (cs^2/s)(1 + k s/2) R / 2 for a distribution whose non-equilibrium first
+// moment carries the factor 1 + k s/2 (k = dt for fhat, h for fbar).
+__device__ __forceinline__ Mom2 moments2r(const F2 g[5], float c, float pr) {
+    Mom2 m = moments2(g, c);
+    m.P += pr;
+    return m;
+}
+
+// Source R of Eq. 2.1.1 at storage element (row, X) (constant or padded field).
+__device__ __forceinline__ float source_at(const StepArgs &a, int row, int X) {
+    return a.r_mode == 1 ? a.Rc : a.Rp[(long long)row * a.pitch + GHOST + X];
+}
+
 // Non-equilibrium part n = g - feq (Eq. 2.2.5 on D2Q5 with w_j = 1/5 and
 // cs^2 = 2c^2/5: feq_0 = ub/5, feq_{1,3} = ub/5 +- Phi_x/(2c),
 // feq_{2,4} = ub/5 +- Phi_y/(2c), Phi = ub_alpha u + P E_alpha).  feq_0 is

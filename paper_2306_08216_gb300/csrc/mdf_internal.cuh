@@ -66,10 +66,19 @@ struct StepArgs {
     // power-law fluid
     int power_law;
     float K, n_index, nu_min, nu_max, cs2, s_ratio, a_pl;  // a_pl = cs2 dt / 2
-    // body force
+    // body force: F for the h step (Eq. 2.3.25); F + dt/2 dF/dt for the dt
+    // step (Eq. 2.3.24), mode 0 none, 1 constant, 2 padded field
     int force_mode;
     float Fx, Fy;
     const float *Fxp, *Fyp;  // padded layout
+    int force_mode_d;
+    float Fxd, Fyd;
+    const float *Fxdp, *Fydp;
+    // source R of Eq. 2.1.1 (mode 0 none, 1 constant Rc, 2 padded field Rp)
+    // and its pressure factors (Eq. 2.3.23) for fhat and fbar
+    int r_mode;
+    float Rc, rk_hat, rk_bar;
+    const float *Rp;
     // wall velocities (west, east, south, north)
     float uw[4], vw[4];
     int *err;

@@ -184,10 +184,10 @@ __device__ __forceinline__ void march(const CUtensorMap *tmap, const StepArgs &a
                 const unsigned char *Pr = ringP + o0;
                 const bool yadj_p = ywall && r == 1, yadj_m = ywall && r == a.ny - 2;
                 F2 fF = splat(0.0f);
-                if (a.force_mode == 1) fF = dw * mk2(a.Fx, a.Fy);
-                else if (a.force_mode == 2) {
+                if (a.force_mode_d == 1) fF = dw * mk2(a.Fxd, a.Fyd);
+                else if (a.force_mode_d == 2) {
                     const long long fi = (long long)r * a.pitch + GHOST + X;
-                    fF = dw * mk2(a.Fxp[fi], a.Fyp[fi]);
+                    fF = dw * mk2(a.Fxdp[fi], a.Fydp[fi]);
                 }
                 F2 out[5];
 #pragma unroll
@@ -245,7 +245,10 @@ __device__ __forceinline__ void march(const CUtensorMap *tmap, const StepArgs &a
             F2 g[5];
 #pragma unroll
             for (int j = 0; j < 5; ++j) g[j] = mk2(src[j * NT + t], src[(5 + j) * NT + t]);
-            const Mom2 m = moments2(g, c);
+            const int pw = (WALLS && ywall) ? p : wrap(p, a.ny);
+            const Mom2 m = a.r_mode && pw >= 0 && pw < a.ny && X >= -GHOST && X < a.nx + GHOST
+                               ? moments2r(g, c, a.rk_hat * source_at(a, pw, X))
+                               : moments2(g, c);
             F2 n[5];
             noneq2(g, m, inv2c, n);
             const F2 n13 = n[1] - n[3], n24 = n[2] - n[4];
@@ -360,7 +363,7 @@ __device__ __forceinline__ void march(const CUtensorMap *tmap, const StepArgs &a
                         mKk_ = splat(-(1.0f - k[t]));
                         Dk_ = splat(0.5f * (k[NT + t] - k[t]));
                     }
-                    const Mom2 m = moments2(fb, c);
+                    const Mom2 m = a.r_mode ? moments2r(fb, c, a.rk_bar * source_at(a, qw, X)) : moments2(fb, c);
                     F2 n[5], f[5];
                     noneq2(fb, m, inv2c, n);
                     relax2(fb, n, n[1] - n[3], n[2] - n[4], mKk_, Dk_, f);

@@ -49,11 +49,19 @@ __device__ __forceinline__ W3 weights(float k, float step, const StepArgs &a) {
     return w;
 }
 
-// Force increment factor (step/5) (Fx, Fy) at a node, F_{j,alpha} = w_j F_alpha.
+// Force increment factor (step/5) (Fx, Fy) at a node, F_{j,alpha} = w_j F_alpha:
+// the h step's F, and the dt step's F + dt/2 dF/dt (Eq. 2.3.24).
 __device__ __forceinline__ F2 force_at(const StepArgs &a, int row, int X, F2 factor) {
+    if (a.force_mode == 0) return splat(0.0f);
     if (a.force_mode == 1) return factor * mk2(a.Fx, a.Fy);
     const long long fi = (long long)row * a.pitch + GHOST + X;
     return factor * mk2(a.Fxp[fi], a.Fyp[fi]);
+}
+__device__ __forceinline__ F2 force_at_d(const StepArgs &a, int row, int X, F2 factor) {
+    if (a.force_mode_d == 0) return splat(0.0f);
+    if (a.force_mode_d == 1) return factor * mk2(a.Fxd, a.Fyd);
+    const long long fi = (long long)row * a.pitch + GHOST + X;
+    return factor * mk2(a.Fxdp[fi], a.Fydp[fi]);
 }
 
 template <int NT, int MK, bool FORCED, int ST>
@@ -142,7 +150,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
 #pragma unroll
                 for (int j = 0; j < 5; ++j) out[j] = lds2(Pr, (j * NT + t) * 8);
                 if (forced) {
-                    const F2 fF = force_at(a, r, X, pair_of(a.pdw));
+                    const F2 fF = force_at_d(a, r, X, pair_of(a.pdw));
 #pragma unroll
                     for (int j = 0; j < 5; ++j) out[j] = out[j] + fF;
                 }
@@ -169,7 +177,9 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
                 if (ST == STORAGE_FP32) {
 #pragma unroll
                     for (int j = 0; j < 5; ++j) g[j] = mk2(src[j * NT + t], src[(5 + j) * NT + t]);
-                    const Mom2 m = moments2(g, c);
+                    const Mom2 m = (forced && a.r_mode)
+                                       ? moments2r(g, c, a.rk_hat * source_at(a, wrap(p, a.ny), X))
+                                       : moments2(g, c);
                     noneq2(g, m, inv2c, n);
                 } else {
                     // fhat = feq(u, v, P) + n: the stored macroscopic fields
@@ -244,7 +254,8 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
                     fb[4] = stream2<false>(BY[s2][1] + hFq, BY[s3][1], BY[s2][1], BY[s1][1], BY[k][1], false, wy.w1,
                                            wy.w0, wy.w2);
                     // Step 3: f = feq + (I + h/2 Lt)^-1 (fbar - feq)
-                    const Mom2 m = moments2(fb, c);
+                    const Mom2 m = (forced && a.r_mode) ? moments2r(fb, c, a.rk_bar * source_at(a, qw, X))
+                                                        : moments2(fb, c);
                     F2 n[5], f[5];
                     noneq2(fb, m, inv2c, n);
                     relax2(fb, n, n[1] - n[3], n[2] - n[4], pair_of(a.pmKk), pair_of(a.pDk), f);
@@ -307,7 +318,7 @@ cudaError_t fast_occupancy_t(int *occ, int *smem) {
 template <int NT, int MK, int ST>
 cudaError_t fast_launch_f(const CUtensorMap *tmap, const StepArgs &args,
                           const StepPlan &plan, cudaStream_t stream) {
-    return args.force_mode ? fast_launch_t<NT, MK, true, ST>(tmap, args, plan, stream)
+    return (args.force_mode || args.force_mode_d || args.r_mode) ? fast_launch_t<NT, MK, true, ST>(tmap, args, plan, stream)
                            : fast_launch_t<NT, MK, false, ST>(tmap, args, plan, stream);
 }
 

@@ -67,6 +67,10 @@ _SIGNATURES = [
     ("mdf_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("mdf_set_force", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("mdf_set_force_rate", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("mdf_set_source", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                      ctypes.c_int]),
     ("mdf_init_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_int]),
     ("mdf_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -208,7 +212,8 @@ class Solver:
 
     def __init__(self, nx, ny, nu=0.01, grid="uniform", lx=1.0, ly=1.0, x=None, y=None,
                  power_law=None, walls=(False, False), u_wall=(0, 0, 0, 0), v_wall=(0, 0, 0, 0),
-                 c=1.0, cfl=0.5, eta=0.8, s_ratio=1.5, force=None, stream=None, storage="fp32", _handle=None):
+                 c=1.0, cfl=0.5, eta=0.8, s_ratio=1.5, force=None, stream=None, storage="fp32", force_rate=None,
+                 source=None, _handle=None):
         self.nx, self.ny = nx, ny
         self._owned = _handle is None
         if _handle is not None:  # a problem of a batch: the batch owns the context
@@ -223,6 +228,10 @@ class Solver:
             self.set_stream(stream)
         if force is not None:
             self.set_force(force)
+        if force_rate is not None:
+            self.set_force_rate(force_rate)
+        if source is not None:
+            self.set_source(source)
 
     def close(self):
         if getattr(self, "_h", None) and getattr(self, "_owned", True):
@@ -261,6 +270,29 @@ class Solver:
             n = self.nx * self.ny
             fx, fy = _Arr(force[0], n), _Arr(force[1], n)
             _check(lib().mdf_set_force(self._h, 2, 0.0, 0.0, fx.ptr, fy.ptr, fx.on_device), self._h)
+            self.synchronize()
+
+    def set_force_rate(self, rate):
+        """dF/dt of the body force (None, (dfx, dfy) or fields), Eq. 2.3.24."""
+        if rate is None:
+            _check(lib().mdf_set_force_rate(self._h, 0, 0.0, 0.0, None, None, 0), self._h)
+        elif np.isscalar(rate[0]):
+            _check(lib().mdf_set_force_rate(self._h, 1, float(rate[0]), float(rate[1]), None, None, 0), self._h)
+        else:
+            n = self.nx * self.ny
+            fx, fy = _Arr(rate[0], n), _Arr(rate[1], n)
+            _check(lib().mdf_set_force_rate(self._h, 2, 0.0, 0.0, fx.ptr, fy.ptr, fx.on_device), self._h)
+            self.synchronize()
+
+    def set_source(self, R):
+        """Source R of div u = R (None, a constant or a field), Eq. 2.3.23."""
+        if R is None:
+            _check(lib().mdf_set_source(self._h, 0, 0.0, None, 0), self._h)
+        elif np.isscalar(R):
+            _check(lib().mdf_set_source(self._h, 1, float(R), None, 0), self._h)
+        else:
+            a = _Arr(R, self.nx * self.ny)
+            _check(lib().mdf_set_source(self._h, 2, 0.0, a.ptr, a.on_device), self._h)
             self.synchronize()
 
     def init(self, u, v, p):
