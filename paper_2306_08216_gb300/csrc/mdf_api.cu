@@ -52,6 +52,11 @@ static void free_ctx(mdf_ctx *c) {
     if (c->result) cudaFree(c->result);
     if (c->err) cudaFree(c->err);
     if (c->h_result) cudaFreeHost(c->h_result);
+    for (int p = 0; p < 2; ++p)
+        if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->cstream) cudaStreamDestroy(c->cstream);
     delete c;
 }
 
@@ -378,6 +383,12 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
     a.K = (float)fluid->K; a.n_index = (float)fluid->n; a.nu_min = (float)fluid->nu_min;
     a.nu_max = (float)fluid->nu_max; a.cs2 = (float)c->cs2; a.s_ratio = (float)prm.s_ratio;
     a.a_pl = (float)(0.5 * c->cs2 * c->dt);
+    if (fluid->power_law) {
+        a.lnK = (float)log(fluid->K);
+        a.ln_nu_min = (float)log(fluid->nu_min);
+        a.ln_nu_max = (float)log(fluid->nu_max);
+        a.inv_n = (float)(1.0 / fluid->n);
+    }
     a.force_mode = 0;
     for (int s = 0; s < 4; ++s) { a.uw[s] = x.uw[s]; a.vw[s] = x.vw[s]; }
     a.err = c->err;
@@ -573,10 +584,65 @@ mdf_status mdf_init_fields(mdf_ctx *c, const float *u, const float *v, const flo
     return MDF_OK;
 }
 
+static void drop_graphs(mdf_ctx *c) {
+    for (int p = 0; p < 2; ++p) {
+        if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
+        c->graph[p] = nullptr;
+        c->graph_version[p] = -1;
+    }
+}
+
+// Capture kGraphSteps launches starting from buffer `parity` on the capture
+// stream (the kernel arguments, buffer pointers and tensor maps are baked in).
+static mdf_status build_step_graph(mdf_ctx *c, int parity) {
+    if (!c->cstream) {
+        CK(c, cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
+        CK(c, cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+        CK(c, cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+    }
+    if (c->graph[parity]) cudaGraphExecDestroy(c->graph[parity]);
+    c->graph[parity] = nullptr;
+    CK(c, cudaStreamBeginCapture(c->cstream, cudaStreamCaptureModeThreadLocal));
+    StepArgs a = c->args;
+    int cur = parity;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < mdf_ctx::kGraphSteps && e == cudaSuccess; ++i) {
+        a.fout = c->buf[1 - cur];
+        e = step_launch(&c->tmap[cur], a, c->kind, c->plan, c->cstream);
+        cur = 1 - cur;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c->cstream, &g);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph[parity], g, 0);
+    if (g) cudaGraphDestroy(g);
+    CK(c, e);
+    c->graph_version[parity] = c->args_version;
+    return MDF_OK;
+}
+
 mdf_status mdf_step(mdf_ctx *c, int n) {
     if (!c) return MDF_E_INVALID;
     if (n < 0) return fail(c, MDF_E_INVALID, "n must be >= 0");
-    for (int i = 0; i < n; ++i) {
+    int done = 0;
+    const int reps = n / mdf_ctx::kGraphSteps;
+    if (reps >= 2) {
+        // replay a captured graph on the capture stream, ordered after and
+        // before the context's stream by events; an even number of steps
+        // leaves the buffer parity unchanged
+        if (!c->graph[c->cur] || c->graph_version[c->cur] != c->args_version) {
+            mdf_status s = build_step_graph(c, c->cur);
+            if (s != MDF_OK) return s;
+        }
+        CK(c, cudaEventRecord(c->ev_in, c->stream));
+        CK(c, cudaStreamWaitEvent(c->cstream, c->ev_in, 0));
+        for (int r = 0; r < reps; ++r) CK(c, cudaGraphLaunch(c->graph[c->cur], c->cstream));
+        CK(c, cudaEventRecord(c->ev_out, c->cstream));
+        CK(c, cudaStreamWaitEvent(c->stream, c->ev_out, 0));
+        done = reps * mdf_ctx::kGraphSteps;
+        c->steps += done;
+    }
+    for (int i = done; i < n; ++i) {
         c->args.fout = c->buf[1 - c->cur];
         CK(c, step_launch(&c->tmap[c->cur], c->args, c->kind, c->plan, c->stream));
         c->cur = 1 - c->cur;
@@ -795,9 +861,11 @@ mdf_status mdf_set_launch(mdf_ctx *c, int threads, int rows_per_block) {
     p.H = rows_per_block;
     p.gy = (c->ny + p.H - 1) / p.H;
     CK(c, cudaStreamSynchronize(c->stream));
+    if (c->cstream) CK(c, cudaStreamSynchronize(c->cstream));
     c->plan = p;
     c->args.W = p.W;
     c->args.H = p.H;
+    drop_graphs(c);
     return encode_maps(c);
 }
 

@@ -35,6 +35,7 @@ struct mdf_batch {
     CUtensorMap *d_maps[2] = {nullptr, nullptr};   // per parity: maps of the input buffer
     BatchItem *d_items = nullptr;
     int nitems = 0, grid = 0, occ = 0, smem = 0;
+    int forced = 0;                                // some problem has a force, force rate or source
     int cur = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cstream = nullptr;                // capture / replay stream
@@ -102,13 +103,26 @@ static mdf_status upload_args(mdf_batch *b) {
         BCK(b, cudaMemcpy(b->d_args[p], args.data(), b->count * sizeof(StepArgs), cudaMemcpyHostToDevice));
     }
     for (int i = 0; i < b->count; ++i) b->seen_version[i] = b->ctx[i]->args_version;
+    int forced = 0;
+    for (int i = 0; i < b->count; ++i) {
+        const StepArgs &a = b->ctx[i]->args;
+        forced |= (a.force_mode || a.force_mode_d || a.r_mode) ? 1 : 0;
+    }
+    if (forced != b->forced) {
+        // the captured graphs launch the other kernel variant
+        for (int p = 0; p < 2; ++p) {
+            if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
+            b->graph[p] = nullptr;
+        }
+        b->forced = forced;
+    }
     return MDF_OK;
 }
 
 static mdf_status launch_steps(mdf_batch *b, cudaStream_t st, int n) {
     for (int i = 0; i < n; ++i) {
         BCK(b, batch_launch(b->d_items, b->nitems, b->d_args[b->cur], b->d_maps[b->cur], b->metric, b->power_law,
-                            b->walls, b->grid, st));
+                            b->walls, b->grid, b->forced, st));
         b->cur ^= 1;
     }
     return MDF_OK;

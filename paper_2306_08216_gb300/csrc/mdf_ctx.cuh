@@ -45,6 +45,13 @@ struct mdf_ctx {
     mdf::StepArgs args{};
     mdf::AuxArgs aux{};
     cudaStream_t stream = nullptr;
+    // captured graphs of kGraphSteps launches from buffer 0 / 1 (mdf_step),
+    // valid while args_version and the plan are unchanged
+    static constexpr int kGraphSteps = 16;
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_version[2] = {-1, -1};
     long long steps = 0;
     int args_version = 0;  // bumped whenever args change after creation (forcing)
     char last_error[256] = {0};

@@ -219,16 +219,19 @@ __device__ __forceinline__ float power_law_nu(float g, const StepArgs &a) {
     const float n = a.n_index;
     if (n == 1.0f) return fminf(fmaxf(a.K, a.nu_min), a.nu_max);
     if (!(g > 1e-30f)) return n < 1.0f ? a.nu_max : a.nu_min;
-    const float lnK = __logf(a.K), lng = __logf(g);
-    const float lmin = __logf(a.nu_min), lmax = __logf(a.nu_max);
-    float l = (lnK + (n - 1.0f) * lng) / n;
+    const float lnK = a.lnK, lng = __logf(g);
+    const float lmin = a.ln_nu_min, lmax = a.ln_nu_max;
+    // the start is the root when cs^2 dt/2 << nu; Newton converges
+    // quadratically from it, and its step only needs F (no division) to be
+    // exact at the root, so the step may use the fast approximate quotient
+    float l = (lnK + (n - 1.0f) * lng) * a.inv_n;
     l = fminf(fmaxf(l, lmin), lmax);
 #pragma unroll
-    for (int it = 0; it < 8; ++it) {
+    for (int it = 0; it < 6; ++it) {
         const float e = __expf(l);
         const float F = l - lnK - (n - 1.0f) * (lng - __logf(e + a.a_pl));
-        const float dF = 1.0f + (n - 1.0f) * e / (e + a.a_pl);
-        l = l - F / dF;
+        const float dF = 1.0f + (n - 1.0f) * __fdividef(e, e + a.a_pl);
+        l = l - __fdividef(F, dF);
         l = fminf(fmaxf(l, lmin - 1.0f), lmax + 1.0f);
     }
     return fminf(fmaxf(__expf(l), a.nu_min), a.nu_max);

@@ -66,6 +66,7 @@ struct StepArgs {
     // power-law fluid
     int power_law;
     float K, n_index, nu_min, nu_max, cs2, s_ratio, a_pl;  // a_pl = cs2 dt / 2
+    float lnK, ln_nu_min, ln_nu_max, inv_n;                  // ln K, ln nu_min, ln nu_max, 1/n
     // body force: F for the h step (Eq. 2.3.25); F + dt/2 dF/dt for the dt
     // step (Eq. 2.3.24), mode 0 none, 1 constant, 2 padded field
     int force_mode;
@@ -125,7 +126,17 @@ struct BatchItem {
 };
 cudaError_t batch_occupancy(int metric, int power_law, int walls, int *nt, int *occ, int *smem);
 cudaError_t batch_launch(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps, int metric,
-                         int power_law, int walls, int grid, cudaStream_t stream);
+                         int power_law, int walls, int grid, int forced, cudaStream_t stream);
+
+// Walls and/or power law on uniform/separable grids, FP32 storage, in the
+// register-window form of the fast path (mdf_step_walls.cu).
+bool walls_path_applies(int metric, int power_law, int walls, int storage);
+cudaError_t walls_occupancy(int metric, int power_law, int nt, int *occ, int *smem);
+cudaError_t walls_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
+                         cudaStream_t stream);
+cudaError_t walls_batch_occupancy(int metric, int power_law, int *nt, int *occ, int *smem);
+cudaError_t walls_batch_launch(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps,
+                               int metric, int power_law, int grid, int forced, cudaStream_t stream);
 
 // Periodic Newtonian fast path on uniform/separable grids (mdf_step_fast.cu).
 bool fast_path_applies(int metric, int power_law, int walls);

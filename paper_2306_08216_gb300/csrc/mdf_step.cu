@@ -559,11 +559,13 @@ int step_candidates(int metric, int power_law, int walls, int storage, int nx, i
     int n = 0;
     *err = cudaSuccess;
     const bool fast = fast_path_applies(metric, power_law, walls);
+    const bool wpath = !fast && walls_path_applies(metric, power_law, walls, storage);
     const int nts[2] = {128, 256};
-    for (int i = 0; i < (fast ? 2 : 1); ++i) {
+    for (int i = 0; i < (fast || wpath ? 2 : 1); ++i) {
         int occ = 0, smem = 0;
-        cudaError_t e = fast ? fast_occupancy(metric, storage, nts[i], &occ, &smem)
-                             : occupancy(metric, power_law, walls, &occ, &smem);
+        cudaError_t e = fast    ? fast_occupancy(metric, storage, nts[i], &occ, &smem)
+                        : wpath ? walls_occupancy(metric, power_law, nts[i], &occ, &smem)
+                                : occupancy(metric, power_law, walls, &occ, &smem);
         if (e != cudaSuccess) {
             *err = e;
             return n;
@@ -575,12 +577,15 @@ int step_candidates(int metric, int power_law, int walls, int storage, int nx, i
 }
 
 cudaError_t batch_occupancy(int metric, int power_law, int walls, int *nt, int *occ, int *smem) {
+    if (metric != METRIC_CURVILINEAR) return walls_batch_occupancy(metric, power_law, nt, occ, smem);
     *nt = kNT;
     MDF_DISPATCH(batch_occupancy_t, occ, smem)
 }
 
 cudaError_t batch_launch(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps, int metric,
-                         int power_law, int walls, int grid, cudaStream_t stream) {
+                         int power_law, int walls, int grid, int forced, cudaStream_t stream) {
+    if (metric != METRIC_CURVILINEAR)
+        return walls_batch_launch(items, nitems, args, maps, metric, power_law, grid, forced, stream);
     MDF_DISPATCH(batch_launch_t, items, nitems, args, maps, grid, stream)
 }
 
@@ -589,6 +594,8 @@ cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metri
     const int power_law = args.power_law;
     const int walls = (args.xwall || args.ywall) ? 1 : 0;
     if (fast_path_applies(metric, power_law, walls)) return fast_launch(tmap, args, metric, plan, stream);
+    if (walls_path_applies(metric, power_law, walls, args.storage))
+        return walls_launch(tmap, args, metric, plan, stream);
     MDF_DISPATCH(launch_t, tmap, args, plan, stream)
 }
 

@@ -352,6 +352,44 @@ def warm_vs_cold(net, re, nn, R, target=1e-8, check_every=1000, max_steps=150_00
     return out
 
 
+def conv_flops_per_sample(net):
+    """Algorithmic multiply-add FLOPs (x2) of one forward pass of one sample:
+    every 3 x 3 convolution at its resolution with its real channel counts
+    (the output layer's 3 channels, the input layer's 4)."""
+    R = net.R
+    res = [1, 1, 2, 2, 4, 4, 8, 8, 4, 4, 2, 2, 1, 1, 1]  # resolution divisor of each layer
+    return sum(2.0 * (R // d) ** 2 * 9 * ci * co for d, (co, ci) in zip(res, net.layer_shapes()))
+
+
+def train_benchmark(R=128, batch=16, steps=50, warmup=5, seed=0, stream=None):
+    """Device time of mdf_net_train_step on seeded random data (device
+    buffers, no loss read-back): ms per step and achieved TFLOP/s of the
+    convolutions (forward + input gradient + weight gradient = 3 x forward;
+    the first layer's input gradient is skipped, counted anyway)."""
+    import torch
+    net = Net(R, batch, stream=stream)
+    net.set_params(init_params(net, 2306))
+    rng = np.random.default_rng(seed)
+    re, nn = W.warm_start_draws(batch, seed)
+    x = torch.from_numpy(W.warm_start_inputs(re, nn, R)).cuda()
+    t = torch.from_numpy(rng.standard_normal((batch, 3, R, R)).astype(np.float32)).cuda()
+    for _ in range(warmup):
+        net.train_step(x, t, 1e-4, want_loss=False)
+    st = torch.cuda.current_stream() if stream is None else stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(steps):
+        net.train_step(x, t, 1e-4, want_loss=False)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    flops = 3.0 * conv_flops_per_sample(net) * batch
+    net.close()
+    return {"R": R, "batch": batch, "steps": steps, "ms_per_step": ms, "tflops": flops / (ms / 1e3) / 1e12,
+            "flops_per_step": flops}
+
+
 def channel_stats(t):
     q = [0.0, 0.01, 0.5, 0.99, 1.0]
     return {name: np.quantile(t[:, c], q).tolist() for c, name in enumerate(("u", "v", "p"))}
@@ -374,12 +412,19 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--compare", type=int, default=16, help="held-out cavities marched to 1e-8 cold and warm")
-    ap.add_argument("--out", required=True)
-    ap.add_argument("--report", required=True)
+    ap.add_argument("--out")
+    ap.add_argument("--report")
+    ap.add_argument("--train-bench", action="store_true",
+                    help="only time mdf_net_train_step on random data (--R, --batch, --epochs = timed steps)")
     args = ap.parse_args(argv)
 
     from . import build as B
     B.build()
+    if args.train_bench:
+        print(json.dumps(train_benchmark(args.R, args.batch, steps=args.epochs)), flush=True)
+        return 0
+    if not args.out or not args.report:
+        ap.error("--out and --report are required")
     rep = {"args": vars(args)}
     t0 = time.perf_counter()
     x, t, info = generate_dataset(args.train, 1, args.R, target=args.data_target, max_steps=args.data_max_steps)

@@ -314,3 +314,33 @@ def test_taylor_green_4096_full_size_against_oracle():
     # the initial layer of an equilibrium start shifts the amplitude by ~5e-4
     assert abs(amp - math.exp(-2 * nu * t)) < 1e-3
     assert abs(drift[0]) < 1e-6 * n * n * U0 and abs(drift[1]) < 1e-6 * n * n * U0
+
+
+def test_graph_replay_equals_single_launches():
+    """mdf_step(n >= 32) replays captured graphs of 16 launches; the result is
+    bitwise the same as n single launches, and a force or launch-plan change
+    between calls takes effect (the graphs are rebuilt)."""
+    n = 48
+    kw = dict(nu=0.01, walls=(False, True), force=(1e-4, 0.0))
+    a, b = mdf.Solver(n, n, **kw), mdf.Solver(n, n, **kw)
+    for s in (a, b):
+        s.init(*W.zeros(n, n))
+    a.step(70)                      # 4 graph replays + 6 launches
+    for _ in range(70):
+        b.step(1)
+    np.testing.assert_array_equal(a.state(), b.state())
+    for s in (a, b):
+        s.set_force((2e-4, 1e-5))
+    a.step(33)                      # odd start parity after 70 + 33 ...
+    a.step(64)
+    for _ in range(97):
+        b.step(1)
+    np.testing.assert_array_equal(a.state(), b.state())
+    info = a.launch_info()
+    a.set_launch(info["threads"], 8)
+    b.set_launch(info["threads"], 8)
+    a.step(48)
+    for _ in range(48):
+        b.step(1)
+    np.testing.assert_array_equal(a.state(), b.state())
+    assert a.steps == b.steps == 215
