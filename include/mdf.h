@@ -222,7 +222,7 @@ mdf_status mdf_launch_info(const mdf_ctx *ctx, int info[8]);
 
 /* Override the launch plan the library chose (tile-shape tuning): `threads`
  * per block (128, or 256 on periodic Newtonian uniform/separable problems)
- * and `rows_per_block` (>= 8) rows per block.  mdf_create times the
+ * and `rows_per_block` (>= 1) rows per block.  mdf_create times the
  * candidate plans on grids of 2^20 nodes or more and keeps the fastest; this
  * call replaces that choice.  Waits for the context's stream; MDF_E_INVALID
  * for an unsupported block size. */

@@ -856,7 +856,7 @@ mdf_status mdf_set_launch(mdf_ctx *c, int threads, int rows_per_block) {
     for (int i = 0; i < c->ncand; ++i)
         if (c->cand[i].NT == threads) { found = i; break; }
     if (found < 0) return fail(c, MDF_E_INVALID, "no launch plan with %d threads for this problem", threads);
-    if (rows_per_block < 8) return fail(c, MDF_E_INVALID, "rows_per_block must be >= 8");
+    if (rows_per_block < 1) return fail(c, MDF_E_INVALID, "rows_per_block must be >= 1");
     StepPlan p = c->cand[found];
     p.H = rows_per_block;
     p.gy = (c->ny + p.H - 1) / p.H;

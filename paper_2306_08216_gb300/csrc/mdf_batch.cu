@@ -151,7 +151,7 @@ static mdf_status build_graph(mdf_batch *b, int parity) {
 // heights sized to the active work: a band of H rows costs H + 9 row
 // iterations (halo), so long bands are cheapest when there is enough work to
 // fill every resident block; a small batch instead gets bands short enough
-// that its items cover the grid (one item per block, at least 8 rows).
+// that its items cover the grid (one item per block, at least 2 rows).
 static mdf_status build_items(mdf_batch *b) {
     const int count = b->count;
     const int W = kBatchNT - 8;
@@ -159,12 +159,12 @@ static mdf_status build_items(mdf_batch *b) {
     for (int i = 0; i < count; ++i)
         if (b->active[i]) strip_rows += (long long)((b->ctx[i]->nx + W - 1) / W) * b->ctx[i]->ny;
     const long long slots = (long long)std::max(1, b->occ) * b->num_sms;
-    const int band_target = (int)std::max(8ll, std::min((long long)kBandRows, (strip_rows + slots - 1) / slots));
+    const int band_target = (int)std::max(2ll, std::min((long long)kBandRows, (strip_rows + slots - 1) / slots));
     for (int i = 0; i < count; ++i) {
         const int ny = b->ctx[i]->ny;
         const int bands = (ny + band_target - 1) / band_target;
         int H = (ny + bands - 1) / bands;
-        if (H < 8) H = 8;
+        if (H < 2) H = 2;
         b->H[i] = H;
     }
     std::vector<int> order;

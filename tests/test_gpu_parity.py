@@ -87,7 +87,7 @@ def test_set_state_roundtrip_and_single_step():
     assert maxabs(g.state().astype(np.float64), o.state()) <= 2e-8
 
 
-@pytest.mark.parametrize("threads,rows", [(128, 8), (128, 37), (256, 8), (256, 64)])
+@pytest.mark.parametrize("threads,rows", [(128, 8), (128, 37), (256, 8), (256, 64), (128, 1), (128, 3), (256, 2)])
 def test_launch_plans_agree_with_oracle(threads, rows):
     """Every block size / band height the autotuner may pick (periodic fast
     path): ragged strips and bands against the oracle."""
@@ -344,3 +344,20 @@ def test_graph_replay_equals_single_launches():
         b.step(1)
     np.testing.assert_array_equal(a.state(), b.state())
     assert a.steps == b.steps == 215
+
+
+@pytest.mark.parametrize("threads,rows", [(128, 2), (128, 5), (256, 3), (128, 8)])
+def test_wall_kernel_launch_plans_agree_with_oracle(threads, rows):
+    """Band heights down to a couple of rows on the wall and power-law
+    kernel: a power-law cavity and a channel against the oracle."""
+    n = 45
+    kw = dict(nu=0.004, walls=(True, True), u_wall=(0, 0, 0, 0.1), power_law=(0.004, 0.8, 2e-4, 0.08))
+    g, o = pair(n, n, **kw)
+    g.set_launch(threads, rows)
+    sg, so = run_both(g, o, W.zeros(n, n), 60)
+    assert maxabs(sg, so) <= 1e-5 * 0.1
+    kw = dict(nu=0.01, walls=(False, True), force=(1e-4, 0.0))
+    g, o = pair(70, 33, **kw)
+    g.set_launch(threads, rows)
+    sg, so = run_both(g, o, W.zeros(70, 33), 60)
+    assert maxabs(sg, so) <= 1e-5 * (1e-4 / (8 * 0.01))
