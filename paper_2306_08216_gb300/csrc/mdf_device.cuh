@@ -112,7 +112,8 @@ __device__ __forceinline__ void tma_load_row(const CUtensorMap *map, uint64_t *b
 
 // Node in pair form: g[j] = (g_{j,u}, g_{j,v}), j = 0..4.
 // Moments shared by fhat, fbar and f: (u, v) = sum_j g_j, the odd
-// differences (g1 - g3), (g2 - g4) and P of Eq. 2.3.23 (R = 0).
+// differences (g1 - g3), (g2 - g4) and P of Eq. 2.3.23 without the source
+// term (moments2r adds it).
 struct Mom2 {
     F2 uv, d13, d24;
     float u, v, P;

@@ -6,7 +6,12 @@
 //           fbar^+ = feq + (I - 3 Lambda/4)(fhat - feq)         (Eq. 2.2.15)
 //   Step 2  fbar(t+h) = fbar^+ - h c_j.grad fbar^+ + h w_j F     (Eq. 2.3.25 / 2.2.11)
 //   Step 3  f(t+h) = feq + (I + h/2 Lt)^-1 (fbar - feq)          (Eq. 2.2.16)
-//   Step 4  fhat(t+dt) = fhat^+ - dt c_j.grad f(t+h) + dt w_j F  (Eq. 2.3.24)
+//   Step 4  fhat(t+dt) = fhat^+ - dt c_j.grad f(t+h)
+//                        + dt w_j (F + dt/2 dF/dt)                (Eq. 2.3.24)
+// The kernels of this file (shared-ring march) serve curvilinear grids; the
+// file also holds the launch planning and dispatch.  Uniform and separable
+// grids run the register-window marches of mdf_step_fast.cu (periodic,
+// Newtonian) and mdf_step_walls.cu (walls and/or power law).
 // The MRT matrix of Eq. 2.2.4 with s0 = s3 = s4 = s' and s1 = s2 = s equals
 // s' I + (s - s') P_c, P_c the projector on the first moments, so every
 // function of it acts on a distribution through its zeroth and first moments
