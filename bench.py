@@ -299,6 +299,43 @@ def storage_benchmark(mdf, W, torch, stream, ref_solver, nx, steps=500, warmup=2
     return out
 
 
+def body_fitted_benchmark(mdf, W, torch, stream, n=513, steps=300, warmup=20, u0=0.1):
+    """Power-law lid-driven cavities on the body-fitted trapezoid grid
+    (n x n nodes, metric coefficients in FP64 at set-up, curvilinear
+    kernel): device-timed MLUPS and the fraction of the measured copy
+    bandwidth at the algorithmic bytes (state + 4 metric planes), for
+    n_index in {0.5, 1, 1.5} and Re in {100, 400, 1000}."""
+    X, Y = W.trapezoid_grid(n, n)
+    peak, _ = measured_peaks()
+    out = []
+    for n_index in (0.5, 1.0, 1.5):
+        for re in (100.0, 400.0, 1000.0):
+            K = u0 ** (2.0 - n_index) / re  # Re = u0^(2-n) L^n / K, L = 1 (lid width)
+            nu_ref = K * u0 ** (n_index - 1.0)
+            s = mdf.Solver(n, n, nu=nu_ref, grid="curvilinear", x=X, y=Y, walls=(True, True),
+                           u_wall=(0, 0, 0, u0), power_law=(K, n_index, nu_ref / 20, nu_ref * 20), stream=stream)
+            s.init(*W.zeros(n, n))
+            s.step(warmup)
+            s.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            bpn = s.bytes_per_node()
+            gbs = bpn * n * n / (ms / 1e3) / 1e9
+            try:
+                r, _ = s.residual()
+            except mdf.MdfError as e:
+                r = "diverged (%s)" % e
+            out.append({"n_index": n_index, "Re": re, "mlups": n * n / (ms / 1e3) / 1e6, "ms_per_step": ms,
+                        "bytes_per_node": bpn, "achieved_gbs": gbs, "frac": gbs / peak, "residual": r})
+            s.close()
+    return {"workload": "power-law lid-driven cavity, isosceles trapezoid (lid 1, bottom 0.5, height 1), "
+                        "%dx%d nodes, curvilinear kernel" % (n, n), "steps": steps, "runs": out}
+
+
 def warm_start_benchmark(stream, count=16, target=1e-8, max_steps=130_000):
     """Learned warm start + batching against cold starts: `count` held-out
     power-law cavities (128 x 128 nodes, the draws the shipped network was
@@ -360,6 +397,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-storage", action="store_true", help="skip the 16-bit storage runs")
     ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start comparison")
+    ap.add_argument("--no-body-fitted", action="store_true", help="skip the trapezoid power-law runs")
     ap.add_argument("--launch", default=None,
                     help="threads,rows_per_block: pin the launch plan instead of the autotuned one (profiling)")
     ap.add_argument("--nx", type=int, default=NX,
@@ -440,6 +478,9 @@ def main():
     # ---- batched sweep: many cavities, one launch per step
     batch = None if args.no_batch else batch_benchmark(mdf, torch, stream)
 
+    # ---- power-law cavities on the body-fitted trapezoid grid
+    body = None if args.no_body_fitted else body_fitted_benchmark(mdf, W, torch, stream)
+
     # ---- learned warm start + batching against cold starts
     warm = None if args.no_warm_start else warm_start_benchmark(stream)
 
@@ -478,6 +519,7 @@ def main():
         "batch": batch,
         "storage": storage,
         "warm_start": warm,
+        "body_fitted": body,
     }
     if ttr and cpu:
         for k in ttr:
