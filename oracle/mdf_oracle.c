@@ -46,15 +46,20 @@
  *     gdot = sqrt(2 S:S), S from the non-equilibrium first moment
  *     (Eqs. 2.4.1, 2.4.3), solved per node from fhat(t) and clamped to
  *     [nu_min, nu_max]; the rates so found serve the whole step at that node.
- *   - Source R of the continuity equation (Eq. 2.1.1) enters only the
+ *   - Source R of the continuity equation (Eq. 2.1.1) enters the
  *     pressure, P = (sum c f + (cs^2/s_1) R - |u|^2)/d (Eq. 2.3.23), with
  *     s_1 = s = cs^2/nu.  Eq. 2.3.23 is stated for f; computed from fhat or
  *     fbar, whose non-equilibrium first moments are (1 + dt s/2) and
  *     (1 + h s/2) times that of f, the R term takes the same factor
  *     (see moments_rk).  Newtonian fluids only (with a power-law viscosity
- *     nu would depend on P through the trace of the non-equilibrium moment).  The alpha = 0 equation is not evolved
- *     (Remark 1: it influences neither u nor P), and the G source is
- *     dropped (Remark 2).
+ *     nu would depend on P through the trace of the non-equilibrium moment).
+ *     The G source is dropped (Remark 2).
+ *   - The alpha = 0 equation (ubar_0 = rho_0, E_0 = 0, source R; Eq. 2.1.2)
+ *     is evolved on request (rho0 != 0) with the same steps, rates and
+ *     stencils: feq_{j,0} = w_j (rho_0 + c_j.(rho_0 u)/cs^2) with u taken
+ *     from the alpha = 1, 2 moments of the same stage, source w_j R.  It
+ *     feeds back into nothing (Remark 1).  Walls: non-equilibrium
+ *     extrapolation with the wall's rho_0 taken equal to the neighbour's.
  *   - dF/dt enters Step 4 as dt^2/2 w_j dF/dt (Eq. 2.3.24); the h^2/2 term
  *     of the fbar update is dropped (Remark 2).  R, F and dF/dt are set by
  *     the caller (constants or fields) and may change between steps.
@@ -87,6 +92,7 @@ typedef struct {
     double fx, fy;
     const double *force_x, *force_y;
     int threads;
+    int rho0;             /* evolve the alpha = 0 distribution */
 } orc_params;
 
 typedef struct {
@@ -103,6 +109,7 @@ typedef struct {
     double *Rs;           /* source R of Eq. 2.1.1 per node */
     double *fh, *fhp, *fbp, *fb, *f, *fn;  /* 10 planes each */
     double *s_node;       /* per-node first-moment rate s */
+    double *r_fh, *r_fhp, *r_fbp, *r_fb, *r_f, *r_fn;  /* alpha = 0: Q planes each (rho0 != 0) */
     double Minv[Q][Q], M[Q][Q];
     /* constant-rate matrices (Newtonian) */
     double A[Q][Q], Ab[Q][Q], L[Q][Q], L34[Q][Q], Rinv[Q][Q], RL[Q][Q];
@@ -305,6 +312,45 @@ static void nee_node(const orc_ctx *o, double *g, int x, int y) {
     for (int a = 0; a < NA; ++a)
         for (int j = 0; j < Q; ++j)
             g[idx(o, a, j, x, y)] = feq_w[a][j] + (g[idx(o, a, j, nxn, nyn)] - feq_n[a][j]);
+}
+
+/* Eq. 2.2.5 for alpha = 0: ubar_0 = rho_0, E_0 = 0. */
+static void equilibrium0(const orc_ctx *o, double rho, double u, double v, double feq[Q]) {
+    for (int j = 0; j < Q; ++j) feq[j] = o->w[j] * (rho + (o->cx[j] * rho * u + o->cy[j] * rho * v) / o->cs2);
+}
+
+static double rho0_at(const orc_ctx *o, const double *r, long n) {
+    double s = 0.0;
+    for (int j = 0; j < Q; ++j) s += r[(long)j * o->N + n];
+    return s;
+}
+
+/* Non-equilibrium extrapolation of the alpha = 0 distribution r at wall
+ * node (x,y): the wall's rho_0 is the neighbour's, the velocities are the
+ * wall's and the neighbour's (from the alpha = 1, 2 distribution g). */
+static void nee_node0(const orc_ctx *o, double *r, const double *g, int x, int y) {
+    int nxn = x, nyn = y;
+    double uw = 0.0, vw = 0.0;
+    int onx = 0;
+    if (xwall(o) && x == 0) { nxn = 1; uw = o->p.u_wall[0]; vw = o->p.v_wall[0]; onx = 1; }
+    if (xwall(o) && x == o->nx - 1) { nxn = o->nx - 2; uw = o->p.u_wall[1]; vw = o->p.v_wall[1]; onx = 1; }
+    if (ywall(o) && y == 0) { nyn = 1; if (!onx) { uw = o->p.u_wall[2]; vw = o->p.v_wall[2]; } }
+    if (ywall(o) && y == o->ny - 1) { nyn = o->ny - 2; if (!onx) { uw = o->p.u_wall[3]; vw = o->p.v_wall[3]; } }
+    double un, vn, Pn;
+    moments(o, g, nxn, nyn, &un, &vn, &Pn);
+    const long nb = (long)nyn * o->nx + nxn, n = (long)y * o->nx + x;
+    const double rho = rho0_at(o, r, nb);
+    double fw[Q], fn[Q];
+    equilibrium0(o, rho, uw, vw, fw);
+    equilibrium0(o, rho, un, vn, fn);
+    for (int j = 0; j < Q; ++j) r[(long)j * o->N + n] = fw[j] + (r[(long)j * o->N + nb] - fn[j]);
+}
+
+static void apply_nee0(const orc_ctx *o, double *r, const double *g) {
+    if (xwall(o))
+        for (int y = 0; y < o->ny; ++y) { nee_node0(o, r, g, 0, y); nee_node0(o, r, g, o->nx - 1, y); }
+    if (ywall(o))
+        for (int x = 0; x < o->nx; ++x) { nee_node0(o, r, g, x, 0); nee_node0(o, r, g, x, o->ny - 1); }
 }
 
 static void apply_nee(const orc_ctx *o, double *g) {
@@ -557,6 +603,10 @@ orc_ctx *orc_create(const orc_params *p) {
     o->fh = alloc0(NF); o->fhp = alloc0(NF); o->fbp = alloc0(NF);
     o->fb = alloc0(NF); o->f = alloc0(NF); o->fn = alloc0(NF);
     o->s_node = alloc0(N);
+    if (p->rho0) {
+        o->r_fh = alloc0(Q * N); o->r_fhp = alloc0(Q * N); o->r_fbp = alloc0(Q * N);
+        o->r_fb = alloc0(Q * N); o->r_f = alloc0(Q * N); o->r_fn = alloc0(Q * N);
+    }
     step_matrices(o, o->cs2 / p->nu, o->A, o->Ab, o->L, o->L34, o->Rinv, o->RL);
     return o;
 }
@@ -567,6 +617,7 @@ void orc_destroy(orc_ctx *o) {
     free(o->Fx); free(o->Fy); free(o->dFx); free(o->dFy); free(o->Rs);
     free(o->fh); free(o->fhp); free(o->fbp); free(o->fb); free(o->f); free(o->fn);
     free(o->s_node);
+    free(o->r_fh); free(o->r_fhp); free(o->r_fbp); free(o->r_fb); free(o->r_f); free(o->r_fn);
     free(o);
 }
 
@@ -622,8 +673,44 @@ void orc_init(orc_ctx *o, const double *u, const double *v, const double *p) {
             equilibrium(o, uu, vv, p[n], feq);
             for (int a = 0; a < NA; ++a)
                 for (int j = 0; j < Q; ++j) o->fh[idx(o, a, j, x, y)] = feq[a][j];
+            if (o->r_fh) {  /* rho_0 = 1 */
+                double f0[Q];
+                equilibrium0(o, 1.0, uu, vv, f0);
+                for (int j = 0; j < Q; ++j) o->r_fh[(long)j * o->N + n] = f0[j];
+            }
         }
     o->steps = 0;
+}
+
+/* alpha = 0 state: fhat_{j,0} = feq_{j,0}(rho0, u) with u from the current
+ * alpha = 1, 2 state; rho0[ny*nx].  Returns -1 if rho0 is not evolved. */
+int orc_init_rho0(orc_ctx *o, const double *rho0) {
+    if (!o->r_fh) return -1;
+    for (int y = 0; y < o->ny; ++y)
+        for (int x = 0; x < o->nx; ++x) {
+            const long n = (long)y * o->nx + x;
+            double u, v, P, f0[Q];
+            moments(o, o->fh, x, y, &u, &v, &P);
+            equilibrium0(o, rho0[n], u, v, f0);
+            for (int j = 0; j < Q; ++j) o->r_fh[(long)j * o->N + n] = f0[j];
+        }
+    return 0;
+}
+/* rho0 = sum_j fhat_{j,0} per node; Q planes of the alpha = 0 state. */
+int orc_rho0(const orc_ctx *o, double *out) {
+    if (!o->r_fh) return -1;
+    for (long n = 0; n < o->N; ++n) out[n] = rho0_at(o, o->r_fh, n);
+    return 0;
+}
+int orc_get_rho0_state(const orc_ctx *o, double *out) {
+    if (!o->r_fh) return -1;
+    memcpy(out, o->r_fh, sizeof(double) * (size_t)Q * o->N);
+    return 0;
+}
+int orc_set_rho0_state(orc_ctx *o, const double *in) {
+    if (!o->r_fh) return -1;
+    memcpy(o->r_fh, in, sizeof(double) * (size_t)Q * o->N);
+    return 0;
 }
 
 void orc_set_state(orc_ctx *o, const double *fh) {
@@ -671,6 +758,20 @@ static void one_step(orc_ctx *o) {
                     o->fbp[idx(o, a, j, x, y)] = t3[j] + t4[j];
                 }
             }
+            if (o->r_fh) {  /* alpha = 0 */
+                const long n = (long)y * nx + x;
+                double g[Q], f0[Q], t1[Q], t2[Q], t3[Q], t4[Q];
+                for (int j = 0; j < Q; ++j) g[j] = o->r_fh[(long)j * N + n];
+                equilibrium0(o, rho0_at(o, o->r_fh, n), u, v, f0);
+                mat_vec(A, g, t1);
+                mat_vec(L, f0, t2);
+                mat_vec(Ab, g, t3);
+                mat_vec(L34, f0, t4);
+                for (int j = 0; j < Q; ++j) {
+                    o->r_fhp[(long)j * N + n] = t1[j] + t2[j];
+                    o->r_fbp[(long)j * N + n] = t3[j] + t4[j];
+                }
+            }
         }
 
     /* Step 2 (Eq. 2.3.25 via Eq. 2.2.11) and Step 3 (Eq. 2.2.16), at nodes
@@ -702,8 +803,22 @@ static void one_step(orc_ctx *o) {
                 mat_vec(RL, feq[a], t2);
                 for (int j = 0; j < Q; ++j) o->f[idx(o, a, j, x, y)] = t1[j] + t2[j];
             }
+            if (o->r_fh) {  /* alpha = 0: source F_{j,0} = w_j R */
+                double g[Q], f0[Q], t1[Q], t2[Q];
+                for (int j = 0; j < Q; ++j) {
+                    const double *plane = o->r_fbp + (long)j * N;
+                    double cg = (j == 0) ? 0.0 : c_dot_grad(o, plane, j, x, y);
+                    o->r_fb[(long)j * N + n] = plane[n] - h * cg + h * o->w[j] * o->Rs[n];
+                }
+                for (int j = 0; j < Q; ++j) g[j] = o->r_fb[(long)j * N + n];
+                equilibrium0(o, rho0_at(o, o->r_fb, n), u, v, f0);
+                mat_vec(Ri, g, t1);
+                mat_vec(RL, f0, t2);
+                for (int j = 0; j < Q; ++j) o->r_f[(long)j * N + n] = t1[j] + t2[j];
+            }
         }
     apply_nee(o, o->f);
+    if (o->r_fh) apply_nee0(o, o->r_f, o->f);
 
     /* Step 4 (Eq. 2.3.24), at nodes that are not walls. */
 #pragma omp parallel for schedule(static)
@@ -720,8 +835,18 @@ static void one_step(orc_ctx *o) {
                     o->fn[idx(o, a, j, x, y)] = o->fhp[idx(o, a, j, x, y)] - dt * cg + dt * o->w[j] * Fa[a] +
                                                 0.5 * dt * dt * o->w[j] * dFa[a];
                 }
+            if (o->r_fh)
+                for (int j = 0; j < Q; ++j) {
+                    const double *plane = o->r_f + (long)j * N;
+                    double cg = (j == 0) ? 0.0 : c_dot_grad(o, plane, j, x, y);
+                    o->r_fn[(long)j * N + n] = o->r_fhp[(long)j * N + n] - dt * cg + dt * o->w[j] * o->Rs[n];
+                }
         }
     apply_nee(o, o->fn);
+    if (o->r_fh) {
+        apply_nee0(o, o->r_fn, o->fn);
+        double *rt = o->r_fh; o->r_fh = o->r_fn; o->r_fn = rt;
+    }
 
     double *t = o->fh; o->fh = o->fn; o->fn = t;
     o->steps++;

@@ -40,6 +40,7 @@ class OrcParams(ctypes.Structure):
         ("fx", ctypes.c_double), ("fy", ctypes.c_double),
         ("force_x", _D), ("force_y", _D),
         ("threads", ctypes.c_int),
+        ("rho0", ctypes.c_int),
     ]
 
 
@@ -82,6 +83,9 @@ def lib():
         L.orc_max_threads.restype = ctypes.c_int
         L.orc_set_force.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]
         L.orc_set_force_rate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]
+        for fn in ("orc_init_rho0", "orc_rho0", "orc_get_rho0_state", "orc_set_rho0_state"):
+            getattr(L, fn).restype = ctypes.c_int
+            getattr(L, fn).argtypes = [ctypes.c_void_p, _D]
         L.orc_set_source.restype = ctypes.c_int
         L.orc_set_source.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _D]
         _lib = L
@@ -108,12 +112,13 @@ class Oracle:
       force             None, (fx, fy) constants, or (Fx[ny,nx], Fy[ny,nx])
       force_rate        dF/dt in the same forms (Eq. 2.3.24)
       source            R of Eq. 2.1.1: None, a constant or R[ny,nx]
+      rho0              also evolve the alpha = 0 distribution (rho_0, Eq. 2.1.2)
     """
 
     def __init__(self, nx, ny, nu=0.01, grid="uniform", lx=1.0, ly=1.0, x=None, y=None,
                  power_law=None, walls=(False, False), u_wall=(0, 0, 0, 0),
                  v_wall=(0, 0, 0, 0), c=1.0, cfl=0.5, eta=0.8, s_ratio=1.5,
-                 force=None, force_rate=None, source=None, threads=0):
+                 force=None, force_rate=None, source=None, rho0=False, threads=0):
         L = lib()
         p = OrcParams()
         p.nx, p.ny = nx, ny
@@ -147,6 +152,7 @@ class Oracle:
             self._keep += [fxa, fya]
             p.force_x, p.force_y = _ptr(fxa), _ptr(fya)
         p.threads = threads
+        p.rho0 = 1 if rho0 else 0
         self._p = p
         h = L.orc_create(ctypes.byref(p))
         if not h:
@@ -177,6 +183,31 @@ class Oracle:
         """dF/dt (None, (dfx, dfy) or fields) used by the next steps."""
         m, a, b, pa, pb, keep = self._pair(rate)
         lib().orc_set_force_rate(self._h, m, a, b, pa, pb)
+
+    def init_rho0(self, rho):
+        """alpha = 0 state feq_{j,0}(rho0, u) with u of the current state."""
+        a = np.ascontiguousarray(rho, dtype=np.float64).ravel()
+        assert a.size == self.nx * self.ny
+        if lib().orc_init_rho0(self._h, _ptr(a)) != 0:
+            raise ValueError("this oracle does not evolve rho0")
+
+    def rho0(self):
+        out = np.empty((self.ny, self.nx))
+        if lib().orc_rho0(self._h, _ptr(out)) != 0:
+            raise ValueError("this oracle does not evolve rho0")
+        return out
+
+    def rho0_state(self):
+        out = np.empty((5, self.ny, self.nx))
+        if lib().orc_get_rho0_state(self._h, _ptr(out)) != 0:
+            raise ValueError("this oracle does not evolve rho0")
+        return out
+
+    def set_rho0_state(self, r):
+        a = np.ascontiguousarray(r, dtype=np.float64)
+        assert a.shape == (5, self.ny, self.nx)
+        if lib().orc_set_rho0_state(self._h, _ptr(a)) != 0:
+            raise ValueError("this oracle does not evolve rho0")
 
     def set_source(self, R):
         """Source R of the continuity equation (None, a constant or a field)."""

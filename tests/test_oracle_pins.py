@@ -489,3 +489,50 @@ def test_source_needs_a_newtonian_fluid():
     o = Oracle(16, 16, nu=0.01, power_law=(0.01, 0.8, 1e-4, 1.0), walls=(True, True))
     with pytest.raises(ValueError):
         o.set_source(0.1)
+
+
+# ------------------------------------------------------- alpha = 0 (rho_0)
+
+
+@pytest.mark.parametrize("c,bound", [(1.0, 1e-2), (2.0, 3e-3)])
+def test_rho0_advects_and_diffuses_a_fourier_mode(c, bound):
+    """The alpha = 0 equation of Eq. 2.1.2 in a uniform flow is a linear
+    convection-diffusion equation: rho_0 = 1 + e sin(k(x - U t)) exp(-nu k^2 t).
+    The error is the D2Q5 kinetic error (falls as 1/c^2)."""
+    n, ny, U, nu, e = 64, 8, 0.05, 0.01, 0.01
+    k = 2 * math.pi
+    X = np.tile(np.arange(n) / n, (ny, 1))
+    o = Oracle(n, ny, nu=nu, lx=1.0, ly=ny / n, c=c, rho0=True)
+    z = np.zeros((ny, n))
+    o.init(np.full((ny, n), U), z, z)
+    o.init_rho0(1 + e * np.sin(k * X))
+    steps = int(round(2.0 / o.dt))
+    o.step(steps)
+    t = steps * o.dt
+    exact = 1 + e * np.sin(k * (X - U * t)) * math.exp(-nu * k * k * t)
+    assert np.abs(o.rho0() - exact).max() <= bound * e
+
+
+def test_rho0_at_rest_grows_with_the_source():
+    """Fluid at rest with a uniform source R: d rho_0/dt = R exactly."""
+    o = Oracle(16, 16, nu=0.01, source=0.02, rho0=True)
+    o.init(*W.zeros(16, 16))
+    o.step(100)
+    np.testing.assert_allclose(o.rho0(), 1.0 + 0.02 * 100 * o.dt, rtol=1e-13)
+
+
+def test_rho0_does_not_feed_back():
+    """Remark 1: the alpha = 1, 2 state is the same with and without the
+    alpha = 0 equation, to the bit."""
+    n = 33
+    states = []
+    for rho in (False, True):
+        o = Oracle(n, n, nu=0.01, walls=(True, True), u_wall=(0, 0, 0, 0.1), rho0=rho)
+        o.init(*W.zeros(n, n))
+        o.step(300)
+        states.append(o.state())
+        if rho:
+            r = o.rho0()
+    np.testing.assert_array_equal(states[0], states[1])
+    # mass of rho_0 is kept by the walls (zero-gradient NEE reading)
+    assert abs(r.mean() - 1.0) < 1e-3
