@@ -90,7 +90,8 @@ typedef struct {
 /* Scheme parameters: lattice speed c (= |c_j|, Eq. 3.1.0), CFL number
  * (Eq. 3.1, 0 < cfl < 1), mixed-scheme weight eta (Eq. 2.2.12, 0..1) and the
  * ratio s'/s of the free rates (Sec. 4 uses 1.5).  A NULL params pointer
- * selects c = 1, cfl = 0.5, eta = 0.8, s_ratio = 1.5, FP32 storage.
+ * selects c = 1, cfl = 0.5, eta = 0.8, s_ratio = 1.5, FP32 storage and no
+ * alpha = 0 distribution.
  *
  * storage selects how the state is kept in device memory between steps (the
  * arithmetic is FP32 in every mode; the paper stores fhat in full
@@ -111,9 +112,21 @@ typedef struct {
  * on the storage mode; checkpoints of the 16-bit modes hold the raw device
  * buffer (see mdf_save). */
 enum { MDF_STORAGE_FP32 = 0, MDF_STORAGE_FP16 = 1, MDF_STORAGE_BF16 = 2 };
+/*
+ * rho0 != 0 also evolves the alpha = 0 distribution of Eq. 2.1.2
+ * (ubar_0 = rho_0, E_0 = 0, so feq_{j,0} = w_j (rho_0 + c_j.(rho_0 u)/cs^2),
+ * source F_{j,0} = w_j R) with the same Steps (1)-(4), rates and stencils,
+ * u taken from the alpha = 1, 2 moments of the same stage.  Remark 1: it
+ * feeds back into neither u nor P, so the alpha = 1, 2 results do not change.
+ * Walls: non-equilibrium extrapolation with the wall's rho_0 equal to the
+ * interior neighbour's (the paper leaves the alpha = 0 wall condition open).
+ * The state grows to 15 FP32 planes (60 B/node) and every grid kind steps
+ * on the general (shared-ring) kernel; FP32 storage only, and batches reject
+ * it (MDF_E_INVALID).  mdf_init_fields starts it at rho_0 = 1. */
 typedef struct {
     double c, cfl, eta, s_ratio;
     int storage;
+    int rho0;
 } mdf_params;
 
 /* Create a solver: validates the arguments (MDF_E_INVALID before any CUDA
@@ -153,15 +166,29 @@ mdf_status mdf_set_force_rate(mdf_ctx *ctx, int mode, double dfx, double dfy,
  * first moments are (1 + dt s/2) and (1 + h s/2) times that of f
  * (Eqs. 2.2.2, 2.2.16), the term becomes (nu + cs^2 dt/2) R / 2 and
  * (nu + cs^2 h/2) R / 2.  Newtonian fluids and FP32 storage only
- * (MDF_E_INVALID otherwise).  The alpha = 0 distribution (rho_0, Remark 1)
- * is not evolved: it influences neither u nor P. */
+ * (MDF_E_INVALID otherwise).  With params->rho0 set, R is also the source
+ * w_j R of the alpha = 0 distribution (Eq. 2.1.2), added in Steps (2) and
+ * (4) like the body force. */
 mdf_status mdf_set_source(mdf_ctx *ctx, int mode, double r, const float *R, int on_device);
 
 /* Initial state fhat = feq(u, v, p) (Sec. 4: distributions start at
  * equilibrium); wall nodes take the wall velocity.  Resets the step count
- * and the residual snapshot. */
+ * and the residual snapshot.  With params->rho0 set, the alpha = 0
+ * distribution starts at feq_{j,0}(1, u). */
 mdf_status mdf_init_fields(mdf_ctx *ctx, const float *u, const float *v, const float *p,
                            int on_device);
+
+/* The alpha = 0 distribution (contexts created with params->rho0 != 0;
+ * MDF_E_INVALID otherwise).  mdf_init_rho0 sets fhat_{j,0} =
+ * feq_{j,0}(rho0, u) (Eq. 2.2.5 with ubar_0 = rho_0, E_0 = 0) with rho0 an
+ * nx*ny FP32 array (row-major [y][x]) and u the velocity of the current
+ * state; the step count is kept.  mdf_get_rho0 writes rho_0 = sum_j
+ * fhat_{j,0} (nx*ny).  mdf_get/set_rho0_distributions copy the 5 planes
+ * [j][ny][nx] of fhat_{j,0}.  Host outputs are complete on return. */
+mdf_status mdf_init_rho0(mdf_ctx *ctx, const float *rho0, int on_device);
+mdf_status mdf_get_rho0(mdf_ctx *ctx, float *out, int on_device);
+mdf_status mdf_get_rho0_distributions(mdf_ctx *ctx, float *out, int on_device);
+mdf_status mdf_set_rho0_distributions(mdf_ctx *ctx, const float *in, int on_device);
 
 /* Enqueue n time steps (Sec. 2.2 Steps (1)-(4)); one fused kernel launch per
  * step.  Asynchronous. */
@@ -202,8 +229,9 @@ mdf_status mdf_synchronize(mdf_ctx *ctx, double timeout_s);
 
 /* Checkpoint: a 256-byte text header (grid size, step count, dt, plane
  * count) followed by the state.  FP32 storage: the 10 planes of
- * mdf_get_distributions, little-endian FP32; mdf_load requires a context of
- * the same grid size.  16-bit storage: the raw padded device buffer (header
+ * mdf_get_distributions, little-endian FP32, then (rho0 contexts, 15 planes)
+ * the 5 of mdf_get_rho0_distributions; mdf_load requires a context of the
+ * same grid size and plane count.  16-bit storage: the raw padded device buffer (header
  * adds the storage mode and row pitch), so a restart continues bitwise;
  * mdf_load then requires a context with the same grid, storage mode and
  * pitch, else MDF_E_INVALID. */

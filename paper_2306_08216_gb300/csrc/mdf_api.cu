@@ -77,7 +77,7 @@ static mdf_status encode_maps_box(mdf_ctx *c, int box_nt, CUtensorMap maps[2]) {
             return fail(c, MDF_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    const int planes = state_planes(c->prm.storage);
+    const int planes = state_planes(c->prm.storage, c->prm.rho0);
     for (int b = 0; b < 2; ++b) {
         cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->ny, (cuuint64_t)planes};
         cuuint64_t strides[2] = {(cuuint64_t)c->pitch * 4, (cuuint64_t)c->plane * 4};
@@ -224,7 +224,7 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
             !finite_pos(fluid->nu_max) || fluid->nu_min > fluid->nu_max)
             return fail(nullptr, MDF_E_INVALID, "power law needs K, n > 0 and 0 < nu_min <= nu_max");
     }
-    mdf_params prm = params ? *params : mdf_params{1.0, 0.5, 0.8, 1.5, MDF_STORAGE_FP32};
+    mdf_params prm = params ? *params : mdf_params{1.0, 0.5, 0.8, 1.5, MDF_STORAGE_FP32, 0};
     if (!finite_pos(prm.c)) return fail(nullptr, MDF_E_INVALID, "c must be > 0");
     if (!(prm.cfl > 0 && prm.cfl < 1)) return fail(nullptr, MDF_E_INVALID, "cfl must be in (0, 1)");
     if (!(prm.eta >= 0 && prm.eta <= 1)) return fail(nullptr, MDF_E_INVALID, "eta must be in [0, 1]");
@@ -238,6 +238,9 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
         !fast_path_applies(grid->kind, fluid->power_law ? 1 : 0, (xwall || ywall) ? 1 : 0))
         return fail(nullptr, MDF_E_INVALID,
                     "16-bit storage needs a periodic Newtonian problem on a uniform or separable grid");
+    if (prm.rho0 && prm.storage != MDF_STORAGE_FP32)
+        return fail(nullptr, MDF_E_INVALID, "the alpha = 0 distribution needs FP32 storage");
+    prm.rho0 = prm.rho0 ? 1 : 0;
 
     mdf_ctx *c = new mdf_ctx();
     c->nx = grid->nx;
@@ -268,8 +271,8 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
     const int metric = grid->kind;
     {
         cudaError_t pe = cudaSuccess;
-        c->ncand = step_candidates(metric, fluid->power_law ? 1 : 0, (xwall || ywall) ? 1 : 0, prm.storage, c->nx,
-                                   c->ny, c->num_sms, c->cand, mdf_ctx::kMaxCandidates, &pe);
+        c->ncand = step_candidates(metric, fluid->power_law ? 1 : 0, (xwall || ywall) ? 1 : 0, prm.storage, prm.rho0,
+                                   c->nx, c->ny, c->num_sms, c->cand, mdf_ctx::kMaxCandidates, &pe);
         CKE(pe);
         if (c->ncand < 1) CKE(cudaErrorInvalidConfiguration);
     }
@@ -280,7 +283,7 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
         if (pt > c->pitch) c->pitch = pt;
     }
     c->plane = (long long)c->pitch * c->ny;
-    const size_t state_bytes = state_buffer_bytes(prm.storage, c->plane);
+    const size_t state_bytes = state_buffer_bytes(prm.storage, c->plane, prm.rho0);
     for (int b = 0; b < 2; ++b) {
         CKE(cudaMalloc(&c->buf[b], state_bytes));
         CKE(cudaMemset(c->buf[b], 0, state_bytes));
@@ -302,6 +305,7 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
     x.nu = (float)fluid->nu; x.K = (float)fluid->K; x.n_index = (float)fluid->n;
     x.nu_min = (float)fluid->nu_min; x.nu_max = (float)fluid->nu_max;
     x.storage = prm.storage;
+    x.rho0 = prm.rho0;
     x.nscale = (float)ldexp(1.0, NSCALE_EXP - ilogb(prm.c));
     x.ninv = (float)ldexp(1.0, ilogb(prm.c) - NSCALE_EXP);
     CKE(cudaMalloc(&c->partials, (size_t)aux_residual_blocks(x) * 5 * sizeof(double)));
@@ -364,6 +368,7 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
 
     StepArgs &a = c->args;
     a.storage = prm.storage;
+    a.rho0 = prm.rho0;
     a.nscale = x.nscale;
     a.ninv = x.ninv;
     a.nx = c->nx; a.ny = c->ny; a.pitch = c->pitch; a.plane = c->plane;
@@ -735,6 +740,75 @@ mdf_status mdf_set_distributions(mdf_ctx *c, const float *in, int on_device) {
     return MDF_OK;
 }
 
+static mdf_status need_rho0(mdf_ctx *c) {
+    return c->prm.rho0 ? MDF_OK : fail(c, MDF_E_INVALID, "this context does not evolve rho_0 (params->rho0 = 0)");
+}
+
+mdf_status mdf_init_rho0(mdf_ctx *c, const float *rho0, int on_device) {
+    if (!c) return MDF_E_INVALID;
+    mdf_status s = need_rho0(c);
+    if (s != MDF_OK) return s;
+    if (!rho0) return fail(c, MDF_E_INVALID, "rho0 is NULL");
+    const float *src[1] = {rho0};
+    s = stage_in(c, src, 1, on_device);
+    if (s != MDF_OK) return s;
+    CK(c, aux_init_rho0(c->aux, c->scratch, c->buf[c->cur], c->stream));
+    if (!on_device) return wait_stream(c, 0);
+    return MDF_OK;
+}
+
+mdf_status mdf_get_rho0(mdf_ctx *c, float *out, int on_device) {
+    if (!c) return MDF_E_INVALID;
+    mdf_status s = need_rho0(c);
+    if (s != MDF_OK) return s;
+    if (!out) return fail(c, MDF_E_INVALID, "out is NULL");
+    const size_t N = (size_t)c->nx * c->ny;
+    if (on_device) {
+        CK(c, aux_rho0_field(c->aux, c->buf[c->cur], out, c->stream));
+        return MDF_OK;
+    }
+    s = ensure_scratch(c, N * sizeof(float));
+    if (s != MDF_OK) return s;
+    CK(c, aux_rho0_field(c->aux, c->buf[c->cur], c->scratch, c->stream));
+    CK(c, cudaMemcpyAsync(out, c->scratch, N * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    return wait_stream(c, 0);
+}
+
+mdf_status mdf_get_rho0_distributions(mdf_ctx *c, float *out, int on_device) {
+    if (!c) return MDF_E_INVALID;
+    mdf_status s = need_rho0(c);
+    if (s != MDF_OK) return s;
+    if (!out) return fail(c, MDF_E_INVALID, "out is NULL");
+    const size_t n = (size_t)5 * c->nx * c->ny;
+    if (on_device) {
+        CK(c, aux_pack_rho0(c->aux, c->buf[c->cur], out, c->stream));
+        return MDF_OK;
+    }
+    s = ensure_scratch(c, n * sizeof(float));
+    if (s != MDF_OK) return s;
+    CK(c, aux_pack_rho0(c->aux, c->buf[c->cur], c->scratch, c->stream));
+    CK(c, cudaMemcpyAsync(out, c->scratch, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    return wait_stream(c, 0);
+}
+
+mdf_status mdf_set_rho0_distributions(mdf_ctx *c, const float *in, int on_device) {
+    if (!c) return MDF_E_INVALID;
+    mdf_status s = need_rho0(c);
+    if (s != MDF_OK) return s;
+    if (!in) return fail(c, MDF_E_INVALID, "in is NULL");
+    const size_t n = (size_t)5 * c->nx * c->ny;
+    const float *src = in;
+    if (!on_device) {
+        s = ensure_scratch(c, n * sizeof(float));
+        if (s != MDF_OK) return s;
+        CK(c, cudaMemcpyAsync(c->scratch, in, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        src = c->scratch;
+    }
+    CK(c, aux_unpack_rho0(c->aux, src, c->buf[c->cur], c->stream));
+    if (!on_device) return wait_stream(c, 0);
+    return MDF_OK;
+}
+
 mdf_status mdf_synchronize(mdf_ctx *c, double timeout_s) {
     if (!c) return MDF_E_INVALID;
     return wait_stream(c, timeout_s);
@@ -764,17 +838,19 @@ static mdf_status save_raw(mdf_ctx *c, const char *path) {
 mdf_status mdf_save(mdf_ctx *c, const char *path) {
     if (!c || !path) return c ? fail(c, MDF_E_INVALID, "path is NULL") : MDF_E_INVALID;
     if (c->prm.storage != MDF_STORAGE_FP32) return save_raw(c, path);
-    const size_t n = (size_t)NPLANES * c->nx * c->ny;
+    const int planes = state_planes(c->prm.storage, c->prm.rho0);
+    const size_t N = (size_t)c->nx * c->ny, n = (size_t)planes * N;
     float *h = (float *)malloc(n * sizeof(float));
     if (!h) return fail(c, MDF_E_NOMEM, "host buffer");
     mdf_status s = mdf_get_distributions(c, h, 0);
+    if (s == MDF_OK && c->prm.rho0) s = mdf_get_rho0_distributions(c, h + NPLANES * N, 0);
     if (s != MDF_OK) { free(h); return s; }
     FILE *fp = fopen(path, "wb");
     if (!fp) { free(h); return fail(c, MDF_E_INVALID, "cannot open %s", path); }
     char hdr[256];
     memset(hdr, 0, sizeof(hdr));
     snprintf(hdr, sizeof(hdr), "MDFCKPT1 nx=%d ny=%d steps=%lld dt=%.17g planes=%d\n", c->nx, c->ny, c->steps, c->dt,
-             NPLANES);
+             planes);
     const bool ok = fwrite(hdr, 1, sizeof(hdr), fp) == sizeof(hdr) && fwrite(h, sizeof(float), n, fp) == n;
     fclose(fp);
     free(h);
@@ -817,17 +893,18 @@ mdf_status mdf_load(mdf_ctx *c, const char *path) {
         if (s == MDF_OK) { c->steps = steps; c->snap_step = steps; }
         return s;
     }
-    if (planes != NPLANES) {
+    if (planes != state_planes(c->prm.storage, c->prm.rho0)) {
         fclose(fp);
-        return fail(c, MDF_E_INVALID, "checkpoint does not match this grid");
+        return fail(c, MDF_E_INVALID, "checkpoint plane count %d does not match this solver", planes);
     }
-    const size_t n = (size_t)NPLANES * c->nx * c->ny;
+    const size_t N = (size_t)c->nx * c->ny, n = (size_t)planes * N;
     float *h = (float *)malloc(n * sizeof(float));
     if (!h) { fclose(fp); return fail(c, MDF_E_NOMEM, "host buffer"); }
     const bool ok = fread(h, sizeof(float), n, fp) == n;
     fclose(fp);
     if (!ok) { free(h); return fail(c, MDF_E_INVALID, "short read from %s", path); }
     mdf_status s = mdf_set_distributions(c, h, 0);
+    if (s == MDF_OK && c->prm.rho0) s = mdf_set_rho0_distributions(c, h + NPLANES * N, 0);
     free(h);
     if (s == MDF_OK) { c->steps = steps; c->snap_step = steps; }
     return s;
@@ -871,7 +948,7 @@ mdf_status mdf_set_launch(mdf_ctx *c, int threads, int rows_per_block) {
 
 double mdf_bytes_per_node(const mdf_ctx *c) {
     if (!c) return NAN;
-    double b = 2.0 * 4.0 * state_planes(c->prm.storage);
+    double b = 2.0 * 4.0 * state_planes(c->prm.storage, c->prm.rho0);
     if (c->force_mode == MDF_FORCE_FIELD) b += 8.0;
     if (c->args.force_mode_d == MDF_FORCE_FIELD && c->args.Fxdp != c->args.Fxp) b += 8.0;
     if (c->args.r_mode == MDF_FORCE_FIELD) b += 4.0;

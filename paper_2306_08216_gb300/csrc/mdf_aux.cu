@@ -29,6 +29,18 @@ __device__ __forceinline__ void equilibrium(float u, float v, float P, float inv
     out[5] = v5; out[6] = v5 + F1y; out[8] = v5 - F1y; out[7] = v5 + F2y; out[9] = v5 - F2y;
 }
 
+// The alpha = 0 equilibrium (Eq. 2.2.5 with ubar_0 = rho_0, E_0 = 0):
+// rho/5 for j = 0 (formed as rho - 4 rho/5, as the step does) and
+// rho/5 +- rho u/(2c), rho/5 +- rho v/(2c) for j = 1, 3 and 2, 4.
+__device__ __forceinline__ void equilibrium0(float rho, float u, float v, float inv2c, float out[5]) {
+    const float r5 = 0.2f * rho, fx = rho * u * inv2c, fy = rho * v * inv2c;
+    out[0] = fmaf(-4.0f, r5, rho);
+    out[1] = r5 + fx;
+    out[3] = r5 - fx;
+    out[2] = r5 + fy;
+    out[4] = r5 - fy;
+}
+
 // ---- access to one node of either state layout ------------------------------
 
 // Non-equilibrium pair n_j = (n_{u,j}, n_{v,j}), j = 1..4, of a 16-bit
@@ -120,6 +132,9 @@ __global__ void init_kernel(AuxArgs a, const float *u, const float *v, const flo
         }
 #pragma unroll
         for (int k = 0; k < NPLANES; ++k) f[k * a.plane + s] = 0.0f;
+        if (a.rho0)
+#pragma unroll
+            for (int j = 0; j < 5; ++j) f[(NPLANES + j) * a.plane + s] = 0.0f;
         return;
     }
     const long long n = (long long)y * a.nx + xs;
@@ -139,6 +154,43 @@ __global__ void init_kernel(AuxArgs a, const float *u, const float *v, const flo
     equilibrium(uu, vv, p[n], a.inv2c, e);
 #pragma unroll
     for (int k = 0; k < NPLANES; ++k) f[k * a.plane + s] = e[k];
+    if (a.rho0) {  // rho_0 = 1 at rest density
+        float e0[5];
+        equilibrium0(1.0f, uu, vv, a.inv2c, e0);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) f[(NPLANES + j) * a.plane + s] = e0[j];
+    }
+}
+
+// alpha = 0 distribution at equilibrium with the given rho_0 and the
+// velocity of the current alpha = 1, 2 state (FP32 storage).
+__global__ void init_rho0_kernel(AuxArgs a, const float *rho0, float *f) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (col >= a.pitch || y >= a.ny) return;
+    const int X = col - GHOST;
+    const long long s = (long long)y * a.pitch + col;
+    int xs = X;
+    if (!a.xwall) xs = wrapi(X, a.nx);
+    else if (X < 0 || X >= a.nx) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) f[(NPLANES + j) * a.plane + s] = 0.0f;
+        return;
+    }
+    float u, v, e0[5];
+    node_uv(a, f, s, u, v);
+    equilibrium0(rho0 ? rho0[(long long)y * a.nx + xs] : 1.0f, u, v, a.inv2c, e0);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) f[(NPLANES + j) * a.plane + s] = e0[j];
+}
+
+// rho_0 = sum_j fhat_{j,0} per node, dense [ny][nx].
+__global__ void rho0_field_kernel(AuxArgs a, const float *f, float *dense) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= a.nx) return;
+    const float *g = f + NPLANES * a.plane + (long long)y * a.pitch + GHOST + x;
+    dense[(long long)y * a.nx + x] = (g[0] + g[a.plane]) + (g[2 * a.plane] + g[3 * a.plane]) + g[4 * a.plane];
 }
 
 // Dense [2][5][ny][nx] <-> padded planes.  On unpack, ghost columns of a
@@ -520,6 +572,26 @@ cudaError_t aux_unpack(const AuxArgs &a, const float *dense, float *f, cudaStrea
         return cudaGetLastError();
     }
     unpack_kernel<<<rows_grid(a.pitch, a.ny, 128, NPLANES), 128, 0, st>>>(a, dense, f);
+    return cudaGetLastError();
+}
+
+cudaError_t aux_init_rho0(const AuxArgs &a, const float *rho0, float *f, cudaStream_t st) {
+    init_rho0_kernel<<<rows_grid(a.pitch, a.ny, 128), 128, 0, st>>>(a, rho0, f);
+    return cudaGetLastError();
+}
+
+cudaError_t aux_rho0_field(const AuxArgs &a, const float *f, float *dense, cudaStream_t st) {
+    rho0_field_kernel<<<rows_grid(a.nx, a.ny, 128), 128, 0, st>>>(a, f, dense);
+    return cudaGetLastError();
+}
+
+cudaError_t aux_pack_rho0(const AuxArgs &a, const float *f, float *dense, cudaStream_t st) {
+    pack_kernel<<<rows_grid(a.nx, a.ny, 128, 5), 128, 0, st>>>(a, f + NPLANES * a.plane, dense);
+    return cudaGetLastError();
+}
+
+cudaError_t aux_unpack_rho0(const AuxArgs &a, const float *dense, float *f, cudaStream_t st) {
+    unpack_kernel<<<rows_grid(a.pitch, a.ny, 128, 5), 128, 0, st>>>(a, dense, f + NPLANES * a.plane);
     return cudaGetLastError();
 }
 

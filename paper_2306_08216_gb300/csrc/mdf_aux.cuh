@@ -20,6 +20,7 @@ struct AuxArgs {
     int r_mode;                                  // source R: 0 none, 1 constant, 2 padded field
     float Rc, rk_hat;                            // constant R; P factor for fhat (Eq. 2.3.23)
     const float *Rp;
+    int rho0;                                    // planes 10..14 hold the alpha = 0 distribution
 };
 
 struct FieldPtrs {
@@ -42,6 +43,13 @@ cudaError_t aux_fields(const AuxArgs &a, const float *f, const FieldPtrs &dst, c
 int aux_residual_blocks(const AuxArgs &a);
 cudaError_t aux_residual(const AuxArgs &a, const float *f, float *su, float *sv, double *partials, double *out,
                          cudaStream_t st);
+// alpha = 0 distribution: fhat_{j,0} = feq_{j,0}(rho0, u) with u from the
+// current state (rho0 dense [ny][nx]; NULL = 1 everywhere); its zeroth
+// moment as a dense field; its 5 planes to / from dense [5][ny][nx].
+cudaError_t aux_init_rho0(const AuxArgs &a, const float *rho0, float *f, cudaStream_t st);
+cudaError_t aux_rho0_field(const AuxArgs &a, const float *f, float *dense, cudaStream_t st);
+cudaError_t aux_pack_rho0(const AuxArgs &a, const float *f, float *dense, cudaStream_t st);
+cudaError_t aux_unpack_rho0(const AuxArgs &a, const float *dense, float *f, cudaStream_t st);
 cudaError_t aux_snapshot(const AuxArgs &a, const float *f, float *su, float *sv, cudaStream_t st);
 
 }  // namespace mdf

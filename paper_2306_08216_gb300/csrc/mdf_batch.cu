@@ -210,9 +210,11 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
     const int metric = grids[0].kind;
     const int power_law = fluids[0].power_law ? 1 : 0;
     const int walls = (bcs[0].type[0] == MDF_BC_WALL || bcs[0].type[2] == MDF_BC_WALL) ? 1 : 0;
-    for (int i = 0; i < count; ++i)
-        if (params && params[i].storage != MDF_STORAGE_FP32)
+    for (int i = 0; i < count && params; ++i) {
+        if (params[i].storage != MDF_STORAGE_FP32)
             return bfail(nullptr, MDF_E_INVALID, "problem %d: batches keep FP32 storage", i);
+        if (params[i].rho0) return bfail(nullptr, MDF_E_INVALID, "problem %d: batches do not evolve rho_0", i);
+    }
     for (int i = 1; i < count; ++i) {
         const int w = (bcs[i].type[0] == MDF_BC_WALL || bcs[i].type[2] == MDF_BC_WALL) ? 1 : 0;
         if (grids[i].kind != metric || (fluids[i].power_law ? 1 : 0) != power_law || w != walls)

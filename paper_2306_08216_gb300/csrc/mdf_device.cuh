@@ -252,6 +252,56 @@ __device__ __forceinline__ F2 stream2(F2 base, F2 pf, F2 p0, F2 pb1, F2 pb2, boo
     return fma2(w1, pf - pb1, fma2(w0, d0, fma2(w2, dfar, base)));
 }
 
+// ---- the alpha = 0 (rho_0) lane: one scalar distribution of 5 populations
+// with ubar_0 = rho_0 and E_0 = 0 (Eq. 2.1.2), feq_{j,0} = w_j (rho_0 +
+// c_j.(rho_0 u)/cs^2): rho_0/5 for j = 0 (as rho_0 - 4 rho_0/5) and
+// rho_0/5 +- rho_0 u/(2c), rho_0/5 +- rho_0 v/(2c) for j = 1,3 and 2,4.
+
+// Non-equilibrium part n = g - feq_0(sum g, u, v).
+__device__ __forceinline__ void noneq0(const float g[5], float u, float v, float inv2c, float n[5]) {
+    const float rho = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
+    const float r5 = 0.2f * rho;
+    const float fx = rho * u * inv2c, fy = rho * v * inv2c;
+    n[0] = g[0] - fmaf(-4.0f, r5, rho);
+    n[1] = g[1] - (r5 + fx);
+    n[3] = g[3] - (r5 - fx);
+    n[2] = g[2] - (r5 + fy);
+    n[4] = g[4] - (r5 - fy);
+}
+
+// The local maps of relax2 on the scalar lane.
+__device__ __forceinline__ void relax0(const float g[5], const float n[5], float mK, float D, float out[5]) {
+    const float dx = D * (n[1] - n[3]), dy = D * (n[2] - n[4]);
+    out[0] = fmaf(mK, n[0], g[0]);
+    out[1] = fmaf(mK, n[1], g[1]) + dx;
+    out[3] = fmaf(mK, n[3], g[3]) - dx;
+    out[2] = fmaf(mK, n[2], g[2]) + dy;
+    out[4] = fmaf(mK, n[4], g[4]) - dy;
+}
+
+// Wall node of the rho_0 lane: g_nb + feq_0(rho_nb, u_w) - feq_0(rho_nb, u_nb)
+// (the wall's rho_0 is the neighbour's; (un, vn) is the neighbour's velocity).
+__device__ __forceinline__ void nee0(const float g[5], float uw, float vw, float un, float vn, float inv2c,
+                                     float out[5]) {
+    const float rho = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
+    const float dx = rho * (uw - un) * inv2c, dy = rho * (vw - vn) * inv2c;
+    out[0] = g[0];
+    out[1] = g[1] + dx;
+    out[3] = g[3] - dx;
+    out[2] = g[2] + dy;
+    out[4] = g[4] - dy;
+}
+
+// stream2 on the scalar lane.
+template <bool WALLS>
+__device__ __forceinline__ float stream1(float base, float pf, float p0, float pb1, float pb2, bool wall_adj, float w1,
+                                         float w0, float w2) {
+    const float d0 = p0 - pb1;
+    float dfar = pb2 - pb1;
+    if (WALLS && wall_adj) dfar = -d0;
+    return fmaf(w1, pf - pb1, fmaf(w0, d0, fmaf(w2, dfar, base)));
+}
+
 __device__ __forceinline__ int wrap(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;
@@ -295,6 +345,23 @@ __device__ __forceinline__ void store_node(const StepArgs &a, int row, int X, co
 // ------------------------------------------------------------ 16-bit storage
 
 // 16-bit pair word (low half: alpha = u, high half: alpha = v) <-> pair.
+// Store the rho_0 lane of one node (planes 10..14), with its periodic
+// images in the ghost columns when the x axis is periodic.
+template <bool XPER>
+__device__ __forceinline__ void store_node0(const StepArgs &a, int row, int X, const float v[5]) {
+    const long long base = (long long)row * a.pitch + GHOST + X;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) a.fout[(NPLANES + j) * a.plane + base] = v[j];
+    if (XPER) {
+        if (X < GHOST)
+#pragma unroll
+            for (int j = 0; j < 5; ++j) a.fout[(NPLANES + j) * a.plane + base + a.nx] = v[j];
+        if (X >= a.nx - GHOST)
+#pragma unroll
+            for (int j = 0; j < 5; ++j) a.fout[(NPLANES + j) * a.plane + base - a.nx] = v[j];
+    }
+}
+
 template <int ST>
 __device__ __forceinline__ F2 unpack16(unsigned w) {
     float2 f;

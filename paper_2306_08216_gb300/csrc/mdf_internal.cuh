@@ -15,6 +15,7 @@ namespace mdf {
 // (written by the step that produces the plane) and are unused otherwise.
 constexpr int GHOST = 4;
 constexpr int NPLANES = 10;
+constexpr int RHO0_PLANES = 15;  // with the alpha = 0 distribution: planes 10..14 = fhat_{j,0}
 
 enum MetricKind { METRIC_UNIFORM = 0, METRIC_SEPARABLE = 1, METRIC_CURVILINEAR = 2 };
 
@@ -32,10 +33,13 @@ constexpr int DEV_FPLANES = 3;  // u, v, P
 constexpr int DEV_PLANES = 7;   // plus 4 pair planes
 constexpr int NSCALE_EXP = 12;
 
-// 32-bit planes of one state buffer.
-inline int state_planes(int storage) { return storage == STORAGE_FP32 ? NPLANES : DEV_PLANES; }
-inline size_t state_buffer_bytes(int storage, long long plane) {
-    return (size_t)state_planes(storage) * plane * 4;
+// 32-bit planes of one state buffer (FP32 storage with the alpha = 0
+// distribution: 15 planes).
+inline int state_planes(int storage, int rho0 = 0) {
+    return storage == STORAGE_FP32 ? (rho0 ? RHO0_PLANES : NPLANES) : DEV_PLANES;
+}
+inline size_t state_buffer_bytes(int storage, long long plane, int rho0 = 0) {
+    return (size_t)state_planes(storage, rho0) * plane * 4;
 }
 
 // Error codes the kernels raise in StepArgs::err (first one wins).
@@ -44,6 +48,7 @@ enum DeviceError { DEVERR_NONE = 0, DEVERR_TMA_TIMEOUT = 1 };
 struct StepArgs {
     float *fout;            // output state (same layout as the input)
     int storage;            // StorageKind of both state buffers
+    int rho0;               // the buffers also hold the alpha = 0 distribution
     float nscale, ninv;     // 16-bit storage: S and 1/S
     int nx, ny, pitch;      // nodes, row pitch in floats
     long long plane;        // floats per plane (pitch * ny)
@@ -113,8 +118,8 @@ struct StepPlan {
 
 // Candidate launch plans of the fused step (the first one is the default);
 // returns how many were written to out[0..max).
-int step_candidates(int metric, int power_law, int walls, int storage, int nx, int ny, int num_sms, StepPlan *out,
-                    int max, cudaError_t *err);
+int step_candidates(int metric, int power_law, int walls, int storage, int rho0, int nx, int ny, int num_sms,
+                    StepPlan *out, int max, cudaError_t *err);
 cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
                         cudaStream_t stream);
 int step_pitch(int nx, int W);
@@ -137,6 +142,12 @@ cudaError_t walls_launch(const CUtensorMap *tmap, const StepArgs &args, int metr
 cudaError_t walls_batch_occupancy(int metric, int power_law, int *nt, int *occ, int *smem);
 cudaError_t walls_batch_launch(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps,
                                int metric, int power_law, int grid, int forced, cudaStream_t stream);
+
+// The shared-ring march with the alpha = 0 distribution (planes 10..14) on
+// every grid kind, FP32 storage (mdf_step_rho0.cu).
+cudaError_t rho0_occupancy(int metric, int power_law, int walls, int *occ, int *smem);
+cudaError_t rho0_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
+                        cudaStream_t stream);
 
 // Periodic Newtonian fast path on uniform/separable grids (mdf_step_fast.cu).
 bool fast_path_applies(int metric, int power_law, int walls);

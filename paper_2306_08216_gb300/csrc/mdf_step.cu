@@ -42,7 +42,7 @@
 // read from HBM once.  Walls use non-equilibrium extrapolation written by the
 // interior neighbour's thread, and the second-order upwind point beyond a
 // wall is replaced by its linear extrapolation Pi(-1) = 2 Pi(0) - Pi(1).
-#include "mdf_device.cuh"
+#include "mdf_march.cuh"
 
 namespace mdf {
 
@@ -50,486 +50,8 @@ namespace {
 
 using namespace dev;
 
-// Shared-memory layout of one ring row: 5 pairs x NT columns, 8 bytes each.
-template <int NT>
-struct Ring {
-    static constexpr int ROW = 5 * NT * 8;  // bytes per ring row
-    static __device__ __forceinline__ int at(int j, int t) { return (j * NT + t) * 8; }
-};
-
-// Difference weights of one axis for pass 1 (h) and pass 2 (dt):
-// w = -step * k * (a1, a0, am2) with k = c/dx (or c times the metric).
-struct AxisW {
-    F2 h1, h0, h2, d1, d0, d2;
-};
-__device__ __forceinline__ AxisW axis_weights(float k, const StepArgs &a) {
-    AxisW w;
-    w.h1 = splat(-a.h * k * a.a1);
-    w.h0 = splat(-a.h * k * a.a0);
-    w.h2 = splat(-a.h * k * a.am2);
-    w.d1 = splat(-a.dt * k * a.a1);
-    w.d0 = splat(-a.dt * k * a.a0);
-    w.d2 = splat(-a.dt * k * a.am2);
-    return w;
-}
-
-// Streaming increment of population j (1..4) at a curvilinear node, added to
-// base: -step (|ct_xi| D_xi + |ct_eta| D_eta), upwinded by the sign of ct.
-// rows[0..4] are the ring rows of chi_eta - 2 .. chi_eta + 2.
-template <int NT>
-__device__ __forceinline__ F2 curvi_term(const unsigned char *const rows[5], int j, int t, float cxi, float ceta,
-                                         bool xadj_p, bool xadj_m, bool yadj_p, bool yadj_m, float step,
-                                         const StepArgs &a, F2 base) {
-    using R = Ring<NT>;
-    const unsigned char *mid = rows[2];
-    const F2 p0 = lds2(mid, R::at(j, t));
-    F2 acc = base;
-    if (cxi != 0.0f) {
-        const float k = -step * fabsf(cxi);
-        const F2 w1 = splat(k * a.a1), w0 = splat(k * a.a0), w2 = splat(k * a.am2);
-        if (cxi > 0.0f)
-            acc = stream2<true>(acc, lds2(mid, R::at(j, t + 1)), p0, lds2(mid, R::at(j, t - 1)),
-                                lds2(mid, R::at(j, t - 2)), xadj_p, w1, w0, w2);
-        else
-            acc = stream2<true>(acc, lds2(mid, R::at(j, t - 1)), p0, lds2(mid, R::at(j, t + 1)),
-                                lds2(mid, R::at(j, t + 2)), xadj_m, w1, w0, w2);
-    }
-    if (ceta != 0.0f) {
-        const float k = -step * fabsf(ceta);
-        const F2 w1 = splat(k * a.a1), w0 = splat(k * a.a0), w2 = splat(k * a.am2);
-        if (ceta > 0.0f)
-            acc = stream2<true>(acc, lds2(rows[3], R::at(j, t)), p0, lds2(rows[1], R::at(j, t)),
-                                lds2(rows[0], R::at(j, t)), yadj_p, w1, w0, w2);
-        else
-            acc = stream2<true>(acc, lds2(rows[1], R::at(j, t)), p0, lds2(rows[3], R::at(j, t)),
-                                lds2(rows[4], R::at(j, t)), yadj_m, w1, w0, w2);
-    }
-    return acc;
-}
-
-// One block's march over strip bx, band by of one problem.  `tmap` is the
-// TMA descriptor of the input state, `a` the problem's arguments (kernel
-// parameter space for a single problem, global memory for a batch).
-template <int NT, int MK, bool PL, bool WALLS>
-__device__ __forceinline__ void march(const CUtensorMap *tmap, const StepArgs &a, int bx, int by, unsigned char *smem,
-                                      int *abort_flag) {
-    using R = Ring<NT>;
-    constexpr int TROW = NPLANES * NT * 4;  // bytes of one TMA row (10 planes x NT floats)
-    unsigned char *tma = smem;
-    unsigned char *ringP = tma + TMA_SLOTS * TROW;   // fhat^+
-    unsigned char *ringB = ringP + RING * R::ROW;    // fbar^+
-    unsigned char *ringF = ringB + RING * R::ROW;    // f(t+h)
-    float *ringK = reinterpret_cast<float *>(ringF + RING * R::ROW);  // power law: recovery rates
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(ringK + (PL ? RING * 2 * NT : 0));
-    int &s_abort = *abort_flag;
-
-    const int t = threadIdx.x;
-    const int x0 = bx * a.W;
-    const int X = x0 - 4 + t;
-    const int y0 = by * a.H;
-    const int y1 = min(y0 + a.H, a.ny);
-    const int nIt = (y1 - y0) + 9;
-    const int rowBase = y0 - 4;
-    const float c = a.c, inv2c = a.inv2c;
-
-    if (t == 0) {
-        s_abort = 0;
-        for (int i = 0; i < TMA_SLOTS; ++i) mbar_init(&mbar[i], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    auto load_row = [&](int it, int slot) {
-        const int p = rowBase + it;
-        const int yy = (WALLS && a.ywall) ? p : wrap(p, a.ny);
-        mbar_expect_tx(&mbar[slot], TROW);
-        tma_load_row(tmap, &mbar[slot], tma + slot * TROW, x0, yy);
-    };
-    int issued = min(TMA_SLOTS, nIt);
-    if (t == 0)
-        for (int i = 0; i < issued; ++i) load_row(i, i);
-
-    // per-column constants
-    const bool xwall = WALLS && a.xwall;
-    const bool ywall = WALLS && a.ywall;
-    const bool colx_wall = xwall && (X == 0 || X == a.nx - 1);
-    const bool colx_out = xwall && (X < 0 || X >= a.nx);
-    const bool xadj_p = xwall && X == 1;
-    const bool xadj_m = xwall && X == a.nx - 2;
-    AxisW wx{}, wy{};
-    if (MK == METRIC_UNIFORM) {
-        wx = axis_weights(a.kx, a);
-        wy = axis_weights(a.ky, a);
-    } else if (MK == METRIC_SEPARABLE) {
-        wx = axis_weights(a.kxv[GHOST + X], a);
-    }
-    const F2 hw = splat(a.h * 0.2f), dw = splat(a.dt * 0.2f);
-    const F2 mKp = splat(-(1.0f - a.rpp)), Dp = splat(0.5f * (a.rp - a.rpp));
-    const F2 mKb = splat(-(1.0f - a.rbp)), Db = splat(0.5f * (a.rb - a.rbp));
-    const F2 mKk = splat(-(1.0f - a.rkp)), Dk = splat(0.5f * (a.rk - a.rkp));
-
-    // Rotating slot offsets: o_k = byte offset of the ring row written k
-    // iterations ago (every ring is indexed by iteration mod 5; o0 is the
-    // slot written in the current iteration).
-    int o0 = 0, o1 = 4 * R::ROW, o2 = 3 * R::ROW, o3 = 2 * R::ROW, o4 = 1 * R::ROW;
-    int k0 = 0, k2 = 3 * 2 * NT;  // the same rotation for the power-law ring (floats)
-    int tslot = 0;
-
-    for (int it = 0; it < nIt; ++it) {
-        const int p = rowBase + it;
-        // ------------------------------------------------ Stage C: row r = p - 5
-        if (it >= 9 && t >= 4 && t < NT - 4) {
-            const int r = p - 5;
-            bool active = (X >= 0 && X < a.nx);
-            if (WALLS) active = active && !colx_wall && !(ywall && (r == 0 || r == a.ny - 1));
-            if (active) {
-                // F rows r-2..r+2 were written 5..1 iterations ago; fhat^+ of
-                // row r 5 iterations ago (slot o0, rewritten by stage A below).
-                const unsigned char *Fm2 = ringF + o0, *Fm1 = ringF + o4, *F0 = ringF + o3;
-                const unsigned char *Fp1 = ringF + o2, *Fp2 = ringF + o1;
-                const unsigned char *Pr = ringP + o0;
-                const bool yadj_p = ywall && r == 1, yadj_m = ywall && r == a.ny - 2;
-                F2 fF = splat(0.0f);
-                if (a.force_mode_d == 1) fF = dw * mk2(a.Fxd, a.Fyd);
-                else if (a.force_mode_d == 2) {
-                    const long long fi = (long long)r * a.pitch + GHOST + X;
-                    fF = dw * mk2(a.Fxdp[fi], a.Fydp[fi]);
-                }
-                F2 out[5];
-#pragma unroll
-                for (int j = 0; j < 5; ++j) out[j] = lds2(Pr, R::at(j, t)) + fF;
-                if (MK != METRIC_CURVILINEAR) {
-                    AxisW wyr = wy;
-                    if (MK == METRIC_SEPARABLE) wyr = axis_weights(a.kyv[r], a);
-                    out[1] = stream2<WALLS>(out[1], lds2(F0, R::at(1, t + 1)), lds2(F0, R::at(1, t)),
-                                            lds2(F0, R::at(1, t - 1)), lds2(F0, R::at(1, t - 2)), xadj_p, wx.d1,
-                                            wx.d0, wx.d2);
-                    out[3] = stream2<WALLS>(out[3], lds2(F0, R::at(3, t - 1)), lds2(F0, R::at(3, t)),
-                                            lds2(F0, R::at(3, t + 1)), lds2(F0, R::at(3, t + 2)), xadj_m, wx.d1,
-                                            wx.d0, wx.d2);
-                    out[2] = stream2<WALLS>(out[2], lds2(Fp1, R::at(2, t)), lds2(F0, R::at(2, t)),
-                                            lds2(Fm1, R::at(2, t)), lds2(Fm2, R::at(2, t)), yadj_p, wyr.d1, wyr.d0,
-                                            wyr.d2);
-                    out[4] = stream2<WALLS>(out[4], lds2(Fm1, R::at(4, t)), lds2(F0, R::at(4, t)),
-                                            lds2(Fp1, R::at(4, t)), lds2(Fp2, R::at(4, t)), yadj_m, wyr.d1, wyr.d0,
-                                            wyr.d2);
-                } else {
-                    const long long mi = (long long)r * a.pitch + GHOST + X;
-                    const float cxx = a.mxx[mi], cxy = a.mxy[mi], cex = a.mex[mi], cey = a.mey[mi];
-                    const unsigned char *const rows[5] = {Fm2, Fm1, F0, Fp1, Fp2};
-                    out[1] = curvi_term<NT>(rows, 1, t, cxx, cex, xadj_p, xadj_m, yadj_p, yadj_m, a.dt, a, out[1]);
-                    out[2] = curvi_term<NT>(rows, 2, t, cxy, cey, xadj_p, xadj_m, yadj_p, yadj_m, a.dt, a, out[2]);
-                    out[3] = curvi_term<NT>(rows, 3, t, -cxx, -cex, xadj_p, xadj_m, yadj_p, yadj_m, a.dt, a, out[3]);
-                    out[4] = curvi_term<NT>(rows, 4, t, -cxy, -cey, xadj_p, xadj_m, yadj_p, yadj_m, a.dt, a, out[4]);
-                }
-                if (!WALLS) {
-                    store_node<true>(a, r, X, out);
-                } else {
-                    // the x axis of a walled kernel may still be periodic
-                    if (xwall) store_node<false>(a, r, X, out);
-                    else store_node<true>(a, r, X, out);
-                    F2 w[5];
-                    if (xadj_p) { nee2(out, a.uw[0], a.vw[0], inv2c, w); store_node<false>(a, r, 0, w); }
-                    if (xadj_m) { nee2(out, a.uw[1], a.vw[1], inv2c, w); store_node<false>(a, r, a.nx - 1, w); }
-                    if (ywall && (r == 1 || r == a.ny - 2)) {
-                        const int rr = (r == 1) ? 0 : a.ny - 1;
-                        const int side = (r == 1) ? 2 : 3;
-                        nee2(out, a.uw[side], a.vw[side], inv2c, w);
-                        if (xwall) store_node<false>(a, rr, X, w);
-                        else store_node<true>(a, rr, X, w);
-                        if (xadj_p) { nee2(out, a.uw[0], a.vw[0], inv2c, w); store_node<false>(a, rr, 0, w); }
-                        if (xadj_m) { nee2(out, a.uw[1], a.vw[1], inv2c, w); store_node<false>(a, rr, a.nx - 1, w); }
-                    }
-                }
-            }
-        }
-        // ------------------------------------------------ Stage A: row p
-        {
-            const bool ok = mbar_wait_bounded(&mbar[tslot], (uint32_t)((it / TMA_SLOTS) & 1));
-            if (!ok) atomicExch(&s_abort, 1);
-            const float *src = reinterpret_cast<const float *>(tma + tslot * TROW);
-            F2 g[5];
-#pragma unroll
-            for (int j = 0; j < 5; ++j) g[j] = mk2(src[j * NT + t], src[(5 + j) * NT + t]);
-            const int pw = (WALLS && ywall) ? p : wrap(p, a.ny);
-            const Mom2 m = a.r_mode && pw >= 0 && pw < a.ny && X >= -GHOST && X < a.nx + GHOST
-                               ? moments2r(g, c, a.rk_hat * source_at(a, pw, X))
-                               : moments2(g, c);
-            F2 n[5];
-            noneq2(g, m, inv2c, n);
-            const F2 n13 = n[1] - n[3], n24 = n[2] - n[4];
-            F2 mKp_ = mKp, Dp_ = Dp, mKb_ = mKb, Db_ = Db;
-            if (PL) {
-                float gx1, gx2, gy1, gy2;
-                split2(splat(c) * n13, gx1, gx2);
-                split2(splat(c) * n24, gy1, gy2);
-                const float sxy = 0.5f * (gy1 + gx2);
-                const float gg = sqrtf(2.0f * (gx1 * gx1 + gy2 * gy2 + 2.0f * sxy * sxy));
-                const Rates Rr = rates_for(a.cs2 / power_law_nu(gg, a), a.s_ratio, a.dt);
-                mKp_ = splat(-(1.0f - Rr.rpp));
-                Dp_ = splat(0.5f * (Rr.rp - Rr.rpp));
-                mKb_ = splat(-(1.0f - Rr.rbp));
-                Db_ = splat(0.5f * (Rr.rb - Rr.rbp));
-                float *k = ringK + k0;
-                k[t] = Rr.rkp;
-                k[NT + t] = Rr.rk;
-            }
-            F2 o[5];
-            relax2(g, n, n13, n24, mKp_, Dp_, o);
-            unsigned char *dP = ringP + o0;
-#pragma unroll
-            for (int j = 0; j < 5; ++j) sts2(dP, R::at(j, t), o[j]);
-            relax2(g, n, n13, n24, mKb_, Db_, o);
-            unsigned char *dB = ringB + o0;
-#pragma unroll
-            for (int j = 0; j < 5; ++j) sts2(dB, R::at(j, t), o[j]);
-        }
-        // all threads are done with TMA slot `tslot`, with the rows stage C
-        // read, and have written the ring rows of stage A
-        if (__syncthreads_or(s_abort)) break;
-        if (t == 0 && issued < nIt) {
-            fence_proxy_async();
-            load_row(issued, tslot);
-            ++issued;
-        }
-        tslot = (tslot == TMA_SLOTS - 1) ? 0 : tslot + 1;
-        // ------------------------------------------------ Stage B: row q = p - 2
-        if (it >= 4 && t >= 2 && t < NT - 2) {
-            const int q = p - 2;
-            bool skip = false;
-            if (WALLS) skip = colx_out || (ywall && (q < 0 || q >= a.ny));
-            // the f row of q goes to slot o0 (the oldest f row, read by stage C above)
-            unsigned char *Fq = ringF + o0;
-            if (!skip) {
-                if (WALLS && ywall && q == a.ny - 1) {
-                    // north wall row: NEE from row ny-2 (this column, written last iteration)
-                    if (!colx_wall) {
-                        const unsigned char *Fn = ringF + o1;
-                        F2 g[5], w[5];
-#pragma unroll
-                        for (int j = 0; j < 5; ++j) g[j] = lds2(Fn, R::at(j, t));
-                        nee2(g, a.uw[3], a.vw[3], inv2c, w);
-#pragma unroll
-                        for (int j = 0; j < 5; ++j) sts2(Fq, R::at(j, t), w[j]);
-                        if (xadj_p) {
-                            nee2(g, a.uw[0], a.vw[0], inv2c, w);
-#pragma unroll
-                            for (int j = 0; j < 5; ++j) sts2(Fq, R::at(j, t - 1), w[j]);
-                        }
-                        if (xadj_m) {
-                            nee2(g, a.uw[1], a.vw[1], inv2c, w);
-#pragma unroll
-                            for (int j = 0; j < 5; ++j) sts2(Fq, R::at(j, t + 1), w[j]);
-                        }
-                    }
-                } else if (!(WALLS && ((ywall && q == 0) || colx_wall))) {
-                    // fbar^+ rows q-2..q+2 were written 4..0 iterations ago
-                    const unsigned char *Bm2 = ringB + o4, *Bm1 = ringB + o3, *B0 = ringB + o2;
-                    const unsigned char *Bp1 = ringB + o1, *Bp2 = ringB + o0;
-                    const int qw = (WALLS && ywall) ? q : wrap(q, a.ny);
-                    const bool yadj_p = ywall && q == 1, yadj_m = ywall && q == a.ny - 2;
-                    F2 fF = splat(0.0f);
-                    if (a.force_mode == 1) fF = hw * mk2(a.Fx, a.Fy);
-                    else if (a.force_mode == 2) {
-                        const long long fi = (long long)qw * a.pitch + GHOST + X;
-                        fF = hw * mk2(a.Fxp[fi], a.Fyp[fi]);
-                    }
-                    // Step 2 (pass 1): fbar = fbar^+ - h c.grad fbar^+ + h w F
-                    F2 fb[5];
-#pragma unroll
-                    for (int j = 0; j < 5; ++j) fb[j] = lds2(B0, R::at(j, t)) + fF;
-                    if (MK != METRIC_CURVILINEAR) {
-                        AxisW wyq = wy;
-                        if (MK == METRIC_SEPARABLE) wyq = axis_weights(a.kyv[qw], a);
-                        fb[1] = stream2<WALLS>(fb[1], lds2(B0, R::at(1, t + 1)), lds2(B0, R::at(1, t)),
-                                               lds2(B0, R::at(1, t - 1)), lds2(B0, R::at(1, t - 2)), xadj_p, wx.h1,
-                                               wx.h0, wx.h2);
-                        fb[3] = stream2<WALLS>(fb[3], lds2(B0, R::at(3, t - 1)), lds2(B0, R::at(3, t)),
-                                               lds2(B0, R::at(3, t + 1)), lds2(B0, R::at(3, t + 2)), xadj_m, wx.h1,
-                                               wx.h0, wx.h2);
-                        fb[2] = stream2<WALLS>(fb[2], lds2(Bp1, R::at(2, t)), lds2(B0, R::at(2, t)),
-                                               lds2(Bm1, R::at(2, t)), lds2(Bm2, R::at(2, t)), yadj_p, wyq.h1, wyq.h0,
-                                               wyq.h2);
-                        fb[4] = stream2<WALLS>(fb[4], lds2(Bm1, R::at(4, t)), lds2(B0, R::at(4, t)),
-                                               lds2(Bp1, R::at(4, t)), lds2(Bp2, R::at(4, t)), yadj_m, wyq.h1, wyq.h0,
-                                               wyq.h2);
-                    } else {
-                        const long long mi = (long long)qw * a.pitch + GHOST + X;
-                        const float cxx = a.mxx[mi], cxy = a.mxy[mi], cex = a.mex[mi], cey = a.mey[mi];
-                        const unsigned char *const rows[5] = {Bm2, Bm1, B0, Bp1, Bp2};
-                        fb[1] = curvi_term<NT>(rows, 1, t, cxx, cex, xadj_p, xadj_m, yadj_p, yadj_m, a.h, a, fb[1]);
-                        fb[2] = curvi_term<NT>(rows, 2, t, cxy, cey, xadj_p, xadj_m, yadj_p, yadj_m, a.h, a, fb[2]);
-                        fb[3] = curvi_term<NT>(rows, 3, t, -cxx, -cex, xadj_p, xadj_m, yadj_p, yadj_m, a.h, a, fb[3]);
-                        fb[4] = curvi_term<NT>(rows, 4, t, -cxy, -cey, xadj_p, xadj_m, yadj_p, yadj_m, a.h, a, fb[4]);
-                    }
-                    // Step 3: f = feq + (I + h/2 Lt)^-1 (fbar - feq)
-                    F2 mKk_ = mKk, Dk_ = Dk;
-                    if (PL) {
-                        const float *k = ringK + k2;  // rates of row q, written 2 iterations ago
-                        mKk_ = splat(-(1.0f - k[t]));
-                        Dk_ = splat(0.5f * (k[NT + t] - k[t]));
-                    }
-                    const Mom2 m = a.r_mode ? moments2r(fb, c, a.rk_bar * source_at(a, qw, X)) : moments2(fb, c);
-                    F2 n[5], f[5];
-                    noneq2(fb, m, inv2c, n);
-                    relax2(fb, n, n[1] - n[3], n[2] - n[4], mKk_, Dk_, f);
-#pragma unroll
-                    for (int j = 0; j < 5; ++j) sts2(Fq, R::at(j, t), f[j]);
-                    if (WALLS) {
-                        F2 w[5];
-                        if (xadj_p) {  // west wall node of this row
-                            nee2(f, a.uw[0], a.vw[0], inv2c, w);
-#pragma unroll
-                            for (int j = 0; j < 5; ++j) sts2(Fq, R::at(j, t - 1), w[j]);
-                        }
-                        if (xadj_m) {
-                            nee2(f, a.uw[1], a.vw[1], inv2c, w);
-#pragma unroll
-                            for (int j = 0; j < 5; ++j) sts2(Fq, R::at(j, t + 1), w[j]);
-                        }
-                        if (ywall && q == 1) {  // south wall row (and corners) from row 1
-                            unsigned char *F0r = ringF + o1;
-                            nee2(f, a.uw[2], a.vw[2], inv2c, w);
-#pragma unroll
-                            for (int j = 0; j < 5; ++j) sts2(F0r, R::at(j, t), w[j]);
-                            if (xadj_p) {
-                                nee2(f, a.uw[0], a.vw[0], inv2c, w);
-#pragma unroll
-                                for (int j = 0; j < 5; ++j) sts2(F0r, R::at(j, t - 1), w[j]);
-                            }
-                            if (xadj_m) {
-                                nee2(f, a.uw[1], a.vw[1], inv2c, w);
-#pragma unroll
-                                for (int j = 0; j < 5; ++j) sts2(F0r, R::at(j, t + 1), w[j]);
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // rotate: the slot written in this iteration becomes "1 iteration ago"
-        {
-            const int tmp = o4;
-            o4 = o3; o3 = o2; o2 = o1; o1 = o0; o0 = tmp;
-            if (PL) {
-                k0 = (k0 == 4 * 2 * NT) ? 0 : k0 + 2 * NT;
-                k2 = (k2 == 4 * 2 * NT) ? 0 : k2 + 2 * NT;
-            }
-        }
-    }
-    // On an aborted march, wait (bounded) for the row copies still in flight
-    // before the block's shared memory is released, and report the fault.
-    if (s_abort) {
-        if (t == 0) {
-            for (int it = issued - TMA_SLOTS; it < issued; ++it) {
-                if (it < 0) continue;
-                mbar_wait_bounded(&mbar[it % TMA_SLOTS], (uint32_t)((it / TMA_SLOTS) & 1));
-            }
-            atomicCAS(a.err, DEVERR_NONE, DEVERR_TMA_TIMEOUT);
-        }
-    }
-    // every copy was consumed: the barriers may be invalidated for reuse
-    __syncthreads();
-    if (t == 0)
-        for (int i = 0; i < TMA_SLOTS; ++i) mbar_inval(&mbar[i]);
-    __syncthreads();
-}
-
-template <int NT, int MK, bool PL, bool WALLS>
-__global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ int s_abort;
-    march<NT, MK, PL, WALLS>(&tmap, a, blockIdx.x, blockIdx.y, smem, &s_abort);
-}
-
-// Many problems in one persistent launch: block b takes work items
-// b, b + gridDim.x, ... of the table (problem, strip, band), which lists the
-// largest problems first.  Arguments and TMA descriptors live in global memory.
-template <int NT, int MK, bool PL, bool WALLS>
-__global__ void __launch_bounds__(NT) batch_kernel(const BatchItem *__restrict__ items, int nitems,
-                                                   const StepArgs *__restrict__ args,
-                                                   const CUtensorMap *__restrict__ maps) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ int s_abort;
-    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-        const BatchItem item = items[w];
-        march<NT, MK, PL, WALLS>(&maps[item.problem], args[item.problem], item.bx, item.by, smem, &s_abort);
-        if (s_abort) break;
-    }
-}
-
-template <int NT, int MK, bool PL, bool WALLS>
-int smem_bytes() {
-    return TMA_SLOTS * NPLANES * NT * 4 + 3 * RING * Ring<NT>::ROW + (PL ? RING * 2 * NT * 4 : 0) + TMA_SLOTS * 8;
-}
-
-template <int NT, int MK, bool PL, bool WALLS>
-cudaError_t launch_t(const CUtensorMap *tmap, const StepArgs &args, const StepPlan &plan, cudaStream_t stream) {
-    auto k = step_kernel<NT, MK, PL, WALLS>;
-    const int smem = smem_bytes<NT, MK, PL, WALLS>();
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    k<<<dim3(plan.gx, plan.gy), NT, smem, stream>>>(*tmap, args);
-    return cudaGetLastError();
-}
-
-template <int NT, int MK, bool PL, bool WALLS>
-cudaError_t occupancy_t(int *occ, int *smem) {
-    auto k = step_kernel<NT, MK, PL, WALLS>;
-    *smem = smem_bytes<NT, MK, PL, WALLS>();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, NT, *smem);
-}
-
-template <int NT, int MK, bool PL, bool WALLS>
-cudaError_t batch_launch_t(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps,
-                           int grid, cudaStream_t stream) {
-    auto k = batch_kernel<NT, MK, PL, WALLS>;
-    const int smem = smem_bytes<NT, MK, PL, WALLS>();
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    k<<<grid, NT, smem, stream>>>(items, nitems, args, maps);
-    return cudaGetLastError();
-}
-
-template <int NT, int MK, bool PL, bool WALLS>
-cudaError_t batch_occupancy_t(int *occ, int *smem) {
-    auto k = batch_kernel<NT, MK, PL, WALLS>;
-    *smem = smem_bytes<NT, MK, PL, WALLS>();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, NT, *smem);
-}
-
-constexpr int kNT = 128;
-
-#define MDF_DISPATCH(FN, ...)                                                         \
-    switch (metric * 4 + (power_law ? 2 : 0) + (walls ? 1 : 0)) {                     \
-        case 0: return FN<kNT, METRIC_UNIFORM, false, false>(__VA_ARGS__);            \
-        case 1: return FN<kNT, METRIC_UNIFORM, false, true>(__VA_ARGS__);             \
-        case 2: return FN<kNT, METRIC_UNIFORM, true, false>(__VA_ARGS__);             \
-        case 3: return FN<kNT, METRIC_UNIFORM, true, true>(__VA_ARGS__);              \
-        case 4: return FN<kNT, METRIC_SEPARABLE, false, false>(__VA_ARGS__);          \
-        case 5: return FN<kNT, METRIC_SEPARABLE, false, true>(__VA_ARGS__);           \
-        case 6: return FN<kNT, METRIC_SEPARABLE, true, false>(__VA_ARGS__);           \
-        case 7: return FN<kNT, METRIC_SEPARABLE, true, true>(__VA_ARGS__);            \
-        case 8: return FN<kNT, METRIC_CURVILINEAR, false, false>(__VA_ARGS__);        \
-        case 9: return FN<kNT, METRIC_CURVILINEAR, false, true>(__VA_ARGS__);         \
-        case 10: return FN<kNT, METRIC_CURVILINEAR, true, false>(__VA_ARGS__);        \
-        default: return FN<kNT, METRIC_CURVILINEAR, true, true>(__VA_ARGS__);         \
-    }
-
 cudaError_t occupancy(int metric, int power_law, int walls, int *occ, int *smem) {
-    MDF_DISPATCH(occupancy_t, occ, smem)
+    MDF_MARCH_DISPATCH(false, occupancy_t, occ, smem)
 }
 
 }  // namespace
@@ -562,17 +84,18 @@ static void fill_plan(int nt, int occ, int smem, int waves, int nx, int ny, int 
     plan->gy = (ny + H - 1) / H;
 }
 
-int step_candidates(int metric, int power_law, int walls, int storage, int nx, int ny, int num_sms, StepPlan *out,
-                    int max, cudaError_t *err) {
+int step_candidates(int metric, int power_law, int walls, int storage, int rho0, int nx, int ny, int num_sms,
+                    StepPlan *out, int max, cudaError_t *err) {
     int n = 0;
     *err = cudaSuccess;
-    const bool fast = fast_path_applies(metric, power_law, walls);
-    const bool wpath = !fast && walls_path_applies(metric, power_law, walls, storage);
+    const bool fast = !rho0 && fast_path_applies(metric, power_law, walls);
+    const bool wpath = !rho0 && !fast && walls_path_applies(metric, power_law, walls, storage);
     const int nts[2] = {128, 256};
     for (int i = 0; i < (fast || wpath ? 2 : 1); ++i) {
         int occ = 0, smem = 0;
         cudaError_t e = fast    ? fast_occupancy(metric, storage, nts[i], &occ, &smem)
                         : wpath ? walls_occupancy(metric, power_law, nts[i], &occ, &smem)
+                        : rho0  ? rho0_occupancy(metric, power_law, walls, &occ, &smem)
                                 : occupancy(metric, power_law, walls, &occ, &smem);
         if (e != cudaSuccess) {
             *err = e;
@@ -586,25 +109,26 @@ int step_candidates(int metric, int power_law, int walls, int storage, int nx, i
 
 cudaError_t batch_occupancy(int metric, int power_law, int walls, int *nt, int *occ, int *smem) {
     if (metric != METRIC_CURVILINEAR) return walls_batch_occupancy(metric, power_law, nt, occ, smem);
-    *nt = kNT;
-    MDF_DISPATCH(batch_occupancy_t, occ, smem)
+    *nt = kMarchNT;
+    MDF_CURVI_DISPATCH(batch_occupancy_t, occ, smem)
 }
 
 cudaError_t batch_launch(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps, int metric,
                          int power_law, int walls, int grid, int forced, cudaStream_t stream) {
     if (metric != METRIC_CURVILINEAR)
         return walls_batch_launch(items, nitems, args, maps, metric, power_law, grid, forced, stream);
-    MDF_DISPATCH(batch_launch_t, items, nitems, args, maps, grid, stream)
+    MDF_CURVI_DISPATCH(batch_launch_t, items, nitems, args, maps, grid, stream)
 }
 
 cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
                         cudaStream_t stream) {
     const int power_law = args.power_law;
     const int walls = (args.xwall || args.ywall) ? 1 : 0;
+    if (args.rho0) return rho0_launch(tmap, args, metric, plan, stream);
     if (fast_path_applies(metric, power_law, walls)) return fast_launch(tmap, args, metric, plan, stream);
     if (walls_path_applies(metric, power_law, walls, args.storage))
         return walls_launch(tmap, args, metric, plan, stream);
-    MDF_DISPATCH(launch_t, tmap, args, plan, stream)
+    MDF_MARCH_DISPATCH(false, launch_t, tmap, args, plan, stream)
 }
 
 }  // namespace mdf

@@ -52,7 +52,7 @@ class BC(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("cfl", ctypes.c_double), ("eta", ctypes.c_double),
-                ("s_ratio", ctypes.c_double), ("storage", ctypes.c_int)]
+                ("s_ratio", ctypes.c_double), ("storage", ctypes.c_int), ("rho0", ctypes.c_int)]
 
 
 # mdf_params.storage: how the state is kept between steps (arithmetic is FP32)
@@ -73,6 +73,10 @@ _SIGNATURES = [
                                       ctypes.c_int]),
     ("mdf_init_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_int]),
+    ("mdf_init_rho0", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("mdf_get_rho0", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("mdf_get_rho0_distributions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("mdf_set_rho0_distributions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("mdf_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("mdf_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
     ("mdf_residual", ctypes.c_int, [ctypes.c_void_p, _D, _D]),
@@ -173,7 +177,7 @@ class _Arr:
 
 def problem_structs(nx, ny, nu=0.01, grid="uniform", lx=1.0, ly=1.0, x=None, y=None, power_law=None,
                     walls=(False, False), u_wall=(0, 0, 0, 0), v_wall=(0, 0, 0, 0), c=1.0, cfl=0.5, eta=0.8,
-                    s_ratio=1.5, storage="fp32"):
+                    s_ratio=1.5, storage="fp32", rho0=False):
     """The C structs (mdf_grid, mdf_fluid, mdf_bc, mdf_params) of one problem,
     plus the arrays they point to (keep them alive while the structs are used)."""
     keep = []
@@ -194,7 +198,7 @@ def problem_structs(nx, ny, nu=0.01, grid="uniform", lx=1.0, ly=1.0, x=None, y=N
         b.v_wall[k] = v_wall[k]
     if storage not in STORAGE:
         raise ValueError("storage must be one of %s" % sorted(STORAGE))
-    p = Params(c, cfl, eta, s_ratio, STORAGE[storage])
+    p = Params(c, cfl, eta, s_ratio, STORAGE[storage], 1 if rho0 else 0)
     return g, f, b, p, keep
 
 
@@ -207,20 +211,22 @@ class Solver:
     (west, east, south, north), c, cfl, eta, s_ratio, force (None, (fx, fy)
     constants or (Fx, Fy) fields), and storage ("fp32", or "fp16" / "bf16":
     u, v, P in FP32 plus the non-equilibrium part in 16 bits; periodic
-    Newtonian problems on uniform or separable grids only).
+    Newtonian problems on uniform or separable grids only), force_rate,
+    source, and rho0 (True: also evolve the alpha = 0 distribution of
+    Eq. 2.1.2, which starts at rho_0 = 1; FP32 storage only).
     """
 
     def __init__(self, nx, ny, nu=0.01, grid="uniform", lx=1.0, ly=1.0, x=None, y=None,
                  power_law=None, walls=(False, False), u_wall=(0, 0, 0, 0), v_wall=(0, 0, 0, 0),
                  c=1.0, cfl=0.5, eta=0.8, s_ratio=1.5, force=None, stream=None, storage="fp32", force_rate=None,
-                 source=None, _handle=None):
+                 source=None, rho0=False, _handle=None):
         self.nx, self.ny = nx, ny
         self._owned = _handle is None
         if _handle is not None:  # a problem of a batch: the batch owns the context
             self._h = _handle
             return
         g, f, b, p, self._keep = problem_structs(nx, ny, nu, grid, lx, ly, x, y, power_law, walls, u_wall, v_wall,
-                                                 c, cfl, eta, s_ratio, storage)
+                                                 c, cfl, eta, s_ratio, storage, rho0)
         h = ctypes.c_void_p()
         _check(lib().mdf_create(ctypes.byref(g), ctypes.byref(f), ctypes.byref(b), ctypes.byref(p), ctypes.byref(h)))
         self._h = h
@@ -300,6 +306,31 @@ class Solver:
         a = [_Arr(t, n) for t in (u, v, p)]
         _check(lib().mdf_init_fields(self._h, a[0].ptr, a[1].ptr, a[2].ptr, a[0].on_device), self._h)
         if a[0].on_device:
+            self.synchronize()
+
+    def init_rho0(self, rho0):
+        """fhat_{j,0} = feq_{j,0}(rho0, u) with u of the current state."""
+        a = _Arr(rho0, self.nx * self.ny)
+        _check(lib().mdf_init_rho0(self._h, a.ptr, a.on_device), self._h)
+        if a.on_device:
+            self.synchronize()
+
+    def rho0(self):
+        """rho_0 = sum_j fhat_{j,0} as float32 [ny, nx]."""
+        out = np.empty((self.ny, self.nx), dtype=np.float32)
+        _check(lib().mdf_get_rho0(self._h, out.ctypes.data_as(ctypes.c_void_p), 0), self._h)
+        return out
+
+    def rho0_state(self):
+        """fhat_{j,0} as float32 [5, ny, nx]."""
+        out = np.empty((5, self.ny, self.nx), dtype=np.float32)
+        _check(lib().mdf_get_rho0_distributions(self._h, out.ctypes.data_as(ctypes.c_void_p), 0), self._h)
+        return out
+
+    def set_rho0_state(self, g):
+        a = _Arr(g, 5 * self.nx * self.ny)
+        _check(lib().mdf_set_rho0_distributions(self._h, a.ptr, a.on_device), self._h)
+        if a.on_device:
             self.synchronize()
 
     def step(self, n=1):

@@ -119,6 +119,27 @@ def test_batch_rejects_16bit_storage(lib):
     assert b"FP32 storage" in lib.mdf_batch_last_error(None)
 
 
+def test_rho0_needs_fp32_storage(lib):
+    g, f, b, p = mdf.problem_structs(16, 16, storage="bf16", rho0=True)[:4]
+    st, msg = mdf.create_status(g, f, b, p)
+    assert st == mdf.MDF_E_INVALID and "alpha = 0" in msg, (st, msg)
+
+
+def test_batch_rejects_rho0(lib):
+    g, f, b, p = _good()
+    p.rho0 = 1
+    G, F, B, P = (mdf.Grid * 2)(g, g), (mdf.Fluid * 2)(f, f), (mdf.BC * 2)(b, b), (mdf.Params * 2)(p, p)
+    h = ctypes.c_void_p()
+    assert lib.mdf_batch_create(2, G, F, B, P, ctypes.byref(h)) == mdf.MDF_E_INVALID
+    assert b"rho_0" in lib.mdf_batch_last_error(None)
+
+
+def test_rho0_calls_reject_null_contexts(lib):
+    for fn in (lib.mdf_init_rho0, lib.mdf_get_rho0, lib.mdf_get_rho0_distributions,
+               lib.mdf_set_rho0_distributions):
+        assert fn(None, None, 0) == mdf.MDF_E_INVALID
+
+
 def test_storage_names():
     assert mdf.STORAGE == {"fp32": 0, "fp16": 1, "bf16": 2}
     with pytest.raises(ValueError):
