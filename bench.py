@@ -299,6 +299,38 @@ def storage_benchmark(mdf, W, torch, stream, ref_solver, nx, steps=500, warmup=2
     return out
 
 
+def rho0_benchmark(mdf, W, torch, stream, nx, steps=300, warmup=20):
+    """The Taylor-Green workload with the alpha = 0 distribution of Eq. 2.1.2
+    evolved beside alpha = 1, 2 (rho_0 = 1 + 0.1 sin 2 pi x cos 2 pi y; 15
+    FP32 planes, general shared-ring kernel): device-timed MLUPS, the
+    fraction of the measured copy bandwidth at 120 B per node, and the
+    change of total rho_0 (conserved on a periodic grid without source)."""
+    import numpy as np
+    u, v, p = W.taylor_green(nx, U0)
+    X, Y = np.meshgrid(np.arange(nx) / nx, np.arange(nx) / nx)
+    s = mdf.Solver(nx, nx, nu=NU, lx=2 * math.pi, ly=2 * math.pi, stream=stream, rho0=True)
+    s.init(u, v, p)
+    s.init_rho0(1 + 0.1 * np.sin(2 * math.pi * X) * np.cos(2 * math.pi * Y))
+    m0 = float(s.rho0().astype(np.float64).sum())
+    s.step(warmup)
+    s.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    bpn = s.bytes_per_node()
+    gbs = bpn * nx * nx / (ms / 1e3) / 1e9
+    peak, _ = measured_peaks()
+    m1 = float(s.rho0().astype(np.float64).sum())
+    out = {"workload": "taylor_green_%dx%d_fp32_rho0" % (nx, nx), "mlups": nx * nx / (ms / 1e3) / 1e6,
+           "ms_per_step": ms, "bytes_per_node": bpn, "achieved_gbs": gbs, "frac": gbs / peak,
+           "rho0_total_rel_change": (m1 - m0) / m0, "steps": warmup + steps, "launch": s.launch_info()}
+    del s
+    return out
+
+
 def body_fitted_benchmark(mdf, W, torch, stream, n=513, steps=300, warmup=20, u0=0.1):
     """Power-law lid-driven cavities on the body-fitted trapezoid grid
     (n x n nodes, metric coefficients in FP64 at set-up, curvilinear
@@ -398,6 +430,7 @@ def main():
     ap.add_argument("--no-storage", action="store_true", help="skip the 16-bit storage runs")
     ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start comparison")
     ap.add_argument("--no-body-fitted", action="store_true", help="skip the trapezoid power-law runs")
+    ap.add_argument("--no-rho0", action="store_true", help="skip the run with the alpha = 0 distribution")
     ap.add_argument("--launch", default=None,
                     help="threads,rows_per_block: pin the launch plan instead of the autotuned one (profiling)")
     ap.add_argument("--nx", type=int, default=NX,
@@ -475,6 +508,9 @@ def main():
     # ---- 16-bit deviation storage on the same workload
     storage = None if args.no_storage else storage_benchmark(mdf, W, torch, stream, solver, nx)
 
+    # ---- the same workload with the alpha = 0 distribution evolved
+    rho0 = None if args.no_rho0 else rho0_benchmark(mdf, W, torch, stream, nx)
+
     # ---- batched sweep: many cavities, one launch per step
     batch = None if args.no_batch else batch_benchmark(mdf, torch, stream)
 
@@ -520,6 +556,7 @@ def main():
         "storage": storage,
         "warm_start": warm,
         "body_fitted": body,
+        "rho0": rho0,
     }
     if ttr and cpu:
         for k in ttr:

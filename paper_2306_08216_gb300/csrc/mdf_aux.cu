@@ -3,7 +3,9 @@
 // fields (Sec. 2.4), the FP64 residual/drift reduction, and the packing
 // between the padded plane layout and dense caller arrays.  Every kernel
 // reads and writes both state layouts (10 FP32 planes, or u, v, P in FP32
-// plus 8 16-bit non-equilibrium planes).
+// plus 8 16-bit non-equilibrium planes); with the alpha = 0 distribution
+// the FP32 layout has 5 more planes, which the *_rho0 kernels initialise,
+// sum and copy.
 #include <math.h>
 
 #include "mdf_aux.cuh"

@@ -2,6 +2,36 @@
 // grids, and every grid when the alpha = 0 distribution is evolved): the
 // device function, its kernels and their launch helpers, included by
 // mdf_step.cu (alpha = 1, 2 only) and mdf_step_rho0.cu (with alpha = 0).
+//
+// Arithmetic layout.  The two distributions alpha = u, v (Eq. 2.1.2 with
+// alpha = 1, 2) see the same collision rates and the same difference
+// weights, so each population j is carried as one 64-bit pair
+// (fhat_{j,u}, fhat_{j,v}) and processed with the packed FP32 instructions
+// of sm_100-family GPUs (add/sub/mul/fma .f32x2); shared rings hold the
+// pairs, so every ring access is one 64-bit load or store.
+//
+// Work decomposition.  A block owns a strip of W = NT - 8 output columns and
+// marches down a band of H rows.  Thread t holds column x0 - 4 + t; the 8
+// extra columns are the halo of the two chained stencils (reach 2 + 2).  Per
+// row of the march, with p the newest row:
+//   C: fhat(t+dt) of row r = p - 5 from the f ring and the fhat^+ ring -> HBM;
+//   A: row p of fhat arrives by TMA (one 3-D box of 10 planes x NT columns);
+//      fhat^+ and fbar^+ of row p go to their rings;
+//   -- barrier --
+//   B: fbar and f(t+h) of row q = p - 2 (x stencils across threads, y
+//      stencils across ring rows) go to the f ring; walls by NEE;
+//   -- barrier --
+// All rings have five rows; slot offsets rotate by one each row.  Only the x
+// halo (8 of NT columns) and 9 rows per band are recomputed; every row is
+// read from HBM once.  Walls use non-equilibrium extrapolation written by the
+// interior neighbour's thread, and the second-order upwind point beyond a
+// wall is replaced by its linear extrapolation Pi(-1) = 2 Pi(0) - Pi(1).
+//
+// The alpha = 0 lane (template flag RHO0) carries fhat_{j,0} (planes
+// 10..14) through the same stages as scalars, in three more rings of 5 x NT
+// floats: relaxed in stage A with the node's u, v; streamed and recovered in
+// stage B with the u, v of the alpha = 1, 2 fbar; streamed in stage C; walls
+// by non-equilibrium extrapolation with the neighbour's rho_0.
 #pragma once
 
 #include "mdf_device.cuh"

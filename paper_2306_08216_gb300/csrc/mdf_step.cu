@@ -8,10 +8,11 @@
 //   Step 3  f(t+h) = feq + (I + h/2 Lt)^-1 (fbar - feq)          (Eq. 2.2.16)
 //   Step 4  fhat(t+dt) = fhat^+ - dt c_j.grad f(t+h)
 //                        + dt w_j (F + dt/2 dF/dt)                (Eq. 2.3.24)
-// The kernels of this file (shared-ring march) serve curvilinear grids; the
-// file also holds the launch planning and dispatch.  Uniform and separable
-// grids run the register-window marches of mdf_step_fast.cu (periodic,
-// Newtonian) and mdf_step_walls.cu (walls and/or power law).
+// This file instantiates the shared-ring march (mdf_march.cuh) for
+// curvilinear grids and holds the launch planning and dispatch.  Uniform
+// and separable grids run the register-window marches of mdf_step_fast.cu
+// (periodic, Newtonian) and mdf_step_walls.cu (walls and/or power law);
+// with the alpha = 0 distribution every grid runs mdf_step_rho0.cu.
 // The MRT matrix of Eq. 2.2.4 with s0 = s3 = s4 = s' and s1 = s2 = s equals
 // s' I + (s - s') P_c, P_c the projector on the first moments, so every
 // function of it acts on a distribution through its zeroth and first moments
@@ -19,29 +20,8 @@
 // (Eq. 2.2.5) each of the three local maps costs a handful of FMAs per
 // population and no 5x5 product appears (cf. the 2x5x5 loop count of Sec. 4.2).
 //
-// Arithmetic layout.  The two distributions alpha = u, v (Eq. 2.1.2 with
-// alpha = 1, 2) see the same collision rates and the same difference
-// weights, so each population j is carried as one 64-bit pair
-// (fhat_{j,u}, fhat_{j,v}) and processed with the packed FP32 instructions
-// of sm_100-family GPUs (add/sub/mul/fma .f32x2); shared rings hold the
-// pairs, so every ring access is one 64-bit load or store.
-//
-// Work decomposition.  A block owns a strip of W = NT - 8 output columns and
-// marches down a band of H rows.  Thread t holds column x0 - 4 + t; the 8
-// extra columns are the halo of the two chained stencils (reach 2 + 2).  Per
-// row of the march, with p the newest row:
-//   C: fhat(t+dt) of row r = p - 5 from the f ring and the fhat^+ ring -> HBM;
-//   A: row p of fhat arrives by TMA (one 3-D box of 10 planes x NT columns);
-//      fhat^+ and fbar^+ of row p go to their rings;
-//   -- barrier --
-//   B: fbar and f(t+h) of row q = p - 2 (x stencils across threads, y
-//      stencils across ring rows) go to the f ring; walls by NEE;
-//   -- barrier --
-// All rings have five rows; slot offsets rotate by one each row.  Only the x
-// halo (8 of NT columns) and 9 rows per band are recomputed; every row is
-// read from HBM once.  Walls use non-equilibrium extrapolation written by the
-// interior neighbour's thread, and the second-order upwind point beyond a
-// wall is replaced by its linear extrapolation Pi(-1) = 2 Pi(0) - Pi(1).
+// The shared-ring march itself (arithmetic layout, work decomposition,
+// walls) is in mdf_march.cuh.
 #include "mdf_march.cuh"
 
 namespace mdf {
