@@ -248,13 +248,22 @@ const char *mdf_last_error(const mdf_ctx *ctx);    /* ctx may be NULL */
  * info[6] blocks resident per SM (occupancy query; 0 without a GPU). */
 mdf_status mdf_launch_info(const mdf_ctx *ctx, int info[8]);
 
-/* Override the launch plan the library chose (tile-shape tuning): `threads`
- * per block (128, or 256 on periodic Newtonian uniform/separable problems)
- * and `rows_per_block` (>= 1) rows per block.  mdf_create times the
- * candidate plans on grids of 2^20 nodes or more and keeps the fastest; this
- * call replaces that choice.  Waits for the context's stream; MDF_E_INVALID
- * for an unsupported block size. */
+/* Override the launch plan the library chose (tile-shape tuning).  The step
+ * has two kernel families: marches, where a block of `threads` (128, or 256
+ * on uniform/separable grids) sweeps a strip of threads - 8 columns down a
+ * band of `rows_per_block` (>= 1) rows, and the tile kernel (threads = 0;
+ * rows_per_block is ignored), where a block of 16 x 16 threads computes one
+ * 16 x 16 tile in three phases with a recomputed halo of 4 nodes: on grids
+ * too small to fill the GPU with long bands it avoids the serial march
+ * (FP32 storage without the alpha = 0 distribution).  mdf_create times every
+ * candidate plan for a few steps and keeps the fastest (the tile kernel only
+ * if it beats the best march by more than 10 %); this call replaces that
+ * choice.  Waits for the context's stream; MDF_E_INVALID for an unsupported
+ * block size. */
 mdf_status mdf_set_launch(mdf_ctx *ctx, int threads, int rows_per_block);
+
+/* Kernel family of the current launch plan: 0 march, 1 tile (-1 for NULL). */
+int mdf_launch_kind(const mdf_ctx *ctx);
 
 /* Algorithmic bytes moved per node update by the fused step (state read and
  * written once, plus force/metric planes read once). */

@@ -145,17 +145,20 @@ static mdf_status wait_stream(mdf_ctx *c, double timeout_s) {
     return MDF_OK;
 }
 
-// Launch-plan autotuner: on grids of a million nodes or more, time every
-// candidate plan (block size, band height) for a few steps on the rest state
-// (a fixed point of the step, so buffer 0 keeps its contents; the output goes
-// to buffer 1) and keep the fastest.  Smaller grids keep the default plan.
+// Launch-plan autotuner: time every candidate plan (march block size and
+// band height, or the tile kernel) for a few steps from the initial state
+// in buffer 0 (which keeps its contents; the output goes to buffer 1) and
+// keep the fastest.  March plans compute the same values whatever the band
+// split; the tile kernel is taken only when it beats the best march by more
+// than 10 %, so that timing noise near the crossover cannot flip the kernel
+// (and the last bits of the results) from one run to the next.
 static mdf_status autotune(mdf_ctx *c) {
-    if (c->ncand > 1 && (long long)c->nx * c->ny >= (1ll << 20)) {
+    if (c->ncand > 1) {
         cudaEvent_t e0, e1;
         CK(c, cudaEventCreate(&e0));
         CK(c, cudaEventCreate(&e1));
-        float best = 1e30f;
-        int best_i = 0;
+        float best = 1e30f, best_tile = 1e30f;
+        int best_i = 0, tile_i = -1;
         // two rounds over the candidates, 8 timed launches each; keep the
         // fastest time seen per candidate
         for (int round = 0; round < 2; ++round)
@@ -167,6 +170,7 @@ static mdf_status autotune(mdf_ctx *c) {
             a.W = c->plan.W;
             a.H = c->plan.H;
             a.fout = c->buf[1];
+            a.fin = c->buf[0];
             CK(c, step_launch(&c->tmap[0], a, c->kind, c->plan, 0));
             CK(c, cudaEventRecord(e0, 0));
             for (int r = 0; r < 8; ++r) CK(c, step_launch(&c->tmap[0], a, c->kind, c->plan, 0));
@@ -174,14 +178,19 @@ static mdf_status autotune(mdf_ctx *c) {
             CK(c, cudaEventSynchronize(e1));
             float ms = 0.0f;
             CK(c, cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) {
+            if (c->plan.kind == PLAN_TILE) {
+                if (ms < best_tile) {
+                    best_tile = ms;
+                    tile_i = i;
+                }
+            } else if (ms < best) {
                 best = ms;
                 best_i = i;
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        c->plan = c->cand[best_i];
+        c->plan = c->cand[(tile_i >= 0 && best_tile < 0.9f * best) ? tile_i : best_i];
     }
     c->args.W = c->plan.W;
     c->args.H = c->plan.H;
@@ -194,10 +203,29 @@ mdf_status ctx_encode_maps(mdf_ctx *c, int box_nt, CUtensorMap maps[2]) { return
 mdf_status ctx_wait(mdf_ctx *c, double timeout_s) { return wait_stream(c, timeout_s); }
 }  // namespace mdf
 
+static mdf_status create_ctx(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc *bc,
+                             const mdf_params *params, int tune, mdf_ctx **out);
+
+namespace mdf {
+// Contexts that only serve as problems of a batch step with the batch's own
+// launch plan: the single-problem autotuner is skipped.
+mdf_status ctx_create_untuned(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc *bc,
+                              const mdf_params *params, mdf_ctx **out) {
+    return create_ctx(grid, fluid, bc, params, 0, out);
+}
+}  // namespace mdf
+
 extern "C" {
 
 mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc *bc, const mdf_params *params,
                       mdf_ctx **out) {
+    return create_ctx(grid, fluid, bc, params, 1, out);
+}
+
+}  // extern "C"
+
+static mdf_status create_ctx(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc *bc,
+                             const mdf_params *params, int tune, mdf_ctx **out) {
     if (!out) return fail(nullptr, MDF_E_INVALID, "out is NULL");
     *out = nullptr;
     if (!grid || !fluid || !bc) return fail(nullptr, MDF_E_INVALID, "grid, fluid and bc are required");
@@ -427,13 +455,20 @@ mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc
     CKE(aux_init(x, c->scratch, c->scratch + N, c->scratch + 2 * N, c->buf[0], 0));
     CKE(aux_snapshot(x, c->buf[0], c->snap_u, c->snap_v, 0));
     CKE(cudaDeviceSynchronize());
-    CKC(autotune(c));
+    if (tune) CKC(autotune(c));
+    else {
+        c->args.W = c->plan.W;
+        c->args.H = c->plan.H;
+        CKC(encode_maps(c));
+    }
     c->cur = 0;
     *out = c;
     return MDF_OK;
 #undef CKE
 #undef CKC
 }
+
+extern "C" {
 
 void mdf_destroy(mdf_ctx *c) {
     if (!c) return;
@@ -613,6 +648,7 @@ static mdf_status build_step_graph(mdf_ctx *c, int parity) {
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < mdf_ctx::kGraphSteps && e == cudaSuccess; ++i) {
         a.fout = c->buf[1 - cur];
+        a.fin = c->buf[cur];
         e = step_launch(&c->tmap[cur], a, c->kind, c->plan, c->cstream);
         cur = 1 - cur;
     }
@@ -649,6 +685,7 @@ mdf_status mdf_step(mdf_ctx *c, int n) {
     }
     for (int i = done; i < n; ++i) {
         c->args.fout = c->buf[1 - c->cur];
+        c->args.fin = c->buf[c->cur];
         CK(c, step_launch(&c->tmap[c->cur], c->args, c->kind, c->plan, c->stream));
         c->cur = 1 - c->cur;
         ++c->steps;
@@ -930,13 +967,17 @@ mdf_status mdf_launch_info(const mdf_ctx *c, int info[8]) {
 mdf_status mdf_set_launch(mdf_ctx *c, int threads, int rows_per_block) {
     if (!c) return MDF_E_INVALID;
     int found = -1;
-    for (int i = 0; i < c->ncand; ++i)
-        if (c->cand[i].NT == threads) { found = i; break; }
+    for (int i = 0; i < c->ncand; ++i) {
+        const bool tile = c->cand[i].kind == PLAN_TILE;
+        if (threads == 0 ? tile : (!tile && c->cand[i].NT == threads)) { found = i; break; }
+    }
     if (found < 0) return fail(c, MDF_E_INVALID, "no launch plan with %d threads for this problem", threads);
-    if (rows_per_block < 1) return fail(c, MDF_E_INVALID, "rows_per_block must be >= 1");
+    if (threads != 0 && rows_per_block < 1) return fail(c, MDF_E_INVALID, "rows_per_block must be >= 1");
     StepPlan p = c->cand[found];
-    p.H = rows_per_block;
-    p.gy = (c->ny + p.H - 1) / p.H;
+    if (threads != 0) {
+        p.H = rows_per_block;
+        p.gy = (c->ny + p.H - 1) / p.H;
+    }
     CK(c, cudaStreamSynchronize(c->stream));
     if (c->cstream) CK(c, cudaStreamSynchronize(c->cstream));
     c->plan = p;
@@ -945,6 +986,8 @@ mdf_status mdf_set_launch(mdf_ctx *c, int threads, int rows_per_block) {
     drop_graphs(c);
     return encode_maps(c);
 }
+
+int mdf_launch_kind(const mdf_ctx *c) { return c ? c->plan.kind : -1; }
 
 double mdf_bytes_per_node(const mdf_ctx *c) {
     if (!c) return NAN;

@@ -97,6 +97,7 @@ static mdf_status upload_args(mdf_batch *b) {
             a.W = kBatchNT - 8;
             a.H = b->H[i];
             a.fout = c->buf[1 - p];
+            a.fin = c->buf[p];
             a.err = b->ctx[0]->err;  // one fault word for the whole batch
             args[i] = a;
         }
@@ -238,7 +239,7 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
 #define BCKE(call) BCKC(([&]() -> mdf_status { BCK(b, call); return MDF_OK; })())
     for (int i = 0; i < count; ++i) {
         mdf_ctx *c = nullptr;
-        mdf_status s = mdf_create(&grids[i], &fluids[i], &bcs[i], params ? &params[i] : nullptr, &c);
+        mdf_status s = ctx_create_untuned(&grids[i], &fluids[i], &bcs[i], params ? &params[i] : nullptr, &c);
         if (s != MDF_OK) {
             bfail(b, s, "problem %d: %s", i, mdf_last_error(nullptr));
             BCKC(s);

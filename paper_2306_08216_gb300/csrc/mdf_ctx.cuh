@@ -62,5 +62,7 @@ namespace mdf {
 // Shared helpers of the host runtime (mdf_api.cu).
 mdf_status ctx_fail(mdf_ctx *c, mdf_status st, const char *msg);
 mdf_status ctx_encode_maps(mdf_ctx *c, int box_nt, CUtensorMap maps[2]);
+mdf_status ctx_create_untuned(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc *bc,
+                              const mdf_params *params, mdf_ctx **out);
 mdf_status ctx_wait(mdf_ctx *c, double timeout_s);
 }  // namespace mdf

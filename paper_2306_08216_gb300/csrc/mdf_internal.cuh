@@ -47,6 +47,7 @@ enum DeviceError { DEVERR_NONE = 0, DEVERR_TMA_TIMEOUT = 1 };
 
 struct StepArgs {
     float *fout;            // output state (same layout as the input)
+    const float *fin;       // input state (the tile kernel reads it with plain loads; the marches use TMA)
     int storage;            // StorageKind of both state buffers
     int rho0;               // the buffers also hold the alpha = 0 distribution
     float nscale, ninv;     // 16-bit storage: S and 1/S
@@ -109,12 +110,15 @@ inline unsigned long long pack_pair(float x) {
 
 // Fused step kernel launcher (mdf_step.cu).
 struct StepPlan {
+    int kind;     // PLAN_MARCH or PLAN_TILE
     int NT;       // threads per block
     int W, H;     // output columns / rows per block
     int gx, gy;   // grid
     int smem;     // dynamic shared memory bytes
     int occ;      // resident blocks per SM
 };
+
+enum PlanKind { PLAN_MARCH = 0, PLAN_TILE = 1 };
 
 // Candidate launch plans of the fused step (the first one is the default);
 // returns how many were written to out[0..max).
@@ -148,6 +152,13 @@ cudaError_t walls_batch_launch(const BatchItem *items, int nitems, const StepArg
 cudaError_t rho0_occupancy(int metric, int power_law, int walls, int *occ, int *smem);
 cudaError_t rho0_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
                         cudaStream_t stream);
+
+// One block per 2-D tile of output nodes, three phases per step, for grids
+// too small for marching bands (mdf_step_tile.cu); FP32 storage without the
+// alpha = 0 distribution.
+bool tile_path_applies(int storage, int rho0);
+cudaError_t tile_occupancy(int metric, int power_law, int walls, int *tx, int *ty, int *occ, int *smem);
+cudaError_t tile_launch(const StepArgs &args, int metric, const StepPlan &plan, cudaStream_t stream);
 
 // Periodic Newtonian fast path on uniform/separable grids (mdf_step_fast.cu).
 bool fast_path_applies(int metric, int power_law, int walls);

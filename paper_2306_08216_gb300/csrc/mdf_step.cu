@@ -50,6 +50,7 @@ int step_pitch(int nx, int W) {
 // than fewer long ones (257^2 cavity: 10.7 us per step with 2-row bands,
 // 15.1 us with 8-row bands).
 static void fill_plan(int nt, int occ, int smem, int waves, int nx, int ny, int num_sms, StepPlan *plan) {
+    plan->kind = PLAN_MARCH;
     plan->NT = nt;
     plan->W = nt - 8;
     plan->occ = occ;
@@ -84,6 +85,26 @@ int step_candidates(int metric, int power_law, int walls, int storage, int rho0,
         if (occ < 1) continue;
         for (int waves = 1; waves <= 2 && n < max; ++waves) fill_plan(nts[i], occ, smem, waves, nx, ny, num_sms, &out[n++]);
     }
+    // the tile kernel, last: the marches stay the default
+    if (tile_path_applies(storage, rho0) && n < max) {
+        int tx = 0, ty = 0, occ = 0, smem = 0;
+        const cudaError_t e = tile_occupancy(metric, power_law, walls, &tx, &ty, &occ, &smem);
+        if (e != cudaSuccess) {
+            *err = e;
+            return n;
+        }
+        if (occ >= 1) {
+            StepPlan &p = out[n++];
+            p.kind = PLAN_TILE;
+            p.NT = tx * ty;
+            p.W = tx;
+            p.H = ty;
+            p.gx = (nx + tx - 1) / tx;
+            p.gy = (ny + ty - 1) / ty;
+            p.smem = smem;
+            p.occ = occ;
+        }
+    }
     return n;
 }
 
@@ -104,6 +125,7 @@ cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metri
                         cudaStream_t stream) {
     const int power_law = args.power_law;
     const int walls = (args.xwall || args.ywall) ? 1 : 0;
+    if (plan.kind == PLAN_TILE) return tile_launch(args, metric, plan, stream);
     if (args.rho0) return rho0_launch(tmap, args, metric, plan, stream);
     if (fast_path_applies(metric, power_law, walls)) return fast_launch(tmap, args, metric, plan, stream);
     if (walls_path_applies(metric, power_law, walls, args.storage))

@@ -90,6 +90,7 @@ _SIGNATURES = [
     ("mdf_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("mdf_launch_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     ("mdf_set_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("mdf_launch_kind", ctypes.c_int, [ctypes.c_void_p]),
     ("mdf_bytes_per_node", ctypes.c_double, [ctypes.c_void_p]),
     ("mdf_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Grid), ctypes.POINTER(Fluid),
                                         ctypes.POINTER(BC), ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]),
@@ -392,9 +393,13 @@ class Solver:
         _check(lib().mdf_launch_info(self._h, info), self._h)
         keys = ["threads", "cols_per_block", "rows_per_block", "grid_x", "grid_y", "smem_bytes",
                 "blocks_per_sm", "pitch"]
-        return dict(zip(keys, list(info)))
+        d = dict(zip(keys, list(info)))
+        d["kernel"] = "tile" if lib().mdf_launch_kind(self._h) == 1 else "march"
+        return d
 
-    def set_launch(self, threads, rows_per_block):
+    def set_launch(self, threads, rows_per_block=0):
+        """threads 128 / 256: a march plan with that block size and band
+        height; threads 0: the 16 x 16 tile kernel."""
         _check(lib().mdf_set_launch(self._h, int(threads), int(rows_per_block)), self._h)
 
     def bytes_per_node(self):

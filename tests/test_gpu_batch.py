@@ -41,6 +41,7 @@ def test_batch_of_power_law_cavities_equals_solo_runs_bitwise():
         kw = dict(kw)
         nx, ny = kw.pop("nx"), kw.pop("ny")
         solo = mdf.Solver(nx, ny, **kw)
+        solo.set_launch(128, 8)  # the march the batch kernel shares (not the tile kernel)
         solo.init(*W.zeros(nx, ny))
         solo.step(43)
         np.testing.assert_array_equal(batch.problem(i).state(), solo.state())
@@ -106,6 +107,7 @@ def _solo_state(kw, steps):
     kw = dict(kw)
     nx, ny = kw.pop("nx"), kw.pop("ny")
     solo = mdf.Solver(nx, ny, **kw)
+    solo.set_launch(128, 8)  # the march the batch kernel shares
     solo.init(*W.zeros(nx, ny))
     solo.step(steps)
     return solo.state()
