@@ -127,42 +127,63 @@ __global__ void __launch_bounds__(TX *TY, 2) tile_kernel(const StepArgs a) {
     const F2 mKp = pair_of_bits(a.pmKp), Dp = pair_of_bits(a.pDp), mKb = pair_of_bits(a.pmKb), Db = pair_of_bits(a.pDb);
 
     // ------------------------------------------------ A: fbar^+ on tile + 4
-    F2 hp[5];  // fhat^+ of the thread's own node
-#pragma unroll 1
-    for (int i = t; i < T::N8; i += T::NT) {
-        int lx, ly;
-        if (i < T::NT) {  // the first pass takes the thread's own node
+    // The thread's nodes of the region: first its own output node, then
+    // nodes of the halo ring (4 rows above, 4 below, 4 columns each side).
+    // All their loads are issued before any arithmetic, so that the passes
+    // share one memory latency.
+    constexpr int PASSES = (T::N8 + T::NT - 1) / T::NT;
+    auto region_node = [&](int i, int &lx, int &ly) {
+        if (i < T::NT) {
             lx = 4 + i % TX;
             ly = 4 + i / TX;
-        } else {  // then the halo ring: 4 rows above, 4 below, 4 columns each side
-            int h = i - T::NT;
-            if (h < 4 * T::X8) {
-                ly = h / T::X8;
-                lx = h % T::X8;
-            } else if (h < 8 * T::X8) {
-                h -= 4 * T::X8;
-                ly = TY + 4 + h / T::X8;
-                lx = h % T::X8;
-            } else {
-                h -= 8 * T::X8;
-                ly = 4 + h / 8;
-                const int cc = h % 8;
-                lx = cc < 4 ? cc : TX + cc;
+            return;
+        }
+        int h = i - T::NT;
+        if (h < 4 * T::X8) {
+            ly = h / T::X8;
+            lx = h % T::X8;
+        } else if (h < 8 * T::X8) {
+            h -= 4 * T::X8;
+            ly = TY + 4 + h / T::X8;
+            lx = h % T::X8;
+        } else {
+            h -= 8 * T::X8;
+            ly = 4 + h / 8;
+            const int cc = h % 8;
+            lx = cc < 4 ? cc : TX + cc;
+        }
+    };
+    F2 gq[PASSES][5];
+#pragma unroll
+    for (int q = 0; q < PASSES; ++q) {
+        const int i = t + q * T::NT;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) gq[q][j] = splat(0.0f);
+        if (i < T::N8) {
+            int lx, ly;
+            region_node(i, lx, ly);
+            const int X = x0 - 4 + lx, Y = y0 - 4 + ly;
+            const bool ok = (xwall ? (X >= 0 && X < a.nx) : true) && (ywall ? (Y >= 0 && Y < a.ny) : true);
+            if (ok) {
+                const long long s =
+                    (long long)(ywall ? Y : wrap(Y, a.ny)) * a.pitch + GHOST + (xwall ? X : wrap(X, a.nx));
+#pragma unroll
+                for (int j = 0; j < 5; ++j) gq[q][j] = mk2(a.fin[j * a.plane + s], a.fin[(5 + j) * a.plane + s]);
             }
         }
+    }
+    F2 hp[5];  // fhat^+ of the thread's own node
+#pragma unroll
+    for (int q = 0; q < PASSES; ++q) {
+        const int i = t + q * T::NT;
+        if (i >= T::N8) break;
+        int lx, ly;
+        region_node(i, lx, ly);
         const int X = x0 - 4 + lx, Y = y0 - 4 + ly;
         const bool okx = xwall ? (X >= 0 && X < a.nx) : true;
         const bool oky = ywall ? (Y >= 0 && Y < a.ny) : true;
         const int Xw = xwall ? X : wrap(X, a.nx), Yw = ywall ? Y : wrap(Y, a.ny);
-        F2 g[5];
-        if (okx && oky) {
-            const long long s = (long long)Yw * a.pitch + GHOST + Xw;
-#pragma unroll
-            for (int j = 0; j < 5; ++j) g[j] = mk2(a.fin[j * a.plane + s], a.fin[(5 + j) * a.plane + s]);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 5; ++j) g[j] = splat(0.0f);
-        }
+        const F2 *g = gq[q];
         const Mom2 m = (a.r_mode && okx && oky) ? moments2r(g, c, a.rk_hat * source_at(a, Yw, Xw)) : moments2(g, c);
         F2 n[5];
         noneq2(g, m, inv2c, n);
@@ -186,7 +207,7 @@ __global__ void __launch_bounds__(TX *TY, 2) tile_kernel(const StepArgs a) {
             }
         }
         F2 o[5];
-        if (i < T::NT) relax2(g, n, n13, n24, mKp_, Dp_, hp);
+        if (q == 0) relax2(g, n, n13, n24, mKp_, Dp_, hp);
         relax2(g, n, n13, n24, mKb_, Db_, o);
         const int n8 = ly * T::X8 + lx;
 #pragma unroll
