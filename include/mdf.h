@@ -316,6 +316,15 @@ mdf_status mdf_batch_problem(mdf_batch *batch, int index, mdf_ctx **ctx);
 /* info[0] problems, [1] work items, [2] blocks per launch, [3] blocks per
  * SM, [4] nodes in all problems, [5] steps taken. */
 mdf_status mdf_batch_info(const mdf_batch *batch, long long info[6]);
+/* Kernel family of the batch step: 0 marches (work items are strips x bands
+ * of each problem), 1 tiles (work items are the 16 x 16 tiles of each
+ * problem, the tile kernel of mdf_set_launch).  mdf_batch_create times both
+ * and keeps the marches unless the tiles are more than 10 % faster;
+ * mdf_batch_set_launch replaces that choice (waits for the batch's streams;
+ * MDF_E_INVALID for another kind).  mdf_batch_launch_kind returns the
+ * current one (-1 for NULL). */
+mdf_status mdf_batch_set_launch(mdf_batch *batch, int kind);
+int mdf_batch_launch_kind(const mdf_batch *batch);
 const char *mdf_batch_last_error(const mdf_batch *batch);
 
 /* Residual and drift with no allocation at all (the paper has no

@@ -3,11 +3,13 @@
 // Each problem of a batch is an ordinary context (mdf_create: its own state
 // buffers, metrics, forcing and residual snapshot), so every single-problem
 // call (mdf_fields, mdf_get_distributions, mdf_residual, ...) works on it.
-// mdf_batch_step advances all of them together: one launch of batch_kernel
-// per time step, whose blocks walk a table of work items (problem, strip,
-// band) ordered largest problem first, with the problems' arguments and TMA
-// descriptors in global memory.  Repeated steps are replayed from captured
-// CUDA graphs of kGraphSteps launches.
+// mdf_batch_step advances all of them together: one launch per time step of
+// a persistent kernel whose blocks walk a table of work items ordered
+// largest problem first, with the problems' arguments (and TMA descriptors)
+// in global memory: either marches (problem, strip, band: walls_batch_kernel
+// or batch_kernel) or tiles (problem, tile x, tile y: tile_batch_kernel).
+// The batch times both at creation and keeps the faster.  Repeated steps are
+// replayed from captured CUDA graphs of kGraphSteps launches.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -35,6 +37,7 @@ struct mdf_batch {
     CUtensorMap *d_maps[2] = {nullptr, nullptr};   // per parity: maps of the input buffer
     BatchItem *d_items = nullptr;
     int nitems = 0, grid = 0, occ = 0, smem = 0;
+    int tile = 0, occ_tile = 0, smem_tile = 0;     // tile mode: one work item per 16 x 16 tile
     int forced = 0;                                // some problem has a force, force rate or source
     int cur = 0;
     cudaStream_t stream = nullptr;
@@ -120,10 +123,17 @@ static mdf_status upload_args(mdf_batch *b) {
     return MDF_OK;
 }
 
+static cudaError_t launch_one(mdf_batch *b, int parity, cudaStream_t st) {
+    if (b->tile)
+        return tile_batch_launch(b->d_items, b->nitems, b->d_args[parity], b->metric, b->power_law, b->walls, b->grid,
+                                 st);
+    return batch_launch(b->d_items, b->nitems, b->d_args[parity], b->d_maps[parity], b->metric, b->power_law,
+                        b->walls, b->grid, b->forced, st);
+}
+
 static mdf_status launch_steps(mdf_batch *b, cudaStream_t st, int n) {
     for (int i = 0; i < n; ++i) {
-        BCK(b, batch_launch(b->d_items, b->nitems, b->d_args[b->cur], b->d_maps[b->cur], b->metric, b->power_law,
-                            b->walls, b->grid, b->forced, st));
+        BCK(b, launch_one(b, b->cur, st));
         b->cur ^= 1;
     }
     return MDF_OK;
@@ -177,13 +187,14 @@ static mdf_status build_items(mdf_batch *b) {
     std::vector<BatchItem> items;
     for (int i : order) {
         mdf_ctx *c = b->ctx[i];
-        const int gx = (c->nx + W - 1) / W;
-        const int gy = (c->ny + b->H[i] - 1) / b->H[i];
+        const int tw = b->tile ? TILE_X : W, th = b->tile ? TILE_Y : b->H[i];
+        const int gx = (c->nx + tw - 1) / tw;
+        const int gy = (c->ny + th - 1) / th;
         for (int by = 0; by < gy; ++by)
             for (int bx = 0; bx < gx; ++bx) items.push_back(BatchItem{i, bx, by, 0});
     }
     b->nitems = (int)items.size();
-    b->grid = std::min(b->nitems, std::max(1, b->occ) * b->num_sms);
+    b->grid = std::min(b->nitems, std::max(1, b->tile ? b->occ_tile : b->occ) * b->num_sms);
     if (b->nitems > b->items_cap) {
         if (b->d_items) cudaFree(b->d_items);
         b->d_items = nullptr;
@@ -198,6 +209,34 @@ static mdf_status build_items(mdf_batch *b) {
         b->graph[p] = nullptr;
     }
     return MDF_OK;
+}
+
+// Time a few steps of each kernel family from the initial states (buffer 0
+// of every problem is read, buffer 1 written, so the states are unchanged)
+// and keep the march unless the tiles are more than 10 % faster.
+static mdf_status choose_kernel(mdf_batch *b) {
+    cudaEvent_t e0, e1;
+    BCK(b, cudaEventCreate(&e0));
+    BCK(b, cudaEventCreate(&e1));
+    float best[2] = {1e30f, 1e30f};
+    for (int round = 0; round < 2; ++round)
+        for (int k = 0; k < 2; ++k) {
+            b->tile = k;
+            mdf_status s = build_items(b);
+            if (s != MDF_OK) return s;
+            BCK(b, launch_one(b, 0, 0));
+            BCK(b, cudaEventRecord(e0, 0));
+            for (int r = 0; r < 4; ++r) BCK(b, launch_one(b, 0, 0));
+            BCK(b, cudaEventRecord(e1, 0));
+            BCK(b, cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            BCK(b, cudaEventElapsedTime(&ms, e0, e1));
+            best[k] = std::min(best[k], ms);
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tile = best[1] < 0.9f * best[0] ? 1 : 0;
+    return build_items(b);
 }
 
 extern "C" {
@@ -268,6 +307,8 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
         BCKE(cudaMemcpy(b->d_maps[p], b->h_maps[p].data(), count * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
     }
     BCKC(upload_args(b));
+    BCKE(tile_batch_occupancy(metric, power_law, walls, &b->occ_tile, &b->smem_tile));
+    if (b->occ_tile >= 1) BCKC(choose_kernel(b));
     BCKE(cudaMallocHost(&b->h_res, (size_t)count * 5 * sizeof(double)));
     BCKE(cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking));
     BCKE(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
@@ -413,6 +454,18 @@ mdf_status mdf_batch_info(const mdf_batch *b, long long info[6]) {
     info[5] = b->steps;
     return MDF_OK;
 }
+
+mdf_status mdf_batch_set_launch(mdf_batch *b, int kind) {
+    if (!b) return MDF_E_INVALID;
+    if (kind != 0 && kind != 1) return bfail(b, MDF_E_INVALID, "kind must be 0 (march) or 1 (tile)");
+    if (kind == 1 && b->occ_tile < 1) return bfail(b, MDF_E_INVALID, "the tile kernel does not fit");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    BCK(b, cudaStreamSynchronize(b->cstream));
+    b->tile = kind;
+    return build_items(b);
+}
+
+int mdf_batch_launch_kind(const mdf_batch *b) { return b ? b->tile : -1; }
 
 const char *mdf_batch_last_error(const mdf_batch *b) { return b ? b->last_error : g_batch_error; }
 

@@ -119,6 +119,7 @@ struct StepPlan {
 };
 
 enum PlanKind { PLAN_MARCH = 0, PLAN_TILE = 1 };
+constexpr int TILE_X = 16, TILE_Y = 16;  // output tile of the tile kernel (halo of 4 on each side)
 
 // Candidate launch plans of the fused step (the first one is the default);
 // returns how many were written to out[0..max).
@@ -159,6 +160,10 @@ cudaError_t rho0_launch(const CUtensorMap *tmap, const StepArgs &args, int metri
 bool tile_path_applies(int storage, int rho0);
 cudaError_t tile_occupancy(int metric, int power_law, int walls, int *tx, int *ty, int *occ, int *smem);
 cudaError_t tile_launch(const StepArgs &args, int metric, const StepPlan &plan, cudaStream_t stream);
+// The same kernel over the work items (problem, tile x, tile y) of a batch.
+cudaError_t tile_batch_occupancy(int metric, int power_law, int walls, int *occ, int *smem);
+cudaError_t tile_batch_launch(const BatchItem *items, int nitems, const StepArgs *args, int metric, int power_law,
+                              int walls, int grid, cudaStream_t stream);
 
 // Periodic Newtonian fast path on uniform/separable grids (mdf_step_fast.cu).
 bool fast_path_applies(int metric, int power_law, int walls);

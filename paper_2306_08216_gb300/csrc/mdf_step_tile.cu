@@ -112,16 +112,23 @@ __device__ __forceinline__ void stream_tile(const unsigned char *A, int n, int S
     }
 }
 
+template <int TX, int TY, int MK, bool WALLS>
+__device__ __forceinline__ void tile_output(const StepArgs &a, int X, int Y, int li, int lj, const unsigned char *Fs,
+                                            const F2 hp[5]);
+
+// One tile (bx, by) of one problem.  Every thread reaches every barrier
+// (no early exit), so a block may step several tiles in a row: the barrier
+// after phase A of the next tile orders its shared-memory writes after the
+// reads of the previous tile.
 template <int TX, int TY, int MK, bool PL, bool WALLS>
-__global__ void __launch_bounds__(TX *TY, 2) tile_kernel(const StepArgs a) {
+__device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, unsigned char *smem) {
     using T = Tile<TX, TY>;
-    extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *Bs = smem;                          // fbar^+ [5][N8] pairs
     unsigned char *Fs = smem + T::B_BYTES;             // f(t+h) [5][N4] pairs
     float *Ks = reinterpret_cast<float *>(Fs + T::F_BYTES);  // power law: rkp [N4], rk [N4]
 
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx * TX, y0 = by * TY;
     const bool xwall = WALLS && a.xwall, ywall = WALLS && a.ywall;
     const float c = a.c, inv2c = a.inv2c;
     const F2 mKp = pair_of_bits(a.pmKp), Dp = pair_of_bits(a.pDp), mKb = pair_of_bits(a.pmKb), Db = pair_of_bits(a.pDb);
@@ -290,6 +297,17 @@ __global__ void __launch_bounds__(TX *TY, 2) tile_kernel(const StepArgs a) {
     const int X = x0 + li, Y = y0 + lj;
     if (X >= a.nx || Y >= a.ny) return;
     if (WALLS && ((xwall && (X == 0 || X == a.nx - 1)) || (ywall && (Y == 0 || Y == a.ny - 1)))) return;
+    tile_output<TX, TY, MK, WALLS>(a, X, Y, li, lj, Fs, hp);
+}
+
+// Phase C of the own node (X, Y): pass 2 from the f region, the output and
+// the NEE output of an adjacent wall node.
+template <int TX, int TY, int MK, bool WALLS>
+__device__ __forceinline__ void tile_output(const StepArgs &a, int X, int Y, int li, int lj, const unsigned char *Fs,
+                                            const F2 hp[5]) {
+    using T = Tile<TX, TY>;
+    const bool xwall = WALLS && a.xwall, ywall = WALLS && a.ywall;
+    const float inv2c = a.inv2c;
     const bool xadj_p = xwall && X == 1, xadj_m = xwall && X == a.nx - 2;
     const bool yadj_p = ywall && Y == 1, yadj_m = ywall && Y == a.ny - 2;
     const int n4 = (lj + 2) * T::X4 + li + 2;
@@ -324,7 +342,25 @@ __global__ void __launch_bounds__(TX *TY, 2) tile_kernel(const StepArgs a) {
     }
 }
 
-constexpr int kTX = 16, kTY = 16;
+template <int TX, int TY, int MK, bool PL, bool WALLS>
+__global__ void __launch_bounds__(TX *TY, 2) tile_kernel(const StepArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    tile_step<TX, TY, MK, PL, WALLS>(a, blockIdx.x, blockIdx.y, smem);
+}
+
+// Many problems in one persistent launch: block b steps work items
+// b, b + gridDim.x, ... (problem, tile x, tile y), largest problems first.
+template <int TX, int TY, int MK, bool PL, bool WALLS>
+__global__ void __launch_bounds__(TX *TY, 2) tile_batch_kernel(const BatchItem *__restrict__ items, int nitems,
+                                                               const StepArgs *__restrict__ args) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const BatchItem item = items[w];
+        tile_step<TX, TY, MK, PL, WALLS>(args[item.problem], item.bx, item.by, smem);
+    }
+}
+
+constexpr int kTX = TILE_X, kTY = TILE_Y;
 
 template <int MK, bool PL, bool WALLS>
 constexpr int tile_smem() {
@@ -351,6 +387,29 @@ cudaError_t tile_launch_t(const StepArgs &args, const StepPlan &plan, cudaStream
         configured = true;
     }
     k<<<dim3(plan.gx, plan.gy), kTX * kTY, tile_smem<MK, PL, WALLS>(), stream>>>(args);
+    return cudaGetLastError();
+}
+
+template <int MK, bool PL, bool WALLS>
+cudaError_t tile_batch_occupancy_t(int *occ, int *smem) {
+    auto k = tile_batch_kernel<kTX, kTY, MK, PL, WALLS>;
+    *smem = tile_smem<MK, PL, WALLS>();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, kTX * kTY, *smem);
+}
+
+template <int MK, bool PL, bool WALLS>
+cudaError_t tile_batch_launch_t(const BatchItem *items, int nitems, const StepArgs *args, int grid,
+                                cudaStream_t stream) {
+    auto k = tile_batch_kernel<kTX, kTY, MK, PL, WALLS>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_smem<MK, PL, WALLS>());
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k<<<grid, kTX * kTY, tile_smem<MK, PL, WALLS>(), stream>>>(items, nitems, args);
     return cudaGetLastError();
 }
 
@@ -384,6 +443,15 @@ cudaError_t tile_launch(const StepArgs &args, int metric, const StepPlan &plan, 
     const int power_law = args.power_law;
     const int walls = (args.xwall || args.ywall) ? 1 : 0;
     MDF_TILE_DISPATCH(tile_launch_t, args, plan, stream)
+}
+
+cudaError_t tile_batch_occupancy(int metric, int power_law, int walls, int *occ, int *smem) {
+    MDF_TILE_DISPATCH(tile_batch_occupancy_t, occ, smem)
+}
+
+cudaError_t tile_batch_launch(const BatchItem *items, int nitems, const StepArgs *args, int metric, int power_law,
+                              int walls, int grid, cudaStream_t stream) {
+    MDF_TILE_DISPATCH(tile_batch_launch_t, items, nitems, args, grid, stream)
 }
 
 }  // namespace mdf

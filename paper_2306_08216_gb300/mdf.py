@@ -103,6 +103,8 @@ _SIGNATURES = [
     ("mdf_batch_problem", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     ("mdf_batch_set_active", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     ("mdf_batch_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
+    ("mdf_batch_set_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("mdf_batch_launch_kind", ctypes.c_int, [ctypes.c_void_p]),
     ("mdf_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("mdf_residual_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
@@ -493,4 +495,10 @@ class Batch:
     def info(self):
         v = (ctypes.c_longlong * 6)()
         self._chk(lib().mdf_batch_info(self._h, v))
-        return dict(zip(["problems", "work_items", "blocks", "blocks_per_sm", "nodes", "steps"], list(v)))
+        d = dict(zip(["problems", "work_items", "blocks", "blocks_per_sm", "nodes", "steps"], list(v)))
+        d["kernel"] = "tile" if lib().mdf_batch_launch_kind(self._h) == 1 else "march"
+        return d
+
+    def set_launch(self, kernel):
+        """kernel: "march" (strips x bands per problem) or "tile" (16 x 16 tiles)."""
+        self._chk(lib().mdf_batch_set_launch(self._h, {"march": 0, "tile": 1}[kernel]))

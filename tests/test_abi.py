@@ -134,6 +134,13 @@ def test_batch_rejects_rho0(lib):
     assert b"rho_0" in lib.mdf_batch_last_error(None)
 
 
+def test_launch_kind_calls_reject_null(lib):
+    assert lib.mdf_launch_kind(None) == -1
+    assert lib.mdf_batch_launch_kind(None) == -1
+    assert lib.mdf_batch_set_launch(None, 1) == mdf.MDF_E_INVALID
+    assert lib.mdf_set_launch(None, 0, 0) == mdf.MDF_E_INVALID
+
+
 def test_rho0_calls_reject_null_contexts(lib):
     for fn in (lib.mdf_init_rho0, lib.mdf_get_rho0, lib.mdf_get_rho0_distributions,
                lib.mdf_set_rho0_distributions):

@@ -32,21 +32,26 @@ def cavity(n, re, n_index=None, u0=0.1, m=None):
     return kw
 
 
-def test_batch_of_power_law_cavities_equals_solo_runs_bitwise():
+SOLO_PLAN = {"march": (128, 8), "tile": (0, 0)}  # the single-problem plan each batch kernel shares
+
+
+@pytest.mark.parametrize("kernel", ["march", "tile"])
+def test_batch_of_power_law_cavities_equals_solo_runs_bitwise(kernel):
     probs = [cavity(65, 400, 0.6), cavity(33, 100, 1.0), cavity(47, 250, 1.4, m=39), cavity(130, 1000, 0.9)]
     batch = mdf.Batch(probs)
+    batch.set_launch(kernel)
     batch.step(40)   # graph replays (2 x 16) + 8 direct launches
     batch.step(3)
     for i, kw in enumerate(probs):
         kw = dict(kw)
         nx, ny = kw.pop("nx"), kw.pop("ny")
         solo = mdf.Solver(nx, ny, **kw)
-        solo.set_launch(128, 8)  # the march the batch kernel shares (not the tile kernel)
+        solo.set_launch(*SOLO_PLAN[kernel])
         solo.init(*W.zeros(nx, ny))
         solo.step(43)
         np.testing.assert_array_equal(batch.problem(i).state(), solo.state())
     info = batch.info()
-    assert info["problems"] == 4 and info["steps"] == 43
+    assert info["problems"] == 4 and info["steps"] == 43 and info["kernel"] == kernel
 
 
 def test_batch_problem_against_oracle():
@@ -103,36 +108,39 @@ def test_batch_rejects_mixed_kernel_variants():
     assert e.value.status == mdf.MDF_E_INVALID
 
 
-def _solo_state(kw, steps):
+def _solo_state(kw, steps, kernel):
     kw = dict(kw)
     nx, ny = kw.pop("nx"), kw.pop("ny")
     solo = mdf.Solver(nx, ny, **kw)
-    solo.set_launch(128, 8)  # the march the batch kernel shares
+    solo.set_launch(*SOLO_PLAN[kernel])
     solo.init(*W.zeros(nx, ny))
     solo.step(steps)
     return solo.state()
 
 
-def test_retired_problems_freeze_and_resume_bitwise():
+@pytest.mark.parametrize("kernel", ["march", "tile"])
+def test_retired_problems_freeze_and_resume_bitwise(kernel):
     """A retired problem keeps its state while the others advance; re-admitted
     after an odd number of batch steps (its buffers swap roles), it continues
     exactly as if it had been stepped alone."""
     probs = [cavity(65, 400, 0.8), cavity(40, 100, 1.2), cavity(33, 250, 1.0)]
     batch = mdf.Batch(probs)
+    batch.set_launch(kernel)
+    _solo = lambda kw, steps: _solo_state(kw, steps, kernel)  # noqa: E731
     batch.step(20)
     batch.set_active(1, False)
     batch.step(37)  # odd: the batch parity now differs from problem 1's
     r, st = batch.residual()
     assert st[1] == mdf.MDF_E_STATE and np.isnan(r[1])
     assert st[0] == mdf.MDF_OK and st[2] == mdf.MDF_OK
-    np.testing.assert_array_equal(batch.problem(1).state(), _solo_state(probs[1], 20))
-    np.testing.assert_array_equal(batch.problem(0).state(), _solo_state(probs[0], 57))
+    np.testing.assert_array_equal(batch.problem(1).state(), _solo(probs[1], 20))
+    np.testing.assert_array_equal(batch.problem(0).state(), _solo(probs[0], 57))
     batch.set_active(1, True)
     batch.step(35)
-    np.testing.assert_array_equal(batch.problem(1).state(), _solo_state(probs[1], 55))
-    np.testing.assert_array_equal(batch.problem(2).state(), _solo_state(probs[2], 92))
+    np.testing.assert_array_equal(batch.problem(1).state(), _solo(probs[1], 55))
+    np.testing.assert_array_equal(batch.problem(2).state(), _solo(probs[2], 92))
     assert batch.problem(1).steps == 55 and batch.problem(2).steps == 92
     for i in range(3):
         batch.set_active(i, False)
     batch.step(10)  # nothing left to step
-    np.testing.assert_array_equal(batch.problem(2).state(), _solo_state(probs[2], 92))
+    np.testing.assert_array_equal(batch.problem(2).state(), _solo(probs[2], 92))
