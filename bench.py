@@ -240,6 +240,31 @@ def batch_benchmark(mdf, torch, stream, steps=200, solo_sample=16):
     r, status = batch.residual()
     nodes = info["nodes"]
     batch_mlups = nodes * steps / (ms / 1e3) / 1e6
+    # the same sweep with 16-bit deviation storage (tile mode): throughput and
+    # the largest velocity deviation from the FP32 batch after the same steps,
+    # on the first cavity of every side
+    import numpy as np
+    sides = sorted({p["nx"] for p in probs})
+    sample = [next(i for i, p in enumerate(probs) if p["nx"] == sd) for sd in sides]
+    u32 = {i: batch.problem(i).fields(["u"])["u"].astype(np.float64) for i in sample}
+    storage = {}
+    for mode in ("fp16", "bf16"):
+        b16 = mdf.Batch([dict(p, storage=mode) for p in probs], stream=stream)
+        b16.step(2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b16.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms16 = e0.elapsed_time(e1)
+        r16, st16 = b16.residual()
+        du = max(float(np.abs(b16.problem(i).fields(["u"])["u"] - u32[i]).max()) for i in sample) / 0.1
+        storage[mode] = {"mlups": nodes * steps / (ms16 / 1e3) / 1e6, "ms_per_step": ms16 / steps,
+                         "kernel": b16.info()["kernel"], "bytes_per_node": 56.0,
+                         "diverged": int((st16 == mdf.MDF_E_DIVERGED).sum()),
+                         "max_du_vs_fp32_batch_over_u_lid": du, "du_sample": "first cavity of each side %s" % sides}
+        b16.close()
+    batch_kernel = info["kernel"]
     batch.close()
     # one-problem-per-launch reference on a sample, largest and smallest mixed
     idx = list(range(0, len(probs), max(1, len(probs) // solo_sample)))[:solo_sample]
@@ -262,6 +287,7 @@ def batch_benchmark(mdf, torch, stream, steps=200, solo_sample=16):
                         "n uniform [0.5,1.5], seed %d" % (BATCH_COUNT, BATCH_SEED),
             "steps": steps, "nodes": nodes, "ms_per_step": ms / steps, "value": batch_mlups, "unit": "MLUPS",
             "launches_per_step": 1, "work_items": info["work_items"], "blocks": info["blocks"],
+            "kernel": batch_kernel, "storage": storage,
             "diverged": int((status == mdf.MDF_E_DIVERGED).sum()), "create_seconds": create_s,
             "one_launch_per_problem_mlups": solo_mlups, "solo_sample": len(idx),
             "speedup_vs_one_launch_per_problem": batch_mlups / solo_mlups}

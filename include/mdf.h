@@ -102,8 +102,11 @@ typedef struct {
  *                     of j = 1..4 in FP16 / BF16 (j = 0 follows, since the
  *                     non-equilibrium part carries no zeroth moment),
  *                     scaled by the power of two 2^(12 - floor(log2 c)):
- *                     28 B/node.  Only periodic Newtonian problems on uniform
- *                     or separable grids (MDF_E_INVALID otherwise); rounding
+ *                     28 B/node.  Periodic Newtonian problems on uniform or
+ *                     separable grids step on the fast path; every other
+ *                     problem (walls, power law, curvilinear grids) on the
+ *                     tile kernel (see mdf_set_launch), also in batches;
+ *                     not with the alpha = 0 distribution.  Rounding
  *                     the non-equilibrium part perturbs each step by at most
  *                     2^-11 (FP16) or 2^-8 (BF16) of |fhat - feq|; in FP16
  *                     a non-equilibrium part above about 16 c overflows and
@@ -255,7 +258,8 @@ mdf_status mdf_launch_info(const mdf_ctx *ctx, int info[8]);
  * rows_per_block is ignored), where a block of 16 x 16 threads computes one
  * 16 x 16 tile in three phases with a recomputed halo of 4 nodes: on grids
  * too small to fill the GPU with long bands it avoids the serial march
- * (FP32 storage without the alpha = 0 distribution).  mdf_create times every
+ * (every storage mode, not with the alpha = 0 distribution; the only plan
+ * for 16-bit storage off the periodic fast path).  mdf_create times every
  * candidate plan for a few steps and keeps the fastest (the tile kernel only
  * if it beats the best march by more than 10 %); this call replaces that
  * choice.  Waits for the context's stream; MDF_E_INVALID for an unsupported
@@ -286,8 +290,9 @@ typedef struct mdf_batch mdf_batch;
 
 /* grids/fluids/bcs: `count` entries each; params: NULL or `count` entries.
  * Each problem starts at rest.  MDF_E_INVALID if the problems cannot share
- * one kernel variant, any problem is invalid (see mdf_create) or asks for
- * 16-bit storage (batches keep FP32 storage). */
+ * one kernel variant, any problem is invalid (see mdf_create), the storage
+ * modes differ or a problem asks for the alpha = 0 distribution.  A batch in
+ * 16-bit storage steps in tile mode (see mdf_batch_set_launch). */
 mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *fluids, const mdf_bc *bcs,
                             const mdf_params *params, mdf_batch **out);
 void mdf_batch_destroy(mdf_batch *batch);

@@ -262,10 +262,6 @@ static mdf_status create_ctx(const mdf_grid *grid, const mdf_fluid *fluid, const
             return fail(nullptr, MDF_E_INVALID, "wall velocities must be finite");
     if (prm.storage < MDF_STORAGE_FP32 || prm.storage > MDF_STORAGE_BF16)
         return fail(nullptr, MDF_E_INVALID, "unknown storage mode %d", prm.storage);
-    if (prm.storage != MDF_STORAGE_FP32 &&
-        !fast_path_applies(grid->kind, fluid->power_law ? 1 : 0, (xwall || ywall) ? 1 : 0))
-        return fail(nullptr, MDF_E_INVALID,
-                    "16-bit storage needs a periodic Newtonian problem on a uniform or separable grid");
     if (prm.rho0 && prm.storage != MDF_STORAGE_FP32)
         return fail(nullptr, MDF_E_INVALID, "the alpha = 0 distribution needs FP32 storage");
     prm.rho0 = prm.rho0 ? 1 : 0;

@@ -38,6 +38,7 @@ struct mdf_batch {
     BatchItem *d_items = nullptr;
     int nitems = 0, grid = 0, occ = 0, smem = 0;
     int tile = 0, occ_tile = 0, smem_tile = 0;     // tile mode: one work item per 16 x 16 tile
+    int storage = 0;                               // StorageKind of every problem (16-bit: tile mode only)
     int forced = 0;                                // some problem has a force, force rate or source
     int cur = 0;
     cudaStream_t stream = nullptr;
@@ -125,8 +126,8 @@ static mdf_status upload_args(mdf_batch *b) {
 
 static cudaError_t launch_one(mdf_batch *b, int parity, cudaStream_t st) {
     if (b->tile)
-        return tile_batch_launch(b->d_items, b->nitems, b->d_args[parity], b->metric, b->power_law, b->walls, b->grid,
-                                 st);
+        return tile_batch_launch(b->d_items, b->nitems, b->d_args[parity], b->metric, b->power_law, b->walls,
+                                 b->storage, b->grid, st);
     return batch_launch(b->d_items, b->nitems, b->d_args[parity], b->d_maps[parity], b->metric, b->power_law,
                         b->walls, b->grid, b->forced, st);
 }
@@ -250,9 +251,10 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
     const int metric = grids[0].kind;
     const int power_law = fluids[0].power_law ? 1 : 0;
     const int walls = (bcs[0].type[0] == MDF_BC_WALL || bcs[0].type[2] == MDF_BC_WALL) ? 1 : 0;
+    const int storage = params ? params[0].storage : MDF_STORAGE_FP32;
     for (int i = 0; i < count && params; ++i) {
-        if (params[i].storage != MDF_STORAGE_FP32)
-            return bfail(nullptr, MDF_E_INVALID, "problem %d: batches keep FP32 storage", i);
+        if (params[i].storage != storage)
+            return bfail(nullptr, MDF_E_INVALID, "problem %d: every problem of a batch has the same storage mode", i);
         if (params[i].rho0) return bfail(nullptr, MDF_E_INVALID, "problem %d: batches do not evolve rho_0", i);
     }
     for (int i = 1; i < count; ++i) {
@@ -266,6 +268,7 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
     b->metric = metric;
     b->power_law = power_law;
     b->walls = walls;
+    b->storage = storage;
 #define BCKC(call)                                          \
     do {                                                    \
         mdf_status s_ = (call);                             \
@@ -307,8 +310,15 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
         BCKE(cudaMemcpy(b->d_maps[p], b->h_maps[p].data(), count * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
     }
     BCKC(upload_args(b));
-    BCKE(tile_batch_occupancy(metric, power_law, walls, &b->occ_tile, &b->smem_tile));
-    if (b->occ_tile >= 1) BCKC(choose_kernel(b));
+    BCKE(tile_batch_occupancy(metric, power_law, walls, storage, &b->occ_tile, &b->smem_tile));
+    if (storage != MDF_STORAGE_FP32) {
+        // the marches of a batch keep FP32 storage
+        if (b->occ_tile < 1) BCKC(bfail(b, MDF_E_INVALID, "the tile kernel does not fit"));
+        b->tile = 1;
+        BCKC(build_items(b));
+    } else if (b->occ_tile >= 1) {
+        BCKC(choose_kernel(b));
+    }
     BCKE(cudaMallocHost(&b->h_res, (size_t)count * 5 * sizeof(double)));
     BCKE(cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking));
     BCKE(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
@@ -459,6 +469,8 @@ mdf_status mdf_batch_set_launch(mdf_batch *b, int kind) {
     if (!b) return MDF_E_INVALID;
     if (kind != 0 && kind != 1) return bfail(b, MDF_E_INVALID, "kind must be 0 (march) or 1 (tile)");
     if (kind == 1 && b->occ_tile < 1) return bfail(b, MDF_E_INVALID, "the tile kernel does not fit");
+    if (kind == 0 && b->storage != MDF_STORAGE_FP32)
+        return bfail(b, MDF_E_INVALID, "the marches of a batch keep FP32 storage");
     BCK(b, cudaStreamSynchronize(b->stream));
     BCK(b, cudaStreamSynchronize(b->cstream));
     b->tile = kind;

@@ -71,8 +71,11 @@ int step_candidates(int metric, int power_law, int walls, int storage, int rho0,
     *err = cudaSuccess;
     const bool fast = !rho0 && fast_path_applies(metric, power_law, walls);
     const bool wpath = !rho0 && !fast && walls_path_applies(metric, power_law, walls, storage);
+    // the shared-ring march keeps FP32 storage; 16-bit storage off the fast
+    // path has the tile kernel only
+    const bool march = fast || wpath || storage == STORAGE_FP32;
     const int nts[2] = {128, 256};
-    for (int i = 0; i < (fast || wpath ? 2 : 1); ++i) {
+    for (int i = 0; march && i < (fast || wpath ? 2 : 1); ++i) {
         int occ = 0, smem = 0;
         cudaError_t e = fast    ? fast_occupancy(metric, storage, nts[i], &occ, &smem)
                         : wpath ? walls_occupancy(metric, power_law, nts[i], &occ, &smem)
@@ -88,7 +91,7 @@ int step_candidates(int metric, int power_law, int walls, int storage, int rho0,
     // the tile kernel, last: the marches stay the default
     if (tile_path_applies(storage, rho0) && n < max) {
         int tx = 0, ty = 0, occ = 0, smem = 0;
-        const cudaError_t e = tile_occupancy(metric, power_law, walls, &tx, &ty, &occ, &smem);
+        const cudaError_t e = tile_occupancy(metric, power_law, walls, storage, &tx, &ty, &occ, &smem);
         if (e != cudaSuccess) {
             *err = e;
             return n;

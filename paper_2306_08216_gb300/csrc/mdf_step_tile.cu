@@ -1,471 +1,53 @@
-// mdf_step_tile.cu -- the fused MDF-FDLBM step on grids too small to keep the
-// GPU busy with marching bands.
-//
-// Same time step as the marches (Sec. 2.2 Steps (1)-(4) of arXiv:2306.08216
-// with Eqs. 2.3.24-2.3.25, f32x2 pairs for alpha = u, v, every grid kind,
-// walls by non-equilibrium extrapolation, power law), organised per 2-D
-// tile instead of per band: a block of TX x TY threads owns a TX x TY tile
-// of output nodes and performs the step in three phases separated by
-// barriers:
-//   A  fhat(t) of the tile plus a halo of 4 (read from L2/HBM with plain
-//      loads) -> fbar^+ of every node of that region into shared memory;
-//      fhat^+ of the thread's own node stays in registers (and, for a power
-//      law, the recovery rates of the nodes of the inner region go to shared
-//      memory);
-//   B  fbar (pass 1, Eq. 2.3.25) and f(t+h) (Eq. 2.2.16) on the tile plus a
-//      halo of 2 -> shared memory; then the wall nodes of that region by NEE
-//      from their interior neighbour;
-//   C  fhat(t+dt) (pass 2, Eq. 2.3.24) of the thread's own node -> HBM, and
-//      the NEE value of an adjacent wall node.
-// The halo is recomputed (a 16 x 16 tile computes fbar^+ on 24 x 24 nodes
-// and f on 20 x 20), which the marches avoid; in exchange a step is three
-// short phases per block instead of a march of H + 9 rows, and a 257^2 grid
-// is 289 blocks of 8 warps instead of a few hundred 4-warp marches, so
-// small grids are no longer bound by the length of a serial march.
-#include "mdf_device.cuh"
+// mdf_step_tile.cu -- the tile kernel (mdf_tile.cuh) with FP32 storage, and
+// the entry points that pick the storage mode's instantiation.
+#include "mdf_tile.cuh"
 
 namespace mdf {
 
-namespace {
+MDF_TILE_DEFINE(STORAGE_FP32)
 
-using namespace dev;
-
-// Three 256-thread blocks per SM (at most 85 registers; a few variants spill
-// 20-24 bytes): on the 513^2 trapezoid cavities 18 % faster than two.
-constexpr int kTileMinBlocks = 3;
-
-__device__ __forceinline__ F2 pair_of_bits(unsigned long long bits) {
-    F2 p;
-    p.r = bits;
-    return p;
+// Every storage mode; the alpha = 0 distribution has no tile form.
+bool tile_path_applies(int storage, int rho0) {
+    (void)storage;
+    return !rho0;
 }
 
-// Index of node i on an axis of n nodes: unchanged on a walled axis, else
-// the periodic image.  Region nodes lie within a few tiles of the domain, so
-// the integer modulo is needed only on grids smaller than the region.
-__device__ __forceinline__ int axis_index(int i, int n, bool wall) {
-    if (wall || (i >= 0 && i < n)) return i;
-    if (i < 0 && i >= -n) return i + n;
-    if (i >= n && i < 2 * n) return i - n;
-    return wrap(i, n);
-}
-
-template <int TX, int TY>
-struct Tile {
-    static constexpr int NT = TX * TY;
-    static constexpr int X8 = TX + 8, Y8 = TY + 8, N8 = X8 * Y8;  // fbar^+ region: tile + 4
-    static constexpr int X4 = TX + 4, Y4 = TY + 4, N4 = X4 * Y4;  // f region: tile + 2
-    static constexpr int B_BYTES = 5 * N8 * 8;
-    static constexpr int F_BYTES = 5 * N4 * 8;
-    static constexpr int K_BYTES = 2 * N4 * 4;
-};
-
-// Difference weights of one axis (as the marches): w = -step k (a1, a0, am2).
-struct TW {
-    F2 w1, w0, w2;
-};
-__device__ __forceinline__ TW tweights(float k, float step, const StepArgs &a) {
-    return TW{splat(-step * k * a.a1), splat(-step * k * a.a0), splat(-step * k * a.am2)};
-}
-
-// Streaming increment of population j at a curvilinear node n of the pair
-// array A (row stride S), upwinded by the sign of each contravariant speed.
-template <int NN>
-__device__ __forceinline__ F2 curvi_tile(const unsigned char *A, int j, int n, int S, float cxi, float ceta,
-                                         bool xadj_p, bool xadj_m, bool yadj_p, bool yadj_m, float step,
-                                         const StepArgs &a, F2 acc) {
-    auto at = [&](int m) { return lds2(A, (j * NN + m) * 8); };
-    const F2 p0 = at(n);
-    if (cxi != 0.0f) {
-        const float k = -step * fabsf(cxi);
-        const F2 w1 = splat(k * a.a1), w0 = splat(k * a.a0), w2 = splat(k * a.am2);
-        if (cxi > 0.0f) acc = stream2<true>(acc, at(n + 1), p0, at(n - 1), at(n - 2), xadj_p, w1, w0, w2);
-        else acc = stream2<true>(acc, at(n - 1), p0, at(n + 1), at(n + 2), xadj_m, w1, w0, w2);
-    }
-    if (ceta != 0.0f) {
-        const float k = -step * fabsf(ceta);
-        const F2 w1 = splat(k * a.a1), w0 = splat(k * a.a0), w2 = splat(k * a.am2);
-        if (ceta > 0.0f) acc = stream2<true>(acc, at(n + S), p0, at(n - S), at(n - 2 * S), yadj_p, w1, w0, w2);
-        else acc = stream2<true>(acc, at(n - S), p0, at(n + S), at(n + 2 * S), yadj_m, w1, w0, w2);
-    }
-    return acc;
-}
-
-// Streaming increments of populations 1..4 at node n of the pair array A
-// (NN nodes per population, row stride S), added to out[1..4].  The grid
-// coordinates (Xw, Yw) locate the metric coefficients.
-template <int NN, int MK, bool WALLS>
-__device__ __forceinline__ void stream_tile(const unsigned char *A, int n, int S, float step, int Xw, int Yw,
-                                            bool xadj_p, bool xadj_m, bool yadj_p, bool yadj_m, const StepArgs &a,
-                                            F2 out[5]) {
-    auto at = [&](int j, int m) { return lds2(A, (j * NN + m) * 8); };
-    if (MK != METRIC_CURVILINEAR) {
-        TW wx, wy;
-        if (MK == METRIC_UNIFORM) {
-            wx = tweights(a.kx, step, a);
-            wy = tweights(a.ky, step, a);
-        } else {
-            wx = tweights(a.kxv[GHOST + Xw], step, a);
-            wy = tweights(a.kyv[Yw], step, a);
-        }
-        out[1] = stream2<WALLS>(out[1], at(1, n + 1), at(1, n), at(1, n - 1), at(1, n - 2), xadj_p, wx.w1, wx.w0,
-                                wx.w2);
-        out[3] = stream2<WALLS>(out[3], at(3, n - 1), at(3, n), at(3, n + 1), at(3, n + 2), xadj_m, wx.w1, wx.w0,
-                                wx.w2);
-        out[2] = stream2<WALLS>(out[2], at(2, n + S), at(2, n), at(2, n - S), at(2, n - 2 * S), yadj_p, wy.w1, wy.w0,
-                                wy.w2);
-        out[4] = stream2<WALLS>(out[4], at(4, n - S), at(4, n), at(4, n + S), at(4, n + 2 * S), yadj_m, wy.w1, wy.w0,
-                                wy.w2);
-    } else {
-        const long long mi = (long long)Yw * a.pitch + GHOST + Xw;
-        const float cxx = a.mxx[mi], cxy = a.mxy[mi], cex = a.mex[mi], cey = a.mey[mi];
-        out[1] = curvi_tile<NN>(A, 1, n, S, cxx, cex, xadj_p, xadj_m, yadj_p, yadj_m, step, a, out[1]);
-        out[2] = curvi_tile<NN>(A, 2, n, S, cxy, cey, xadj_p, xadj_m, yadj_p, yadj_m, step, a, out[2]);
-        out[3] = curvi_tile<NN>(A, 3, n, S, -cxx, -cex, xadj_p, xadj_m, yadj_p, yadj_m, step, a, out[3]);
-        out[4] = curvi_tile<NN>(A, 4, n, S, -cxy, -cey, xadj_p, xadj_m, yadj_p, yadj_m, step, a, out[4]);
-    }
-}
-
-template <int TX, int TY, int MK, bool WALLS>
-__device__ __forceinline__ void tile_output(const StepArgs &a, int X, int Y, int li, int lj, const unsigned char *Fs,
-                                            const F2 hp[5]);
-
-// One tile (bx, by) of one problem.  Every thread reaches every barrier
-// (no early exit), so a block may step several tiles in a row: the barrier
-// after phase A of the next tile orders its shared-memory writes after the
-// reads of the previous tile.
-template <int TX, int TY, int MK, bool PL, bool WALLS>
-__device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, unsigned char *smem) {
-    using T = Tile<TX, TY>;
-    unsigned char *Bs = smem;                          // fbar^+ [5][N8] pairs
-    unsigned char *Fs = smem + T::B_BYTES;             // f(t+h) [5][N4] pairs
-    float *Ks = reinterpret_cast<float *>(Fs + T::F_BYTES);  // power law: rkp [N4], rk [N4]
-
-    const int t = threadIdx.x;
-    const int x0 = bx * TX, y0 = by * TY;
-    const bool xwall = WALLS && a.xwall, ywall = WALLS && a.ywall;
-    const float c = a.c, inv2c = a.inv2c;
-    const F2 mKp = pair_of_bits(a.pmKp), Dp = pair_of_bits(a.pDp), mKb = pair_of_bits(a.pmKb), Db = pair_of_bits(a.pDb);
-
-    // ------------------------------------------------ A: fbar^+ on tile + 4
-    // The thread's nodes of the region: first its own output node, then
-    // nodes of the halo ring (4 rows above, 4 below, 4 columns each side).
-    // All their loads are issued before any arithmetic, so that the passes
-    // share one memory latency.
-    constexpr int PASSES = (T::N8 + T::NT - 1) / T::NT;
-    auto region_node = [&](int i, int &lx, int &ly) {
-        if (i < T::NT) {
-            lx = 4 + i % TX;
-            ly = 4 + i / TX;
-            return;
-        }
-        int h = i - T::NT;
-        if (h < 4 * T::X8) {
-            ly = h / T::X8;
-            lx = h % T::X8;
-        } else if (h < 8 * T::X8) {
-            h -= 4 * T::X8;
-            ly = TY + 4 + h / T::X8;
-            lx = h % T::X8;
-        } else {
-            h -= 8 * T::X8;
-            ly = 4 + h / 8;
-            const int cc = h % 8;
-            lx = cc < 4 ? cc : TX + cc;
-        }
-    };
-    F2 gq[PASSES][5];
-#pragma unroll
-    for (int q = 0; q < PASSES; ++q) {
-        const int i = t + q * T::NT;
-#pragma unroll
-        for (int j = 0; j < 5; ++j) gq[q][j] = splat(0.0f);
-        if (i < T::N8) {
-            int lx, ly;
-            region_node(i, lx, ly);
-            const int X = x0 - 4 + lx, Y = y0 - 4 + ly;
-            const bool ok = (xwall ? (X >= 0 && X < a.nx) : true) && (ywall ? (Y >= 0 && Y < a.ny) : true);
-            if (ok) {
-                const long long s =
-                    (long long)axis_index(Y, a.ny, ywall) * a.pitch + GHOST + axis_index(X, a.nx, xwall);
-#pragma unroll
-                for (int j = 0; j < 5; ++j) gq[q][j] = mk2(a.fin[j * a.plane + s], a.fin[(5 + j) * a.plane + s]);
-            }
-        }
-    }
-    F2 hp[5];  // fhat^+ of the thread's own node
-#pragma unroll
-    for (int q = 0; q < PASSES; ++q) {
-        const int i = t + q * T::NT;
-        if (i >= T::N8) break;
-        int lx, ly;
-        region_node(i, lx, ly);
-        const int X = x0 - 4 + lx, Y = y0 - 4 + ly;
-        const bool okx = xwall ? (X >= 0 && X < a.nx) : true;
-        const bool oky = ywall ? (Y >= 0 && Y < a.ny) : true;
-        const int Xw = axis_index(X, a.nx, xwall), Yw = axis_index(Y, a.ny, ywall);
-        const F2 *g = gq[q];
-        const Mom2 m = (a.r_mode && okx && oky) ? moments2r(g, c, a.rk_hat * source_at(a, Yw, Xw)) : moments2(g, c);
-        F2 n[5];
-        noneq2(g, m, inv2c, n);
-        const F2 n13 = n[1] - n[3], n24 = n[2] - n[4];
-        F2 mKp_ = mKp, Dp_ = Dp, mKb_ = mKb, Db_ = Db;
-        if (PL) {
-            float gx1, gx2, gy1, gy2;
-            split2(splat(c) * n13, gx1, gx2);
-            split2(splat(c) * n24, gy1, gy2);
-            const float sxy = 0.5f * (gy1 + gx2);
-            const float gg = sqrtf(2.0f * (gx1 * gx1 + gy2 * gy2 + 2.0f * sxy * sxy));
-            const Rates Rr = rates_for(a.cs2 / power_law_nu(gg, a), a.s_ratio, a.dt);
-            mKp_ = splat(-(1.0f - Rr.rpp));
-            Dp_ = splat(0.5f * (Rr.rp - Rr.rpp));
-            mKb_ = splat(-(1.0f - Rr.rbp));
-            Db_ = splat(0.5f * (Rr.rb - Rr.rbp));
-            if (lx >= 2 && lx < T::X8 - 2 && ly >= 2 && ly < T::Y8 - 2) {
-                const int n4 = (ly - 2) * T::X4 + (lx - 2);
-                Ks[n4] = Rr.rkp;
-                Ks[T::N4 + n4] = Rr.rk;
-            }
-        }
-        F2 o[5];
-        if (q == 0) relax2(g, n, n13, n24, mKp_, Dp_, hp);
-        relax2(g, n, n13, n24, mKb_, Db_, o);
-        const int n8 = ly * T::X8 + lx;
-#pragma unroll
-        for (int j = 0; j < 5; ++j) sts2(Bs, (j * T::N8 + n8) * 8, o[j]);
-    }
-    __syncthreads();
-
-    // ------------------------------------------------ B: f(t+h) on tile + 2
-    const F2 hw = splat(a.h * 0.2f);
-    const F2 mKk = pair_of_bits(a.pmKk), Dk = pair_of_bits(a.pDk);
-#pragma unroll 1
-    for (int i4 = t; i4 < T::N4; i4 += T::NT) {
-        const int lx4 = i4 % T::X4, ly4 = i4 / T::X4;
-        const int X = x0 - 2 + lx4, Y = y0 - 2 + ly4;
-        if (WALLS) {
-            const bool skip = (xwall && (X <= 0 || X >= a.nx - 1)) || (ywall && (Y <= 0 || Y >= a.ny - 1));
-            if (skip) {  // beyond or on a wall: NEE below (the values beyond are never read)
-#pragma unroll
-                for (int j = 0; j < 5; ++j) sts2(Fs, (j * T::N4 + i4) * 8, splat(0.0f));
-                continue;
-            }
-        }
-        const int Xw = axis_index(X, a.nx, xwall), Yw = axis_index(Y, a.ny, ywall);
-        const bool xadj_p = xwall && X == 1, xadj_m = xwall && X == a.nx - 2;
-        const bool yadj_p = ywall && Y == 1, yadj_m = ywall && Y == a.ny - 2;
-        const int n8 = (ly4 + 2) * T::X8 + lx4 + 2;
-        F2 fF = splat(0.0f);
-        if (a.force_mode == 1) fF = hw * mk2(a.Fx, a.Fy);
-        else if (a.force_mode == 2) {
-            const long long fi = (long long)Yw * a.pitch + GHOST + Xw;
-            fF = hw * mk2(a.Fxp[fi], a.Fyp[fi]);
-        }
-        // Step 2 (pass 1): fbar = fbar^+ - h c.grad fbar^+ + h w F
-        F2 fb[5];
-#pragma unroll
-        for (int j = 0; j < 5; ++j) fb[j] = lds2(Bs, (j * T::N8 + n8) * 8) + fF;
-        stream_tile<T::N8, MK, WALLS>(Bs, n8, T::X8, a.h, Xw, Yw, xadj_p, xadj_m, yadj_p, yadj_m, a, fb);
-        // Step 3: f = feq + (I + h/2 Lt)^-1 (fbar - feq)
-        F2 mKk_ = mKk, Dk_ = Dk;
-        if (PL) {
-            const float kp = Ks[i4], kk = Ks[T::N4 + i4];
-            mKk_ = splat(-(1.0f - kp));
-            Dk_ = splat(0.5f * (kk - kp));
-        }
-        const Mom2 m = a.r_mode ? moments2r(fb, c, a.rk_bar * source_at(a, Yw, Xw)) : moments2(fb, c);
-        F2 n[5], f[5];
-        noneq2(fb, m, inv2c, n);
-        relax2(fb, n, n[1] - n[3], n[2] - n[4], mKk_, Dk_, f);
-#pragma unroll
-        for (int j = 0; j < 5; ++j) sts2(Fs, (j * T::N4 + i4) * 8, f[j]);
-    }
-    __syncthreads();
-    if (WALLS) {
-        // wall nodes of the f region from their interior neighbour (corners:
-        // the diagonal neighbour and the west/east wall velocity)
-#pragma unroll 1
-        for (int i4 = t; i4 < T::N4; i4 += T::NT) {
-            const int lx4 = i4 % T::X4, ly4 = i4 / T::X4;
-            const int X = x0 - 2 + lx4, Y = y0 - 2 + ly4;
-            const bool inx = X >= 0 && X < a.nx, iny = Y >= 0 && Y < a.ny;
-            const bool wx = xwall && (X == 0 || X == a.nx - 1) && iny;
-            const bool wy = ywall && (Y == 0 || Y == a.ny - 1) && inx;
-            if (!(wx || wy)) continue;
-            const int dx = xwall ? (X == 0 ? 1 : (X == a.nx - 1 ? -1 : 0)) : 0;
-            const int dy = ywall ? (Y == 0 ? 1 : (Y == a.ny - 1 ? -1 : 0)) : 0;
-            const int side = (xwall && dx != 0) ? (X == 0 ? 0 : 1) : (Y == 0 ? 2 : 3);
-            const int nb = i4 + dy * T::X4 + dx;
-            F2 g[5], w[5];
-#pragma unroll
-            for (int j = 0; j < 5; ++j) g[j] = lds2(Fs, (j * T::N4 + nb) * 8);
-            nee2(g, a.uw[side], a.vw[side], inv2c, w);
-#pragma unroll
-            for (int j = 0; j < 5; ++j) sts2(Fs, (j * T::N4 + i4) * 8, w[j]);
-        }
-        __syncthreads();
-    }
-
-    // ------------------------------------------------ C: fhat(t+dt) of the own node
-    const int li = t % TX, lj = t / TX;
-    const int X = x0 + li, Y = y0 + lj;
-    if (X >= a.nx || Y >= a.ny) return;
-    if (WALLS && ((xwall && (X == 0 || X == a.nx - 1)) || (ywall && (Y == 0 || Y == a.ny - 1)))) return;
-    tile_output<TX, TY, MK, WALLS>(a, X, Y, li, lj, Fs, hp);
-}
-
-// Phase C of the own node (X, Y): pass 2 from the f region, the output and
-// the NEE output of an adjacent wall node.
-template <int TX, int TY, int MK, bool WALLS>
-__device__ __forceinline__ void tile_output(const StepArgs &a, int X, int Y, int li, int lj, const unsigned char *Fs,
-                                            const F2 hp[5]) {
-    using T = Tile<TX, TY>;
-    const bool xwall = WALLS && a.xwall, ywall = WALLS && a.ywall;
-    const float inv2c = a.inv2c;
-    const bool xadj_p = xwall && X == 1, xadj_m = xwall && X == a.nx - 2;
-    const bool yadj_p = ywall && Y == 1, yadj_m = ywall && Y == a.ny - 2;
-    const int n4 = (lj + 2) * T::X4 + li + 2;
-    F2 fF = splat(0.0f);
-    const F2 dw = splat(a.dt * 0.2f);
-    if (a.force_mode_d == 1) fF = dw * mk2(a.Fxd, a.Fyd);
-    else if (a.force_mode_d == 2) {
-        const long long fi = (long long)Y * a.pitch + GHOST + X;
-        fF = dw * mk2(a.Fxdp[fi], a.Fydp[fi]);
-    }
-    F2 out[5];
-#pragma unroll
-    for (int j = 0; j < 5; ++j) out[j] = hp[j] + fF;
-    stream_tile<T::N4, MK, WALLS>(Fs, n4, T::X4, a.dt, X, Y, xadj_p, xadj_m, yadj_p, yadj_m, a, out);
-    if (!WALLS) {
-        store_node<true>(a, Y, X, out);
-        return;
-    }
-    if (xwall) store_node<false>(a, Y, X, out);
-    else store_node<true>(a, Y, X, out);
-    F2 w[5];
-    if (xadj_p) { nee2(out, a.uw[0], a.vw[0], inv2c, w); store_node<false>(a, Y, 0, w); }
-    if (xadj_m) { nee2(out, a.uw[1], a.vw[1], inv2c, w); store_node<false>(a, Y, a.nx - 1, w); }
-    if (ywall && (Y == 1 || Y == a.ny - 2)) {
-        const int rr = (Y == 1) ? 0 : a.ny - 1;
-        const int side = (Y == 1) ? 2 : 3;
-        nee2(out, a.uw[side], a.vw[side], inv2c, w);
-        if (xwall) store_node<false>(a, rr, X, w);
-        else store_node<true>(a, rr, X, w);
-        if (xadj_p) { nee2(out, a.uw[0], a.vw[0], inv2c, w); store_node<false>(a, rr, 0, w); }
-        if (xadj_m) { nee2(out, a.uw[1], a.vw[1], inv2c, w); store_node<false>(a, rr, a.nx - 1, w); }
-    }
-}
-
-template <int TX, int TY, int MK, bool PL, bool WALLS>
-__global__ void __launch_bounds__(TX *TY, kTileMinBlocks) tile_kernel(const StepArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    tile_step<TX, TY, MK, PL, WALLS>(a, blockIdx.x, blockIdx.y, smem);
-}
-
-// Many problems in one persistent launch: block b steps work items
-// b, b + gridDim.x, ... (problem, tile x, tile y), largest problems first.
-template <int TX, int TY, int MK, bool PL, bool WALLS>
-__global__ void __launch_bounds__(TX *TY, kTileMinBlocks) tile_batch_kernel(const BatchItem *__restrict__ items, int nitems,
-                                                               const StepArgs *__restrict__ args) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-        const BatchItem item = items[w];
-        tile_step<TX, TY, MK, PL, WALLS>(args[item.problem], item.bx, item.by, smem);
-    }
-}
-
-constexpr int kTX = TILE_X, kTY = TILE_Y;
-
-template <int MK, bool PL, bool WALLS>
-constexpr int tile_smem() {
-    using T = Tile<kTX, kTY>;
-    return T::B_BYTES + T::F_BYTES + (PL ? T::K_BYTES : 0);
-}
-
-template <int MK, bool PL, bool WALLS>
-cudaError_t tile_occupancy_t(int *occ, int *smem) {
-    auto k = tile_kernel<kTX, kTY, MK, PL, WALLS>;
-    *smem = tile_smem<MK, PL, WALLS>();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, kTX * kTY, *smem);
-}
-
-template <int MK, bool PL, bool WALLS>
-cudaError_t tile_launch_t(const StepArgs &args, const StepPlan &plan, cudaStream_t stream) {
-    auto k = tile_kernel<kTX, kTY, MK, PL, WALLS>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_smem<MK, PL, WALLS>());
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    k<<<dim3(plan.gx, plan.gy), kTX * kTY, tile_smem<MK, PL, WALLS>(), stream>>>(args);
-    return cudaGetLastError();
-}
-
-template <int MK, bool PL, bool WALLS>
-cudaError_t tile_batch_occupancy_t(int *occ, int *smem) {
-    auto k = tile_batch_kernel<kTX, kTY, MK, PL, WALLS>;
-    *smem = tile_smem<MK, PL, WALLS>();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, kTX * kTY, *smem);
-}
-
-template <int MK, bool PL, bool WALLS>
-cudaError_t tile_batch_launch_t(const BatchItem *items, int nitems, const StepArgs *args, int grid,
-                                cudaStream_t stream) {
-    auto k = tile_batch_kernel<kTX, kTY, MK, PL, WALLS>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_smem<MK, PL, WALLS>());
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    k<<<grid, kTX * kTY, tile_smem<MK, PL, WALLS>(), stream>>>(items, nitems, args);
-    return cudaGetLastError();
-}
-
-#define MDF_TILE_DISPATCH(FN, ...)                                                 \
-    switch (metric * 4 + (power_law ? 2 : 0) + (walls ? 1 : 0)) {                  \
-        case 0: return FN<METRIC_UNIFORM, false, false>(__VA_ARGS__);              \
-        case 1: return FN<METRIC_UNIFORM, false, true>(__VA_ARGS__);               \
-        case 2: return FN<METRIC_UNIFORM, true, false>(__VA_ARGS__);               \
-        case 3: return FN<METRIC_UNIFORM, true, true>(__VA_ARGS__);                \
-        case 4: return FN<METRIC_SEPARABLE, false, false>(__VA_ARGS__);            \
-        case 5: return FN<METRIC_SEPARABLE, false, true>(__VA_ARGS__);             \
-        case 6: return FN<METRIC_SEPARABLE, true, false>(__VA_ARGS__);             \
-        case 7: return FN<METRIC_SEPARABLE, true, true>(__VA_ARGS__);              \
-        case 8: return FN<METRIC_CURVILINEAR, false, false>(__VA_ARGS__);          \
-        case 9: return FN<METRIC_CURVILINEAR, false, true>(__VA_ARGS__);           \
-        case 10: return FN<METRIC_CURVILINEAR, true, false>(__VA_ARGS__);          \
-        default: return FN<METRIC_CURVILINEAR, true, true>(__VA_ARGS__);           \
-    }
-
-}  // namespace
-
-bool tile_path_applies(int storage, int rho0) { return storage == STORAGE_FP32 && !rho0; }
-
-cudaError_t tile_occupancy(int metric, int power_law, int walls, int *tx, int *ty, int *occ, int *smem) {
+cudaError_t tile_occupancy(int metric, int power_law, int walls, int storage, int *tx, int *ty, int *occ, int *smem) {
     *tx = kTX;
     *ty = kTY;
-    MDF_TILE_DISPATCH(tile_occupancy_t, occ, smem)
+    switch (storage) {
+        case STORAGE_FP16: return tile_occupancy_st<STORAGE_FP16>(metric, power_law, walls, occ, smem);
+        case STORAGE_BF16: return tile_occupancy_st<STORAGE_BF16>(metric, power_law, walls, occ, smem);
+        default: return tile_occupancy_st<STORAGE_FP32>(metric, power_law, walls, occ, smem);
+    }
 }
 
 cudaError_t tile_launch(const StepArgs &args, int metric, const StepPlan &plan, cudaStream_t stream) {
-    const int power_law = args.power_law;
-    const int walls = (args.xwall || args.ywall) ? 1 : 0;
-    MDF_TILE_DISPATCH(tile_launch_t, args, plan, stream)
+    switch (args.storage) {
+        case STORAGE_FP16: return tile_launch_st<STORAGE_FP16>(args, metric, plan, stream);
+        case STORAGE_BF16: return tile_launch_st<STORAGE_BF16>(args, metric, plan, stream);
+        default: return tile_launch_st<STORAGE_FP32>(args, metric, plan, stream);
+    }
 }
 
-cudaError_t tile_batch_occupancy(int metric, int power_law, int walls, int *occ, int *smem) {
-    MDF_TILE_DISPATCH(tile_batch_occupancy_t, occ, smem)
+cudaError_t tile_batch_occupancy(int metric, int power_law, int walls, int storage, int *occ, int *smem) {
+    switch (storage) {
+        case STORAGE_FP16: return tile_batch_occupancy_st<STORAGE_FP16>(metric, power_law, walls, occ, smem);
+        case STORAGE_BF16: return tile_batch_occupancy_st<STORAGE_BF16>(metric, power_law, walls, occ, smem);
+        default: return tile_batch_occupancy_st<STORAGE_FP32>(metric, power_law, walls, occ, smem);
+    }
 }
 
 cudaError_t tile_batch_launch(const BatchItem *items, int nitems, const StepArgs *args, int metric, int power_law,
-                              int walls, int grid, cudaStream_t stream) {
-    MDF_TILE_DISPATCH(tile_batch_launch_t, items, nitems, args, grid, stream)
+                              int walls, int storage, int grid, cudaStream_t stream) {
+    switch (storage) {
+        case STORAGE_FP16:
+            return tile_batch_launch_st<STORAGE_FP16>(items, nitems, args, metric, power_law, walls, grid, stream);
+        case STORAGE_BF16:
+            return tile_batch_launch_st<STORAGE_BF16>(items, nitems, args, metric, power_law, walls, grid, stream);
+        default:
+            return tile_batch_launch_st<STORAGE_FP32>(items, nitems, args, metric, power_law, walls, grid, stream);
+    }
 }
 
 }  // namespace mdf

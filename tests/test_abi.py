@@ -77,11 +77,8 @@ def _good():
                         setattr(f, "nu_min", 2.0), setattr(f, "nu_max", 1.0)),
     lambda g, f, b, p: setattr(p, "storage", 3),          # unknown storage mode
     lambda g, f, b, p: setattr(p, "storage", -1),
-    # 16-bit storage only on periodic Newtonian problems (uniform / separable grids)
-    lambda g, f, b, p: (setattr(p, "storage", 1), b.type.__setitem__(0, 1), b.type.__setitem__(1, 1)),
-    lambda g, f, b, p: (setattr(p, "storage", 2), b.type.__setitem__(2, 1), b.type.__setitem__(3, 1)),
-    lambda g, f, b, p: (setattr(p, "storage", 2), setattr(f, "power_law", 1), setattr(f, "K", 0.01),
-                        setattr(f, "n", 0.5), setattr(f, "nu_min", 1e-4), setattr(f, "nu_max", 1.0)),
+    # 16-bit storage with the alpha = 0 distribution
+    lambda g, f, b, p: (setattr(p, "storage", 1), setattr(p, "rho0", 1)),
 ])
 def test_invalid_arguments_rejected_before_any_cuda_call(lib, mutate):
     g, f, b, p = _good()
@@ -100,23 +97,25 @@ def test_null_arguments(lib):
     assert lib.mdf_steps_done(None) == -1
 
 
-def test_16bit_storage_rejected_on_curvilinear_grids(lib):
-    """A valid curvilinear problem is accepted up to the storage check: the
-    16-bit layouts exist for the periodic fast path only."""
+def test_16bit_storage_passes_validation_on_every_grid_kind(lib):
+    """16-bit storage is valid on curvilinear grids with walls and a power law
+    (the tile kernel serves it): validation passes, and without a GPU the
+    call fails only at the first CUDA call."""
     n = 16
     X, Y = np.meshgrid(np.arange(n) / n, np.arange(n) / n)
-    g, f, b, p = mdf.problem_structs(n, n, grid="curvilinear", x=X + 0.05 * Y, y=Y, storage="fp16")[:4]
+    g, f, b, p = mdf.problem_structs(n, n, grid="curvilinear", x=X + 0.05 * Y, y=Y, storage="fp16",
+                                     walls=(True, True), power_law=(0.01, 0.8, 1e-4, 1.0))[:4]
     st, msg = mdf.create_status(g, f, b, p)
-    assert st == mdf.MDF_E_INVALID and "16-bit" in msg, (st, msg)
+    assert st != mdf.MDF_E_INVALID, (st, msg)
 
 
-def test_batch_rejects_16bit_storage(lib):
+def test_batch_rejects_mixed_storage(lib):
     g, f, b, p = _good()
-    p.storage = 1
-    G, F, B, P = (mdf.Grid * 2)(g, g), (mdf.Fluid * 2)(f, f), (mdf.BC * 2)(b, b), (mdf.Params * 2)(p, p)
+    q = mdf.Params(1.0, 0.5, 0.8, 1.5, 1)
+    G, F, B, P = (mdf.Grid * 2)(g, g), (mdf.Fluid * 2)(f, f), (mdf.BC * 2)(b, b), (mdf.Params * 2)(p, q)
     h = ctypes.c_void_p()
     assert lib.mdf_batch_create(2, G, F, B, P, ctypes.byref(h)) == mdf.MDF_E_INVALID
-    assert b"FP32 storage" in lib.mdf_batch_last_error(None)
+    assert b"same storage mode" in lib.mdf_batch_last_error(None)
 
 
 def test_rho0_needs_fp32_storage(lib):
