@@ -12,7 +12,10 @@
 // curvilinear grids and holds the launch planning and dispatch.  Uniform
 // and separable grids run the register-window marches of mdf_step_fast.cu
 // (periodic, Newtonian) and mdf_step_walls.cu (walls and/or power law);
-// with the alpha = 0 distribution every grid runs mdf_step_rho0.cu.
+// with the alpha = 0 distribution every grid runs mdf_step_rho0.cu.  The
+// tile kernel (mdf_tile.cuh) is a candidate plan on every grid and the only
+// one for 16-bit storage off the periodic fast path; the autotuner of
+// mdf_create chooses between the families by timing.
 // The MRT matrix of Eq. 2.2.4 with s0 = s3 = s4 = s' and s1 = s2 = s equals
 // s' I + (s - s') P_c, P_c the projector on the first moments, so every
 // function of it acts on a distribution through its zeroth and first moments
