@@ -159,9 +159,9 @@ static mdf_status autotune(mdf_ctx *c) {
         CK(c, cudaEventCreate(&e1));
         float best = 1e30f, best_tile = 1e30f;
         int best_i = 0, tile_i = -1;
-        // two rounds over the candidates, 8 timed launches each; keep the
+        // two passes over the candidates, 8 timed launches each; keep the
         // fastest time seen per candidate
-        for (int round = 0; round < 2; ++round)
+        for (int pass = 0; pass < 2; ++pass)
         for (int i = 0; i < c->ncand; ++i) {
             c->plan = c->cand[i];
             mdf_status s = encode_maps(c);

@@ -220,7 +220,7 @@ static mdf_status choose_kernel(mdf_batch *b) {
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));
     float best[2] = {1e30f, 1e30f};
-    for (int round = 0; round < 2; ++round)
+    for (int pass = 0; pass < 2; ++pass)
         for (int k = 0; k < 2; ++k) {
             b->tile = k;
             mdf_status s = build_items(b);
