@@ -269,6 +269,16 @@ mdf_status mdf_set_launch(mdf_ctx *ctx, int threads, int rows_per_block);
 /* Kernel family of the current launch plan: 0 march, 1 tile (-1 for NULL). */
 int mdf_launch_kind(const mdf_ctx *ctx);
 
+/* Debug aid standing in for a memory checker: writes NaN (the 32-bit
+ * pattern 0x7fc07fc0, NaN as FP32 and as each 16-bit half) into every
+ * storage element of both state buffers, all planes, that no valid result
+ * may read -- the row padding past the last ghost column and, on an x axis
+ * with walls, the ghost columns (on a periodic axis they hold periodic
+ * images and stay).  Steps taken afterwards must give the same results,
+ * bit for bit, as without it; a result that changes or turns NaN read
+ * outside its stencil.  Synchronises. */
+mdf_status mdf_debug_poison(mdf_ctx *ctx);
+
 /* Algorithmic bytes moved per node update by the fused step (state read and
  * written once, plus force/metric planes read once). */
 double mdf_bytes_per_node(const mdf_ctx *ctx);

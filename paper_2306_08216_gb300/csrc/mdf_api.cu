@@ -219,6 +219,7 @@ extern "C" {
 
 mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc *bc, const mdf_params *params,
                       mdf_ctx **out) {
+    MdfRange r("mdf_create");
     return create_ctx(grid, fluid, bc, params, 1, out);
 }
 
@@ -660,6 +661,7 @@ static mdf_status build_step_graph(mdf_ctx *c, int parity) {
 
 mdf_status mdf_step(mdf_ctx *c, int n) {
     if (!c) return MDF_E_INVALID;
+    MdfRange r("mdf_step");
     if (n < 0) return fail(c, MDF_E_INVALID, "n must be >= 0");
     int done = 0;
     const int reps = n / mdf_ctx::kGraphSteps;
@@ -691,6 +693,7 @@ mdf_status mdf_step(mdf_ctx *c, int n) {
 
 mdf_status mdf_fields(mdf_ctx *c, unsigned mask, float *const *out, int on_device) {
     if (!c) return MDF_E_INVALID;
+    MdfRange r("mdf_fields");
     if (mask >> 17) return fail(c, MDF_E_INVALID, "unknown field bits in mask");
     if (mask && !out) return fail(c, MDF_E_INVALID, "out is NULL");
     const size_t N = (size_t)c->nx * c->ny;
@@ -726,6 +729,7 @@ mdf_status mdf_fields(mdf_ctx *c, unsigned mask, float *const *out, int on_devic
 
 mdf_status mdf_residual(mdf_ctx *c, double *residual, double drift[2]) {
     if (!c) return MDF_E_INVALID;
+    MdfRange rr("mdf_residual");
     CK(c, aux_residual(c->aux, c->buf[c->cur], c->snap_u, c->snap_v, c->partials, c->result, c->stream));
     CK(c, cudaMemcpyAsync(c->h_result, c->result, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     mdf_status s = wait_stream(c, 0);
@@ -870,6 +874,7 @@ static mdf_status save_raw(mdf_ctx *c, const char *path) {
 
 mdf_status mdf_save(mdf_ctx *c, const char *path) {
     if (!c || !path) return c ? fail(c, MDF_E_INVALID, "path is NULL") : MDF_E_INVALID;
+    MdfRange r("mdf_save");
     if (c->prm.storage != MDF_STORAGE_FP32) return save_raw(c, path);
     const int planes = state_planes(c->prm.storage, c->prm.rho0);
     const size_t N = (size_t)c->nx * c->ny, n = (size_t)planes * N;
@@ -892,6 +897,7 @@ mdf_status mdf_save(mdf_ctx *c, const char *path) {
 
 mdf_status mdf_load(mdf_ctx *c, const char *path) {
     if (!c || !path) return c ? fail(c, MDF_E_INVALID, "path is NULL") : MDF_E_INVALID;
+    MdfRange r("mdf_load");
     FILE *fp = fopen(path, "rb");
     if (!fp) return fail(c, MDF_E_INVALID, "cannot open %s", path);
     char hdr[256];
@@ -984,6 +990,13 @@ mdf_status mdf_set_launch(mdf_ctx *c, int threads, int rows_per_block) {
 }
 
 int mdf_launch_kind(const mdf_ctx *c) { return c ? c->plan.kind : -1; }
+
+mdf_status mdf_debug_poison(mdf_ctx *c) {
+    if (!c) return MDF_E_INVALID;
+    for (int b = 0; b < 2; ++b)
+        CK(c, aux_poison(c->aux, c->buf[b], state_planes(c->prm.storage, c->prm.rho0), c->stream));
+    return wait_stream(c, 0);
+}
 
 double mdf_bytes_per_node(const mdf_ctx *c) {
     if (!c) return NAN;

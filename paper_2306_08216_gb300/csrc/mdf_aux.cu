@@ -645,6 +645,22 @@ cudaError_t aux_residual(const AuxArgs &a, const float *f, float *su, float *sv,
     return cudaGetLastError();
 }
 
+__global__ void poison_kernel(AuxArgs a, float *f, int planes) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (col >= a.pitch) return;
+    const bool pad = col >= a.nx + 2 * GHOST;
+    const bool ghost = a.xwall && (col < GHOST || col >= a.nx + GHOST);
+    if (!(pad || ghost)) return;
+    unsigned *w = reinterpret_cast<unsigned *>(f);
+    for (int k = 0; k < planes; ++k) w[k * a.plane + (long long)y * a.pitch + col] = 0x7fc07fc0u;
+}
+
+cudaError_t aux_poison(const AuxArgs &a, float *f, int planes, cudaStream_t st) {
+    poison_kernel<<<rows_grid(a.pitch, a.ny, 128), 128, 0, st>>>(a, f, planes);
+    return cudaGetLastError();
+}
+
 cudaError_t aux_snapshot(const AuxArgs &a, const float *f, float *su, float *sv, cudaStream_t st) {
     snapshot_kernel<<<rows_grid(a.nx, a.ny, 128), 128, 0, st>>>(a, f, su, sv);
     return cudaGetLastError();

@@ -50,6 +50,11 @@ cudaError_t aux_init_rho0(const AuxArgs &a, const float *rho0, float *f, cudaStr
 cudaError_t aux_rho0_field(const AuxArgs &a, const float *f, float *dense, cudaStream_t st);
 cudaError_t aux_pack_rho0(const AuxArgs &a, const float *f, float *dense, cudaStream_t st);
 cudaError_t aux_unpack_rho0(const AuxArgs &a, const float *dense, float *f, cudaStream_t st);
+// NaN in every column of every row that no valid result may read: the row
+// padding past the last ghost column and, on an x axis with walls, the
+// ghost columns (32-bit pattern 0x7fc07fc0: NaN as FP32 and as each 16-bit
+// half).
+cudaError_t aux_poison(const AuxArgs &a, float *f, int planes, cudaStream_t st);
 cudaError_t aux_snapshot(const AuxArgs &a, const float *f, float *su, float *sv, cudaStream_t st);
 
 }  // namespace mdf

@@ -361,6 +361,7 @@ mdf_status mdf_batch_init_fields(mdf_batch *b, int index, const float *u, const 
 
 mdf_status mdf_batch_step(mdf_batch *b, int n) {
     if (!b) return MDF_E_INVALID;
+    MdfRange r("mdf_batch_step");
     if (n < 0) return bfail(b, MDF_E_INVALID, "n must be >= 0");
     // arguments changed since the last upload (forcing set on a problem)?
     for (int i = 0; i < b->count; ++i)
@@ -425,6 +426,7 @@ mdf_status mdf_batch_set_active(mdf_batch *b, int index, int active) {
 
 mdf_status mdf_batch_residual(mdf_batch *b, double *residual, int *status) {
     if (!b || !residual) return b ? bfail(b, MDF_E_INVALID, "residual is NULL") : MDF_E_INVALID;
+    MdfRange rr("mdf_batch_residual");
     for (int i = 0; i < b->count; ++i) {
         if (!b->active[i]) continue;
         mdf_ctx *c = b->ctx[i];

@@ -3,9 +3,19 @@
 // (mdf_batch.cu).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mdf.h"
 #include "mdf_aux.cuh"
 #include "mdf_internal.cuh"
+
+// NVTX range around a host call (a no-op unless a profiler is attached).
+struct MdfRange {
+    explicit MdfRange(const char *name) { nvtxRangePushA(name); }
+    ~MdfRange() { nvtxRangePop(); }
+    MdfRange(const MdfRange &) = delete;
+    MdfRange &operator=(const MdfRange &) = delete;
+};
 
 struct mdf_ctx {
     // the members are documented where they are set (mdf_create)

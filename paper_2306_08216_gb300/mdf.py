@@ -91,6 +91,7 @@ _SIGNATURES = [
     ("mdf_launch_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     ("mdf_set_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     ("mdf_launch_kind", ctypes.c_int, [ctypes.c_void_p]),
+    ("mdf_debug_poison", ctypes.c_int, [ctypes.c_void_p]),
     ("mdf_bytes_per_node", ctypes.c_double, [ctypes.c_void_p]),
     ("mdf_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Grid), ctypes.POINTER(Fluid),
                                         ctypes.POINTER(BC), ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]),
@@ -406,6 +407,10 @@ class Solver:
 
     def bytes_per_node(self):
         return lib().mdf_bytes_per_node(self._h)
+
+    def debug_poison(self):
+        """NaN into the storage no valid result may read (see mdf_debug_poison)."""
+        _check(lib().mdf_debug_poison(self._h), self._h)
 
 
 def create_status(grid, fluid, bc, params=None):

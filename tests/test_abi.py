@@ -138,6 +138,7 @@ def test_launch_kind_calls_reject_null(lib):
     assert lib.mdf_batch_launch_kind(None) == -1
     assert lib.mdf_batch_set_launch(None, 1) == mdf.MDF_E_INVALID
     assert lib.mdf_set_launch(None, 0, 0) == mdf.MDF_E_INVALID
+    assert lib.mdf_debug_poison(None) == mdf.MDF_E_INVALID
 
 
 def test_rho0_calls_reject_null_contexts(lib):
