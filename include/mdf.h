@@ -139,6 +139,12 @@ typedef struct {
 mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc *bc,
                       const mdf_params *params, mdf_ctx **out);
 
+/* Fault injection (host side, for tests of the error paths): with the
+ * environment variable MDF_FAIL_ALLOC=k, the k-th device or pinned-host
+ * allocation made while mdf_create (or mdf_batch_create, per problem) builds
+ * a context fails as out of memory: the call returns MDF_E_NOMEM and frees
+ * what it had allocated.  Read at every creation; unset or 0 disables it. */
+
 /* Release every resource of the context (waits for its stream first). */
 void mdf_destroy(mdf_ctx *ctx);
 

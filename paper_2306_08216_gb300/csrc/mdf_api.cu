@@ -42,6 +42,27 @@ static mdf_status fail(mdf_ctx *c, mdf_status st, const char *fmt, ...) {
 
 static bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
 
+// Host-side fault injection for the creation path: with MDF_FAIL_ALLOC=k in
+// the environment, the k-th device (or pinned host) allocation made while a
+// context is created fails as if memory had run out, so that every error
+// path of mdf_create can be exercised without touching the GPU's state.
+// The count restarts with every mdf_create; 0 or unset disables it (a debug
+// aid: the counter is shared by all threads).
+static int g_fail_alloc = 0;
+
+static cudaError_t dev_malloc(void **p, size_t bytes) {
+    if (g_fail_alloc > 0 && --g_fail_alloc == 0) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+template <typename T>
+static cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+static cudaError_t host_malloc(void **p, size_t bytes) {
+    if (g_fail_alloc > 0 && --g_fail_alloc == 0) return cudaErrorMemoryAllocation;
+    return cudaMallocHost(p, bytes);
+}
+
 static void free_ctx(mdf_ctx *c) {
     if (!c) return;
     float *fp[] = {c->buf[0], c->buf[1], c->kxv, c->kyv, c->mxx, c->mxy, c->mex, c->mey, c->Fxp, c->Fyp,
@@ -109,7 +130,7 @@ static mdf_status ensure_scratch(mdf_ctx *c, size_t bytes) {
     if (c->scratch) cudaFree(c->scratch);
     c->scratch = nullptr;
     c->scratch_bytes = 0;
-    CK(c, cudaMalloc(&c->scratch, bytes));
+    CK(c, dev_malloc(&c->scratch, bytes));
     c->scratch_bytes = bytes;
     return MDF_OK;
 }
@@ -211,7 +232,9 @@ namespace mdf {
 // launch plan: the single-problem autotuner is skipped.
 mdf_status ctx_create_untuned(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc *bc,
                               const mdf_params *params, mdf_ctx **out) {
-    return create_ctx(grid, fluid, bc, params, 0, out);
+    const mdf_status s = create_ctx(grid, fluid, bc, params, 0, out);
+    g_fail_alloc = 0;
+    return s;
 }
 }  // namespace mdf
 
@@ -220,7 +243,9 @@ extern "C" {
 mdf_status mdf_create(const mdf_grid *grid, const mdf_fluid *fluid, const mdf_bc *bc, const mdf_params *params,
                       mdf_ctx **out) {
     MdfRange r("mdf_create");
-    return create_ctx(grid, fluid, bc, params, 1, out);
+    const mdf_status s = create_ctx(grid, fluid, bc, params, 1, out);
+    g_fail_alloc = 0;
+    return s;
 }
 
 }  // extern "C"
@@ -267,6 +292,10 @@ static mdf_status create_ctx(const mdf_grid *grid, const mdf_fluid *fluid, const
         return fail(nullptr, MDF_E_INVALID, "the alpha = 0 distribution needs FP32 storage");
     prm.rho0 = prm.rho0 ? 1 : 0;
 
+    {
+        const char *fa = getenv("MDF_FAIL_ALLOC");
+        g_fail_alloc = fa ? atoi(fa) : 0;
+    }
     mdf_ctx *c = new mdf_ctx();
     c->nx = grid->nx;
     c->ny = grid->ny;
@@ -310,16 +339,16 @@ static mdf_status create_ctx(const mdf_grid *grid, const mdf_fluid *fluid, const
     c->plane = (long long)c->pitch * c->ny;
     const size_t state_bytes = state_buffer_bytes(prm.storage, c->plane, prm.rho0);
     for (int b = 0; b < 2; ++b) {
-        CKE(cudaMalloc(&c->buf[b], state_bytes));
+        CKE(dev_malloc(&c->buf[b], state_bytes));
         CKE(cudaMemset(c->buf[b], 0, state_bytes));
     }
     const size_t N = (size_t)c->nx * c->ny;
-    CKE(cudaMalloc(&c->snap_u, N * sizeof(float)));
-    CKE(cudaMalloc(&c->snap_v, N * sizeof(float)));
-    CKE(cudaMalloc(&c->err, sizeof(int)));
+    CKE(dev_malloc(&c->snap_u, N * sizeof(float)));
+    CKE(dev_malloc(&c->snap_v, N * sizeof(float)));
+    CKE(dev_malloc(&c->err, sizeof(int)));
     CKE(cudaMemset(c->err, 0, sizeof(int)));
-    CKE(cudaMalloc(&c->result, 8 * sizeof(double)));
-    CKE(cudaMallocHost(&c->h_result, 8 * sizeof(double)));
+    CKE(dev_malloc(&c->result, 8 * sizeof(double)));
+    CKE(host_malloc(reinterpret_cast<void **>(&c->h_result), 8 * sizeof(double)));
 
     AuxArgs &x = c->aux;
     x.nx = c->nx; x.ny = c->ny; x.pitch = c->pitch; x.plane = c->plane;
@@ -333,7 +362,7 @@ static mdf_status create_ctx(const mdf_grid *grid, const mdf_fluid *fluid, const
     x.rho0 = prm.rho0;
     x.nscale = (float)ldexp(1.0, NSCALE_EXP - ilogb(prm.c));
     x.ninv = (float)ldexp(1.0, ilogb(prm.c) - NSCALE_EXP);
-    CKE(cudaMalloc(&c->partials, (size_t)aux_residual_blocks(x) * 5 * sizeof(double)));
+    CKE(dev_malloc(&c->partials, (size_t)aux_residual_blocks(x) * 5 * sizeof(double)));
 
     // Grid metrics (FP64 on the GPU) and the time step of Eq. 3.1.
     if (grid->kind == MDF_GRID_UNIFORM) {
@@ -345,11 +374,11 @@ static mdf_status create_ctx(const mdf_grid *grid, const mdf_fluid *fluid, const
     } else {
         const size_t ncoord = grid->kind == MDF_GRID_SEPARABLE ? (size_t)(c->nx + c->ny) : 2 * N;
         double *dcoord = nullptr, *dedge = nullptr;
-        CKE(cudaMalloc(&dcoord, ncoord * sizeof(double)));
+        CKE(dev_malloc(&dcoord, ncoord * sizeof(double)));
         const size_t nedge = grid->kind == MDF_GRID_SEPARABLE ? (size_t)(c->nx + c->ny) : N;
         mdf_status st = MDF_OK;
         do {
-            cudaError_t e = cudaMalloc(&dedge, nedge * sizeof(double));
+            cudaError_t e = dev_malloc(&dedge, nedge * sizeof(double));
             if (e != cudaSuccess) { st = fail(c, MDF_E_NOMEM, "metric scratch"); break; }
             double *hedge = (double *)malloc(nedge * sizeof(double));
             if (!hedge) { st = fail(c, MDF_E_NOMEM, "host metric scratch"); break; }
@@ -357,18 +386,18 @@ static mdf_status create_ctx(const mdf_grid *grid, const mdf_fluid *fluid, const
                 e = cudaMemcpy(dcoord, grid->x, c->nx * sizeof(double), cudaMemcpyHostToDevice);
                 if (e == cudaSuccess)
                     e = cudaMemcpy(dcoord + c->nx, grid->y, c->ny * sizeof(double), cudaMemcpyHostToDevice);
-                if (e == cudaSuccess) e = cudaMalloc(&c->kxv, c->pitch * sizeof(float));
-                if (e == cudaSuccess) e = cudaMalloc(&c->kyv, c->ny * sizeof(float));
+                if (e == cudaSuccess) e = dev_malloc(&c->kxv, c->pitch * sizeof(float));
+                if (e == cudaSuccess) e = dev_malloc(&c->kyv, c->ny * sizeof(float));
                 if (e == cudaSuccess)
                     e = aux_metrics1d(x, dcoord, dcoord + c->nx, prm.c, c->kxv, c->kyv, dedge, 0);
             } else {
                 e = cudaMemcpy(dcoord, grid->x, N * sizeof(double), cudaMemcpyHostToDevice);
                 if (e == cudaSuccess) e = cudaMemcpy(dcoord + N, grid->y, N * sizeof(double), cudaMemcpyHostToDevice);
                 const size_t mp = (size_t)c->pitch * c->ny * sizeof(float);
-                if (e == cudaSuccess) e = cudaMalloc(&c->mxx, mp);
-                if (e == cudaSuccess) e = cudaMalloc(&c->mxy, mp);
-                if (e == cudaSuccess) e = cudaMalloc(&c->mex, mp);
-                if (e == cudaSuccess) e = cudaMalloc(&c->mey, mp);
+                if (e == cudaSuccess) e = dev_malloc(&c->mxx, mp);
+                if (e == cudaSuccess) e = dev_malloc(&c->mxy, mp);
+                if (e == cudaSuccess) e = dev_malloc(&c->mex, mp);
+                if (e == cudaSuccess) e = dev_malloc(&c->mey, mp);
                 if (e == cudaSuccess)
                     e = aux_metrics2d(x, dcoord, dcoord + N, prm.c, c->mxx, c->mxy, c->mex, c->mey, dedge, 0);
             }
@@ -376,7 +405,8 @@ static mdf_status create_ctx(const mdf_grid *grid, const mdf_fluid *fluid, const
             if (e == cudaSuccess) e = cudaMemcpy(hedge, dedge, nedge * sizeof(double), cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) {
                 free(hedge);
-                st = fail(c, MDF_E_CUDA, "metric setup: %s", cudaGetErrorString(e));
+                st = fail(c, e == cudaErrorMemoryAllocation ? MDF_E_NOMEM : MDF_E_CUDA, "metric setup: %s",
+                          cudaGetErrorString(e));
                 break;
             }
             double m = INFINITY;
