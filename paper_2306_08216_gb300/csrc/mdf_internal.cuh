@@ -155,11 +155,13 @@ cudaError_t rho0_launch(const CUtensorMap *tmap, const StepArgs &args, int metri
                         cudaStream_t stream);
 
 // One block per 2-D tile of output nodes, three phases per step, for grids
-// too small for marching bands (mdf_step_tile.cu, mdf_step_tile16.cu); every
-// storage mode, without the alpha = 0 distribution.  It is also the only
-// kernel for 16-bit storage outside the periodic fast path.
+// too small for marching bands (mdf_step_tile.cu, mdf_step_tile16.cu,
+// mdf_step_tile_rho0.cu); every storage mode, and the alpha = 0
+// distribution with FP32 storage.  It is also the only kernel for 16-bit
+// storage outside the periodic fast path.
 bool tile_path_applies(int storage, int rho0);
-cudaError_t tile_occupancy(int metric, int power_law, int walls, int storage, int *tx, int *ty, int *occ, int *smem);
+cudaError_t tile_occupancy(int metric, int power_law, int walls, int storage, int rho0, int *tx, int *ty, int *occ,
+                           int *smem);
 cudaError_t tile_launch(const StepArgs &args, int metric, const StepPlan &plan, cudaStream_t stream);
 // The same kernel over the work items (problem, tile x, tile y) of a batch.
 cudaError_t tile_batch_occupancy(int metric, int power_law, int walls, int storage, int *occ, int *smem);

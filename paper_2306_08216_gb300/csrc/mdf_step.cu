@@ -94,7 +94,7 @@ int step_candidates(int metric, int power_law, int walls, int storage, int rho0,
     // the tile kernel, last: the marches stay the default
     if (tile_path_applies(storage, rho0) && n < max) {
         int tx = 0, ty = 0, occ = 0, smem = 0;
-        const cudaError_t e = tile_occupancy(metric, power_law, walls, storage, &tx, &ty, &occ, &smem);
+        const cudaError_t e = tile_occupancy(metric, power_law, walls, storage, rho0, &tx, &ty, &occ, &smem);
         if (e != cudaSuccess) {
             *err = e;
             return n;

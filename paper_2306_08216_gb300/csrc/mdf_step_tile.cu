@@ -6,15 +6,14 @@ namespace mdf {
 
 MDF_TILE_DEFINE(STORAGE_FP32)
 
-// Every storage mode; the alpha = 0 distribution has no tile form.
-bool tile_path_applies(int storage, int rho0) {
-    (void)storage;
-    return !rho0;
-}
+// Every storage mode; the alpha = 0 distribution with FP32 storage.
+bool tile_path_applies(int storage, int rho0) { return !rho0 || storage == STORAGE_FP32; }
 
-cudaError_t tile_occupancy(int metric, int power_law, int walls, int storage, int *tx, int *ty, int *occ, int *smem) {
+cudaError_t tile_occupancy(int metric, int power_law, int walls, int storage, int rho0, int *tx, int *ty, int *occ,
+                           int *smem) {
     *tx = kTX;
     *ty = kTY;
+    if (rho0) return tile_occupancy_rho0(metric, power_law, walls, occ, smem);
     switch (storage) {
         case STORAGE_FP16: return tile_occupancy_st<STORAGE_FP16>(metric, power_law, walls, occ, smem);
         case STORAGE_BF16: return tile_occupancy_st<STORAGE_BF16>(metric, power_law, walls, occ, smem);
@@ -23,6 +22,7 @@ cudaError_t tile_occupancy(int metric, int power_law, int walls, int storage, in
 }
 
 cudaError_t tile_launch(const StepArgs &args, int metric, const StepPlan &plan, cudaStream_t stream) {
+    if (args.rho0) return tile_launch_rho0(args, metric, plan, stream);
     switch (args.storage) {
         case STORAGE_FP16: return tile_launch_st<STORAGE_FP16>(args, metric, plan, stream);
         case STORAGE_BF16: return tile_launch_st<STORAGE_BF16>(args, metric, plan, stream);

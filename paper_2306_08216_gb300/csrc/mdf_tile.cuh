@@ -61,6 +61,8 @@ struct Tile {
     static constexpr int B_BYTES = 5 * N8 * 8;
     static constexpr int F_BYTES = 5 * N4 * 8;
     static constexpr int K_BYTES = 2 * N4 * 4;
+    static constexpr int B0_BYTES = 5 * N8 * 4;  // the alpha = 0 lane: fbar^+ and f as floats
+    static constexpr int F0_BYTES = 5 * N4 * 4;
 };
 
 // Difference weights of one axis (as the marches): w = -step k (a1, a0, am2).
@@ -129,20 +131,72 @@ __device__ __forceinline__ void stream_tile(const unsigned char *A, int n, int S
     }
 }
 
-template <int TX, int TY, int MK, bool WALLS, int ST>
+// The same two helpers on the scalar alpha = 0 lane (arrays of floats).
+template <int NN>
+__device__ __forceinline__ float curvi_tile0(const float *A, int j, int n, int S, float cxi, float ceta, bool xadj_p,
+                                             bool xadj_m, bool yadj_p, bool yadj_m, float step, const StepArgs &a,
+                                             float acc) {
+    auto at = [&](int m) { return A[j * NN + m]; };
+    const float p0 = at(n);
+    if (cxi != 0.0f) {
+        const float k = -step * fabsf(cxi);
+        const float w1 = k * a.a1, w0 = k * a.a0, w2 = k * a.am2;
+        if (cxi > 0.0f) acc = stream1<true>(acc, at(n + 1), p0, at(n - 1), at(n - 2), xadj_p, w1, w0, w2);
+        else acc = stream1<true>(acc, at(n - 1), p0, at(n + 1), at(n + 2), xadj_m, w1, w0, w2);
+    }
+    if (ceta != 0.0f) {
+        const float k = -step * fabsf(ceta);
+        const float w1 = k * a.a1, w0 = k * a.a0, w2 = k * a.am2;
+        if (ceta > 0.0f) acc = stream1<true>(acc, at(n + S), p0, at(n - S), at(n - 2 * S), yadj_p, w1, w0, w2);
+        else acc = stream1<true>(acc, at(n - S), p0, at(n + S), at(n + 2 * S), yadj_m, w1, w0, w2);
+    }
+    return acc;
+}
+
+template <int NN, int MK, bool WALLS>
+__device__ __forceinline__ void stream_tile0(const float *A, int n, int S, float step, int Xw, int Yw, bool xadj_p,
+                                             bool xadj_m, bool yadj_p, bool yadj_m, const StepArgs &a,
+                                             float out[5]) {
+    auto at = [&](int j, int m) { return A[j * NN + m]; };
+    if (MK != METRIC_CURVILINEAR) {
+        float kx = a.kx, ky = a.ky;
+        if (MK == METRIC_SEPARABLE) {
+            kx = a.kxv[GHOST + Xw];
+            ky = a.kyv[Yw];
+        }
+        const float x1 = -step * kx * a.a1, x0 = -step * kx * a.a0, x2 = -step * kx * a.am2;
+        const float y1 = -step * ky * a.a1, y0 = -step * ky * a.a0, y2 = -step * ky * a.am2;
+        out[1] = stream1<WALLS>(out[1], at(1, n + 1), at(1, n), at(1, n - 1), at(1, n - 2), xadj_p, x1, x0, x2);
+        out[3] = stream1<WALLS>(out[3], at(3, n - 1), at(3, n), at(3, n + 1), at(3, n + 2), xadj_m, x1, x0, x2);
+        out[2] = stream1<WALLS>(out[2], at(2, n + S), at(2, n), at(2, n - S), at(2, n - 2 * S), yadj_p, y1, y0, y2);
+        out[4] = stream1<WALLS>(out[4], at(4, n - S), at(4, n), at(4, n + S), at(4, n + 2 * S), yadj_m, y1, y0, y2);
+    } else {
+        const long long mi = (long long)Yw * a.pitch + GHOST + Xw;
+        const float cxx = a.mxx[mi], cxy = a.mxy[mi], cex = a.mex[mi], cey = a.mey[mi];
+        out[1] = curvi_tile0<NN>(A, 1, n, S, cxx, cex, xadj_p, xadj_m, yadj_p, yadj_m, step, a, out[1]);
+        out[2] = curvi_tile0<NN>(A, 2, n, S, cxy, cey, xadj_p, xadj_m, yadj_p, yadj_m, step, a, out[2]);
+        out[3] = curvi_tile0<NN>(A, 3, n, S, -cxx, -cex, xadj_p, xadj_m, yadj_p, yadj_m, step, a, out[3]);
+        out[4] = curvi_tile0<NN>(A, 4, n, S, -cxy, -cey, xadj_p, xadj_m, yadj_p, yadj_m, step, a, out[4]);
+    }
+}
+
+template <int TX, int TY, int MK, bool WALLS, int ST, bool RHO0>
 __device__ __forceinline__ void tile_output(const StepArgs &a, int X, int Y, int li, int lj, const unsigned char *Fs,
-                                            const F2 hp[5]);
+                                            const float *Fs0, const F2 hp[5], const float hp0[5]);
 
 // One tile (bx, by) of one problem.  Every thread reaches every barrier
 // (no early exit), so a block may step several tiles in a row: the barrier
 // after phase A of the next tile orders its shared-memory writes after the
 // reads of the previous tile.
-template <int TX, int TY, int MK, bool PL, bool WALLS, int ST>
+template <int TX, int TY, int MK, bool PL, bool WALLS, int ST, bool RHO0>
 __device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, unsigned char *smem) {
     using T = Tile<TX, TY>;
     unsigned char *Bs = smem;                          // fbar^+ [5][N8] pairs
     unsigned char *Fs = smem + T::B_BYTES;             // f(t+h) [5][N4] pairs
     float *Ks = reinterpret_cast<float *>(Fs + T::F_BYTES);  // power law: rkp [N4], rk [N4]
+    // the alpha = 0 lane (planes 10..14): fbar^+ [5][N8] and f [5][N4] floats
+    float *Bs0 = Ks + (PL ? 2 * T::N4 : 0);
+    float *Fs0 = Bs0 + (RHO0 ? 5 * T::N8 : 0);
 
     const int t = threadIdx.x;
     const int x0 = bx * TX, y0 = by * TY;
@@ -179,7 +233,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, uns
     };
     // the planes of a node: 10 FP32 distributions, or u, v, P and four
     // 16-bit pair words (as 32-bit patterns)
-    constexpr int NW = ST == STORAGE_FP32 ? NPLANES : DEV_PLANES;
+    constexpr int NW = ST == STORAGE_FP32 ? (RHO0 ? RHO0_PLANES : NPLANES) : DEV_PLANES;
     float raw[PASSES][NW];
 #pragma unroll
     for (int q = 0; q < PASSES; ++q) {
@@ -199,7 +253,8 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, uns
             }
         }
     }
-    F2 hp[5];  // fhat^+ of the thread's own node
+    F2 hp[5];      // fhat^+ of the thread's own node
+    float hp0[5];  // ... and of its alpha = 0 populations
 #pragma unroll
     for (int q = 0; q < PASSES; ++q) {
         const int i = t + q * T::NT;
@@ -211,12 +266,15 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, uns
         const bool oky = ywall ? (Y >= 0 && Y < a.ny) : true;
         const int Xw = axis_index(X, a.nx, xwall), Yw = axis_index(Y, a.ny, ywall);
         F2 g[5], n[5];
+        float uq = 0.0f, vq = 0.0f;  // velocity of the node (the alpha = 0 lane's equilibrium)
         if (ST == STORAGE_FP32) {
 #pragma unroll
             for (int j = 0; j < 5; ++j) g[j] = mk2(raw[q][j], raw[q][5 + j]);
             const Mom2 m =
                 (a.r_mode && okx && oky) ? moments2r(g, c, a.rk_hat * source_at(a, Yw, Xw)) : moments2(g, c);
             noneq2(g, m, inv2c, n);
+            uq = m.u;
+            vq = m.v;
         } else {
             // fhat = feq(u, v, P) + n straight from the stored fields (no source
             // term in the 16-bit modes)
@@ -228,6 +286,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, uns
         }
         const F2 n13 = n[1] - n[3], n24 = n[2] - n[4];
         F2 mKp_ = mKp, Dp_ = Dp, mKb_ = mKb, Db_ = Db;
+        float rpp = a.rpp, rp = a.rp, rbp = a.rbp, rb = a.rb;
         if (PL) {
             float gx1, gx2, gy1, gy2;
             split2(splat(c) * n13, gx1, gx2);
@@ -239,6 +298,10 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, uns
             Dp_ = splat(0.5f * (Rr.rp - Rr.rpp));
             mKb_ = splat(-(1.0f - Rr.rbp));
             Db_ = splat(0.5f * (Rr.rb - Rr.rbp));
+            rpp = Rr.rpp;
+            rp = Rr.rp;
+            rbp = Rr.rbp;
+            rb = Rr.rb;
             if (lx >= 2 && lx < T::X8 - 2 && ly >= 2 && ly < T::Y8 - 2) {
                 const int n4 = (ly - 2) * T::X4 + (lx - 2);
                 Ks[n4] = Rr.rkp;
@@ -251,6 +314,17 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, uns
         const int n8 = ly * T::X8 + lx;
 #pragma unroll
         for (int j = 0; j < 5; ++j) sts2(Bs, (j * T::N8 + n8) * 8, o[j]);
+        if (RHO0) {
+            // Step 1 on alpha = 0 with the node's u, v and the same rates
+            float g0[5], n0[5], o0[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) g0[j] = raw[q][NPLANES + j];
+            noneq0(g0, uq, vq, inv2c, n0);
+            if (q == 0) relax0(g0, n0, -(1.0f - rpp), 0.5f * (rp - rpp), hp0);
+            relax0(g0, n0, -(1.0f - rbp), 0.5f * (rb - rbp), o0);
+#pragma unroll
+            for (int j = 0; j < 5; ++j) Bs0[j * T::N8 + n8] = o0[j];
+        }
     }
     __syncthreads();
 
@@ -266,6 +340,9 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, uns
             if (skip) {  // beyond or on a wall: NEE below (the values beyond are never read)
 #pragma unroll
                 for (int j = 0; j < 5; ++j) sts2(Fs, (j * T::N4 + i4) * 8, splat(0.0f));
+                if (RHO0)
+#pragma unroll
+                    for (int j = 0; j < 5; ++j) Fs0[j * T::N4 + i4] = 0.0f;
                 continue;
             }
         }
@@ -297,6 +374,24 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, uns
         relax2(fb, n, n[1] - n[3], n[2] - n[4], mKk_, Dk_, f);
 #pragma unroll
         for (int j = 0; j < 5; ++j) sts2(Fs, (j * T::N4 + i4) * 8, f[j]);
+        if (RHO0) {
+            // Steps 2-3 on alpha = 0: source h w_j R, recovery with the u, v of
+            // the alpha = 1, 2 fbar and the same rates
+            const float sR = a.r_mode ? a.h * 0.2f * source_at(a, Yw, Xw) : 0.0f;
+            float fb0[5], n0[5], f0[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) fb0[j] = Bs0[j * T::N8 + n8] + sR;
+            stream_tile0<T::N8, MK, WALLS>(Bs0, n8, T::X8, a.h, Xw, Yw, xadj_p, xadj_m, yadj_p, yadj_m, a, fb0);
+            float kp = a.rkp, kk = a.rk;
+            if (PL) {
+                kp = Ks[i4];
+                kk = Ks[T::N4 + i4];
+            }
+            noneq0(fb0, m.u, m.v, inv2c, n0);
+            relax0(fb0, n0, -(1.0f - kp), 0.5f * (kk - kp), f0);
+#pragma unroll
+            for (int j = 0; j < 5; ++j) Fs0[j * T::N4 + i4] = f0[j];
+        }
     }
     __syncthreads();
     if (WALLS) {
@@ -320,6 +415,15 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, uns
             nee2(g, a.uw[side], a.vw[side], inv2c, w);
 #pragma unroll
             for (int j = 0; j < 5; ++j) sts2(Fs, (j * T::N4 + i4) * 8, w[j]);
+            if (RHO0) {  // the wall's rho_0 is the neighbour's
+                float un, vn, g0[5], w0[5];
+                split2((g[0] + g[1]) + (g[2] + g[3]) + g[4], un, vn);
+#pragma unroll
+                for (int j = 0; j < 5; ++j) g0[j] = Fs0[j * T::N4 + nb];
+                nee0(g0, a.uw[side], a.vw[side], un, vn, inv2c, w0);
+#pragma unroll
+                for (int j = 0; j < 5; ++j) Fs0[j * T::N4 + i4] = w0[j];
+            }
         }
         __syncthreads();
     }
@@ -329,7 +433,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, uns
     const int X = x0 + li, Y = y0 + lj;
     if (X >= a.nx || Y >= a.ny) return;
     if (WALLS && ((xwall && (X == 0 || X == a.nx - 1)) || (ywall && (Y == 0 || Y == a.ny - 1)))) return;
-    tile_output<TX, TY, MK, WALLS, ST>(a, X, Y, li, lj, Fs, hp);
+    tile_output<TX, TY, MK, WALLS, ST, RHO0>(a, X, Y, li, lj, Fs, Fs0, hp, hp0);
 }
 
 // Phase C of the own node (X, Y): pass 2 from the f region, the output and
@@ -342,9 +446,15 @@ __device__ __forceinline__ void tile_store(const StepArgs &a, int row, int X, co
     else store_node_dev<ST, XPER>(a, row, X, v);
 }
 
-template <int TX, int TY, int MK, bool WALLS, int ST>
+// Store the alpha = 0 populations of one node (planes 10..14).
+template <bool RHO0, bool XPER>
+__device__ __forceinline__ void tile_store0(const StepArgs &a, int row, int X, const float v[5]) {
+    if (RHO0) store_node0<XPER>(a, row, X, v);
+}
+
+template <int TX, int TY, int MK, bool WALLS, int ST, bool RHO0>
 __device__ __forceinline__ void tile_output(const StepArgs &a, int X, int Y, int li, int lj, const unsigned char *Fs,
-                                            const F2 hp[5]) {
+                                            const float *Fs0, const F2 hp[5], const float hp0[5]) {
     using T = Tile<TX, TY>;
     const bool xwall = WALLS && a.xwall, ywall = WALLS && a.ywall;
     const float inv2c = a.inv2c;
@@ -362,30 +472,54 @@ __device__ __forceinline__ void tile_output(const StepArgs &a, int X, int Y, int
 #pragma unroll
     for (int j = 0; j < 5; ++j) out[j] = hp[j] + fF;
     stream_tile<T::N4, MK, WALLS>(Fs, n4, T::X4, a.dt, X, Y, xadj_p, xadj_m, yadj_p, yadj_m, a, out);
+    float out0[5], un = 0.0f, vn = 0.0f;
+    if (RHO0) {
+        // Step 4 on alpha = 0: fhat^+ - dt c.grad f + dt w_j R
+        const float sR = a.r_mode ? a.dt * 0.2f * source_at(a, Y, X) : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) out0[j] = hp0[j] + sR;
+        stream_tile0<T::N4, MK, WALLS>(Fs0, n4, T::X4, a.dt, X, Y, xadj_p, xadj_m, yadj_p, yadj_m, a, out0);
+        split2((out[0] + out[1]) + (out[2] + out[3]) + out[4], un, vn);
+    }
     if (!WALLS) {
         tile_store<ST, true>(a, Y, X, out);
+        tile_store0<RHO0, true>(a, Y, X, out0);
         return;
     }
-    if (xwall) tile_store<ST, false>(a, Y, X, out);
-    else tile_store<ST, true>(a, Y, X, out);
+    if (xwall) {
+        tile_store<ST, false>(a, Y, X, out);
+        tile_store0<RHO0, false>(a, Y, X, out0);
+    } else {
+        tile_store<ST, true>(a, Y, X, out);
+        tile_store0<RHO0, true>(a, Y, X, out0);
+    }
     F2 w[5];
-    if (xadj_p) { nee2(out, a.uw[0], a.vw[0], inv2c, w); tile_store<ST, false>(a, Y, 0, w); }
-    if (xadj_m) { nee2(out, a.uw[1], a.vw[1], inv2c, w); tile_store<ST, false>(a, Y, a.nx - 1, w); }
+    float w0[5];
+    auto wall = [&](int side, int row, int col, bool xper) {
+        nee2(out, a.uw[side], a.vw[side], inv2c, w);
+        if (RHO0) nee0(out0, a.uw[side], a.vw[side], un, vn, inv2c, w0);
+        if (xper) {
+            tile_store<ST, true>(a, row, col, w);
+            tile_store0<RHO0, true>(a, row, col, w0);
+        } else {
+            tile_store<ST, false>(a, row, col, w);
+            tile_store0<RHO0, false>(a, row, col, w0);
+        }
+    };
+    if (xadj_p) wall(0, Y, 0, false);
+    if (xadj_m) wall(1, Y, a.nx - 1, false);
     if (ywall && (Y == 1 || Y == a.ny - 2)) {
         const int rr = (Y == 1) ? 0 : a.ny - 1;
-        const int side = (Y == 1) ? 2 : 3;
-        nee2(out, a.uw[side], a.vw[side], inv2c, w);
-        if (xwall) tile_store<ST, false>(a, rr, X, w);
-        else tile_store<ST, true>(a, rr, X, w);
-        if (xadj_p) { nee2(out, a.uw[0], a.vw[0], inv2c, w); tile_store<ST, false>(a, rr, 0, w); }
-        if (xadj_m) { nee2(out, a.uw[1], a.vw[1], inv2c, w); tile_store<ST, false>(a, rr, a.nx - 1, w); }
+        wall((Y == 1) ? 2 : 3, rr, X, !xwall);
+        if (xadj_p) wall(0, rr, 0, false);
+        if (xadj_m) wall(1, rr, a.nx - 1, false);
     }
 }
 
-template <int TX, int TY, int MK, bool PL, bool WALLS, int ST>
+template <int TX, int TY, int MK, bool PL, bool WALLS, int ST, bool RHO0>
 __global__ void __launch_bounds__(TX *TY, kTileMinBlocks) tile_kernel(const StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    tile_step<TX, TY, MK, PL, WALLS, ST>(a, blockIdx.x, blockIdx.y, smem);
+    tile_step<TX, TY, MK, PL, WALLS, ST, RHO0>(a, blockIdx.x, blockIdx.y, smem);
 }
 
 // Many problems in one persistent launch: block b steps work items
@@ -396,37 +530,38 @@ __global__ void __launch_bounds__(TX *TY, kTileMinBlocks) tile_batch_kernel(cons
     extern __shared__ __align__(128) unsigned char smem[];
     for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
         const BatchItem item = items[w];
-        tile_step<TX, TY, MK, PL, WALLS, ST>(args[item.problem], item.bx, item.by, smem);
+        tile_step<TX, TY, MK, PL, WALLS, ST, false>(args[item.problem], item.bx, item.by, smem);
     }
 }
 
 constexpr int kTX = TILE_X, kTY = TILE_Y;
 
-template <int MK, bool PL, bool WALLS>
+template <int MK, bool PL, bool WALLS, bool RHO0 = false>
 constexpr int tile_smem() {
     using T = Tile<kTX, kTY>;
-    return T::B_BYTES + T::F_BYTES + (PL ? T::K_BYTES : 0);
+    return T::B_BYTES + T::F_BYTES + (PL ? T::K_BYTES : 0) + (RHO0 ? T::B0_BYTES + T::F0_BYTES : 0);
 }
 
-template <int MK, bool PL, bool WALLS, int ST>
+template <int MK, bool PL, bool WALLS, int ST, bool RHO0 = false>
 cudaError_t tile_occupancy_t(int *occ, int *smem) {
-    auto k = tile_kernel<kTX, kTY, MK, PL, WALLS, ST>;
-    *smem = tile_smem<MK, PL, WALLS>();
+    auto k = tile_kernel<kTX, kTY, MK, PL, WALLS, ST, RHO0>;
+    *smem = tile_smem<MK, PL, WALLS, RHO0>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, kTX * kTY, *smem);
 }
 
-template <int MK, bool PL, bool WALLS, int ST>
+template <int MK, bool PL, bool WALLS, int ST, bool RHO0 = false>
 cudaError_t tile_launch_t(const StepArgs &args, const StepPlan &plan, cudaStream_t stream) {
-    auto k = tile_kernel<kTX, kTY, MK, PL, WALLS, ST>;
+    auto k = tile_kernel<kTX, kTY, MK, PL, WALLS, ST, RHO0>;
+    constexpr int smem = tile_smem<MK, PL, WALLS, RHO0>();
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_smem<MK, PL, WALLS>());
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k<<<dim3(plan.gx, plan.gy), kTX * kTY, tile_smem<MK, PL, WALLS>(), stream>>>(args);
+    k<<<dim3(plan.gx, plan.gy), kTX * kTY, smem, stream>>>(args);
     return cudaGetLastError();
 }
 
@@ -470,7 +605,28 @@ cudaError_t tile_batch_launch_t(const BatchItem *items, int nitems, const StepAr
         default: return FN<METRIC_CURVILINEAR, true, true, ST>(__VA_ARGS__);       \
     }
 
+// FN with the alpha = 0 lane (FP32 storage).
+#define MDF_TILE_DISPATCH_RHO0(FN, ...)                                                    \
+    switch (metric * 4 + (power_law ? 2 : 0) + (walls ? 1 : 0)) {                          \
+        case 0: return FN<METRIC_UNIFORM, false, false, STORAGE_FP32, true>(__VA_ARGS__);     \
+        case 1: return FN<METRIC_UNIFORM, false, true, STORAGE_FP32, true>(__VA_ARGS__);      \
+        case 2: return FN<METRIC_UNIFORM, true, false, STORAGE_FP32, true>(__VA_ARGS__);      \
+        case 3: return FN<METRIC_UNIFORM, true, true, STORAGE_FP32, true>(__VA_ARGS__);       \
+        case 4: return FN<METRIC_SEPARABLE, false, false, STORAGE_FP32, true>(__VA_ARGS__);   \
+        case 5: return FN<METRIC_SEPARABLE, false, true, STORAGE_FP32, true>(__VA_ARGS__);    \
+        case 6: return FN<METRIC_SEPARABLE, true, false, STORAGE_FP32, true>(__VA_ARGS__);    \
+        case 7: return FN<METRIC_SEPARABLE, true, true, STORAGE_FP32, true>(__VA_ARGS__);     \
+        case 8: return FN<METRIC_CURVILINEAR, false, false, STORAGE_FP32, true>(__VA_ARGS__); \
+        case 9: return FN<METRIC_CURVILINEAR, false, true, STORAGE_FP32, true>(__VA_ARGS__);  \
+        case 10: return FN<METRIC_CURVILINEAR, true, false, STORAGE_FP32, true>(__VA_ARGS__); \
+        default: return FN<METRIC_CURVILINEAR, true, true, STORAGE_FP32, true>(__VA_ARGS__);  \
+    }
+
 }  // namespace
+
+// The tile kernel with the alpha = 0 lane (mdf_step_tile_rho0.cu).
+cudaError_t tile_occupancy_rho0(int metric, int power_law, int walls, int *occ, int *smem);
+cudaError_t tile_launch_rho0(const StepArgs &args, int metric, const StepPlan &plan, cudaStream_t stream);
 
 // The tile kernel's launch helpers for one storage mode ST (defined in
 // mdf_step_tile.cu for FP32 and mdf_step_tile16.cu for FP16 and BF16).

@@ -40,7 +40,7 @@ CASES = {
     "trapezoid": (37, 37, dict(nu=0.01, grid="curvilinear", x=TRAP[0], y=TRAP[1], **LID), [(128, 3), (0, 0)]),
     "trapezoid_power_law": (37, 37, dict(nu=0.004, grid="curvilinear", x=TRAP[0], y=TRAP[1], **LID, **PL),
                             [(128, 3), (0, 0)]),
-    "rho0_cavity": (45, 37, dict(nu=0.01, rho0=True, **LID), [(128, 3)]),
+    "rho0_cavity": (45, 37, dict(nu=0.01, rho0=True, **LID), [(128, 3), (0, 0)]),
 }
 
 
