@@ -42,6 +42,21 @@ inline size_t state_buffer_bytes(int storage, long long plane, int rho0 = 0) {
     return (size_t)state_planes(storage, rho0) * plane * 4;
 }
 
+// One-time per-kernel launch setup (the dynamic shared-memory attribute) is
+// a property of each device: a launcher keeps a bitmask of the devices
+// (0..63) it has set up and redoes the setup on a device it has not seen.
+// Two host threads may both set a kernel up; that is harmless.
+inline bool needs_device_setup(unsigned long long mask) {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d >= 64 || !((mask >> d) & 1ull);
+}
+inline void mark_device_setup(unsigned long long &mask) {
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d < 64) mask |= 1ull << d;
+}
+
 // Error codes the kernels raise in StepArgs::err (first one wins).
 enum DeviceError { DEVERR_NONE = 0, DEVERR_TMA_TIMEOUT = 1 };
 

@@ -704,11 +704,11 @@ template <int NT, int MK, bool PL, bool WALLS, bool RHO0>
 cudaError_t launch_t(const CUtensorMap *tmap, const StepArgs &args, const StepPlan &plan, cudaStream_t stream) {
     auto k = step_kernel<NT, MK, PL, WALLS, RHO0>;
     const int smem = smem_bytes<NT, MK, PL, WALLS, RHO0>();
-    static bool configured = false;
-    if (!configured) {
+    static unsigned long long configured = 0;  // devices set up
+    if (needs_device_setup(configured)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        mark_device_setup(configured);
     }
     k<<<dim3(plan.gx, plan.gy), NT, smem, stream>>>(*tmap, args);
     return cudaGetLastError();
@@ -728,11 +728,11 @@ cudaError_t batch_launch_t(const BatchItem *items, int nitems, const StepArgs *a
                            int grid, cudaStream_t stream) {
     auto k = batch_kernel<NT, MK, PL, WALLS, RHO0>;
     const int smem = smem_bytes<NT, MK, PL, WALLS, RHO0>();
-    static bool configured = false;
-    if (!configured) {
+    static unsigned long long configured = 0;  // devices set up
+    if (needs_device_setup(configured)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        mark_device_setup(configured);
     }
     k<<<grid, NT, smem, stream>>>(items, nitems, args, maps);
     return cudaGetLastError();

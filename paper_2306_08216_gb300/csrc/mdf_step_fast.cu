@@ -298,11 +298,11 @@ template <int NT, int MK, bool FORCED, int ST>
 cudaError_t fast_launch_t(const CUtensorMap *tmap, const StepArgs &args,
                           const StepPlan &plan, cudaStream_t stream) {
     auto k = fast_kernel<NT, MK, FORCED, ST>;
-    static bool configured = false;
-    if (!configured) {
+    static unsigned long long configured = 0;  // devices set up
+    if (needs_device_setup(configured)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem<NT, ST>());
         if (e != cudaSuccess) return e;
-        configured = true;
+        mark_device_setup(configured);
     }
     k<<<dim3(plan.gx, plan.gy), NT, fast_smem<NT, ST>(), stream>>>(*tmap, args);
     return cudaGetLastError();
