@@ -83,7 +83,11 @@ static void free_ctx(mdf_ctx *c) {
 
 static mdf_status encode_maps_box(mdf_ctx *c, int box_nt, CUtensorMap maps[2]);
 
-static mdf_status encode_maps(mdf_ctx *c) { return encode_maps_box(c, c->plan.NT, c->tmap); }
+// Row boxes of the marches for the current plan (a tile plan does not use
+// them, so any valid box will do).
+static mdf_status encode_maps(mdf_ctx *c) {
+    return encode_maps_box(c, c->plan.kind == PLAN_TILE ? 128 : c->plan.NT, c->tmap);
+}
 
 // Tensor maps of both state buffers for boxes of box_nt columns x 1 row x
 // all planes (32-bit elements; the 16-bit pair words move as opaque 32-bit
