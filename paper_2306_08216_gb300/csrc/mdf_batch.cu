@@ -24,7 +24,6 @@
 using namespace mdf;
 
 namespace {
-constexpr int kBatchNT = 128;     // block size of the general march
 constexpr int kBandRows = 128;    // longest band (rows per work item)
 constexpr int kGraphSteps = 16;   // launches per captured graph (even: parity returns)
 }  // namespace
@@ -36,6 +35,7 @@ struct mdf_batch {
     StepArgs *d_args[2] = {nullptr, nullptr};      // per parity: fout = the other buffer
     CUtensorMap *d_maps[2] = {nullptr, nullptr};   // per parity: maps of the input buffer
     BatchItem *d_items = nullptr;
+    int nt = 0;                                    // block size of the march kernel (strips of nt - 8 columns)
     int nitems = 0, grid = 0, occ = 0, smem = 0;
     int tile = 0, occ_tile = 0, smem_tile = 0;     // tile mode: one work item per 16 x 16 tile
     int storage = 0;                               // StorageKind of every problem (16-bit: tile mode only)
@@ -98,7 +98,7 @@ static mdf_status upload_args(mdf_batch *b) {
         for (int i = 0; i < b->count; ++i) {
             mdf_ctx *c = b->ctx[i];
             StepArgs a = c->args;
-            a.W = kBatchNT - 8;
+            a.W = b->nt - 8;
             a.H = b->H[i];
             a.fout = c->buf[1 - p];
             a.fin = c->buf[p];
@@ -166,7 +166,7 @@ static mdf_status build_graph(mdf_batch *b, int parity) {
 // that its items cover the grid (one item per block, at least 2 rows).
 static mdf_status build_items(mdf_batch *b) {
     const int count = b->count;
-    const int W = kBatchNT - 8;
+    const int W = b->nt - 8;
     long long strip_rows = 0;
     for (int i = 0; i < count; ++i)
         if (b->active[i]) strip_rows += (long long)((b->ctx[i]->nx + W - 1) / W) * b->ctx[i]->ny;
@@ -289,8 +289,8 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
         b->ctx.push_back(c);
         b->nodes += (long long)c->nx * c->ny;
     }
-    int nt = 0, num_sms = 0, dev = 0;
-    BCKE(batch_occupancy(metric, power_law, walls, &nt, &b->occ, &b->smem));
+    int num_sms = 0, dev = 0;
+    BCKE(batch_occupancy(metric, power_law, walls, &b->nt, &b->occ, &b->smem));
     BCKE(cudaGetDevice(&dev));
     BCKE(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
     b->num_sms = num_sms;
@@ -300,7 +300,7 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
     for (int p = 0; p < 2; ++p) b->h_maps[p].resize(count);
     for (int i = 0; i < count; ++i) {
         CUtensorMap m[2];
-        BCKC(ctx_encode_maps(b->ctx[i], kBatchNT, m));
+        BCKC(ctx_encode_maps(b->ctx[i], b->nt, m));
         for (int p = 0; p < 2; ++p) b->h_maps[p][i] = m[p];
     }
     BCKC(build_items(b));

@@ -340,12 +340,12 @@ __device__ __forceinline__ void march_walls(const CUtensorMap *tmap, const StepA
     __syncthreads();
 }
 
-// Resident blocks the register budget is sized for: 3 x 128 threads (up to
-// 170 registers: the wall and power-law logic does not fit 128 without
-// spilling), 2 x 256.
+// Resident blocks the register budget is sized for: 4 x 96 or 3 x 128
+// threads (up to 170 registers: the wall and power-law logic does not fit
+// 128 without spilling), 2 x 256.
 template <int NT>
 constexpr int walls_min_blocks() {
-    return NT <= 128 ? 3 : 2;
+    return NT <= 96 ? 4 : (NT <= 128 ? 3 : 2);
 }
 
 template <int NT, int MK, bool PL, bool FORCED>
@@ -477,14 +477,19 @@ cudaError_t walls_launch(const CUtensorMap *tmap, const StepArgs &args, int metr
     return launch_nt<128>(tmap, args, metric, plan, stream);
 }
 
+// Batches use 96-thread blocks (strips of 88 columns): the 2^k + 1 node
+// sides of a cavity sweep waste fewer thread columns than with 120-column
+// strips (513 nodes: 6 x 96 = 576 threads against 5 x 128 = 640).
+constexpr int kWallsBatchNT = 96;
+
 cudaError_t walls_batch_occupancy(int metric, int power_law, int *nt, int *occ, int *smem) {
-    *nt = 128;
-    MDF_WALLS_DISPATCH(128, batch_occupancy_t, occ, smem)
+    *nt = kWallsBatchNT;
+    MDF_WALLS_DISPATCH(kWallsBatchNT, batch_occupancy_t, occ, smem)
 }
 
 cudaError_t walls_batch_launch(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps,
                                int metric, int power_law, int grid, int forced, cudaStream_t stream) {
-    MDF_WALLS_DISPATCH(128, batch_launch_t, items, nitems, args, maps, grid, forced, stream)
+    MDF_WALLS_DISPATCH(kWallsBatchNT, batch_launch_t, items, nitems, args, maps, grid, forced, stream)
 }
 
 }  // namespace mdf
