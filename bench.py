@@ -220,11 +220,11 @@ def batch_problems(count=BATCH_COUNT, seed=BATCH_SEED, u0=0.1):
     return probs
 
 
-def batch_benchmark(mdf, torch, stream, steps=200, solo_sample=16):
+def batch_benchmark(mdf, torch, stream, steps=200, solo_sample=16, count=BATCH_COUNT):
     """Throughput of the batched step over the seeded 512-cavity sweep, against
     the same cavities stepped one problem per launch (timed on a sample of
     `solo_sample` cavities and scaled by node count)."""
-    probs = batch_problems()
+    probs = batch_problems(count)
     t0 = time.perf_counter()
     batch = mdf.Batch(probs, stream=stream)
     create_s = time.perf_counter() - t0
@@ -284,7 +284,7 @@ def batch_benchmark(mdf, torch, stream, steps=200, solo_sample=16):
         sv.close()
     solo_mlups = solo_nodes * steps / (solo_ms / 1e3) / 1e6
     return {"workload": "%d power-law cavities, sides {65,129,257,513}, Re log-uniform [100,5000], "
-                        "n uniform [0.5,1.5], seed %d" % (BATCH_COUNT, BATCH_SEED),
+                        "n uniform [0.5,1.5], seed %d" % (count, BATCH_SEED),
             "steps": steps, "nodes": nodes, "ms_per_step": ms / steps, "value": batch_mlups, "unit": "MLUPS",
             "launches_per_step": 1, "work_items": info["work_items"], "blocks": info["blocks"],
             "kernel": batch_kernel, "storage": storage,
@@ -459,6 +459,8 @@ def main():
     ap.add_argument("--no-rho0", action="store_true", help="skip the run with the alpha = 0 distribution")
     ap.add_argument("--launch", default=None,
                     help="threads,rows_per_block: pin the launch plan instead of the autotuned one (profiling)")
+    ap.add_argument("--batch-count", type=int, default=BATCH_COUNT,
+                    help="cavities of the batched sweep (default 512; fewer only for profiling)")
     ap.add_argument("--nx", type=int, default=NX,
                     help="grid side (default 4096, the benchmark workload; smaller sides only for profiling)")
     args = ap.parse_args()
@@ -538,7 +540,7 @@ def main():
     rho0 = None if args.no_rho0 else rho0_benchmark(mdf, W, torch, stream, nx)
 
     # ---- batched sweep: many cavities, one launch per step
-    batch = None if args.no_batch else batch_benchmark(mdf, torch, stream)
+    batch = None if args.no_batch else batch_benchmark(mdf, torch, stream, count=args.batch_count)
 
     # ---- power-law cavities on the body-fitted trapezoid grid
     body = None if args.no_body_fitted else body_fitted_benchmark(mdf, W, torch, stream)
