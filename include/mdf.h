@@ -340,9 +340,10 @@ mdf_status mdf_batch_info(const mdf_batch *batch, long long info[6]);
 /* Kernel family of the batch step: 0 marches (work items are strips x bands
  * of each problem), 1 tiles (work items are the 16 x 16 tiles of each
  * problem, the tile kernel of mdf_set_launch).  mdf_batch_create times both
- * and keeps the marches unless the tiles are more than 10 % faster;
- * mdf_batch_set_launch replaces that choice (waits for the batch's streams;
- * MDF_E_INVALID for another kind).  mdf_batch_launch_kind returns the
+ * and keeps the marches unless the tiles are more than 10 % faster, and
+ * mdf_batch_set_active times them again over the problems that remain
+ * (FP32 batches); mdf_batch_set_launch fixes the choice for good (waits for
+ * the batch's streams; MDF_E_INVALID for another kind).  mdf_batch_launch_kind returns the
  * current one (-1 for NULL). */
 mdf_status mdf_batch_set_launch(mdf_batch *batch, int kind);
 int mdf_batch_launch_kind(const mdf_batch *batch);

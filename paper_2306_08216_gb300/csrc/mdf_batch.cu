@@ -38,6 +38,7 @@ struct mdf_batch {
     int nt = 0;                                    // block size of the march kernel (strips of nt - 8 columns)
     int nitems = 0, grid = 0, occ = 0, smem = 0;
     int tile = 0, occ_tile = 0, smem_tile = 0;     // tile mode: one work item per 16 x 16 tile
+    int pinned = 0;                                // mode set by mdf_batch_set_launch (no re-timing)
     int storage = 0;                               // StorageKind of every problem (16-bit: tile mode only)
     int forced = 0;                                // some problem has a force, force rate or source
     int cur = 0;
@@ -212,23 +213,27 @@ static mdf_status build_items(mdf_batch *b) {
     return MDF_OK;
 }
 
-// Time a few steps of each kernel family from the initial states (buffer 0
-// of every problem is read, buffer 1 written, so the states are unchanged)
-// and keep the march unless the tiles are more than 10 % faster.
+// Time a few steps of each kernel family over the active problems (their
+// current buffers are read and the other ones written, so the states are
+// unchanged; the batch's streams must be idle) and keep the march unless the
+// tiles are more than 10 % faster.  Run at creation and whenever the active
+// set changes: a batch whose remaining problems are few and small steps
+// faster by tiles than by the long serial bands of a march.
 static mdf_status choose_kernel(mdf_batch *b) {
     cudaEvent_t e0, e1;
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));
     float best[2] = {1e30f, 1e30f};
+    const int parity = b->cur;
     for (int pass = 0; pass < 2; ++pass)
         for (int k = 0; k < 2; ++k) {
             b->tile = k;
             mdf_status s = build_items(b);
             if (s != MDF_OK) return s;
-            BCK(b, launch_one(b, 0, 0));
-            BCK(b, cudaEventRecord(e0, 0));
-            for (int r = 0; r < 4; ++r) BCK(b, launch_one(b, 0, 0));
-            BCK(b, cudaEventRecord(e1, 0));
+            BCK(b, launch_one(b, parity, b->stream));
+            BCK(b, cudaEventRecord(e0, b->stream));
+            for (int r = 0; r < 4; ++r) BCK(b, launch_one(b, parity, b->stream));
+            BCK(b, cudaEventRecord(e1, b->stream));
             BCK(b, cudaEventSynchronize(e1));
             float ms = 0.0f;
             BCK(b, cudaEventElapsedTime(&ms, e0, e1));
@@ -421,7 +426,10 @@ mdf_status mdf_batch_set_active(mdf_batch *b, int index, int active) {
     b->active[index] = (char)active;
     mdf_status s = build_items(b);
     if (s != MDF_OK) return s;
-    return upload_args(b);
+    s = upload_args(b);
+    if (s != MDF_OK) return s;
+    if (!b->pinned && b->storage == MDF_STORAGE_FP32 && b->occ_tile >= 1 && b->nitems > 0) s = choose_kernel(b);
+    return s;
 }
 
 mdf_status mdf_batch_residual(mdf_batch *b, double *residual, int *status) {
@@ -476,6 +484,7 @@ mdf_status mdf_batch_set_launch(mdf_batch *b, int kind) {
     BCK(b, cudaStreamSynchronize(b->stream));
     BCK(b, cudaStreamSynchronize(b->cstream));
     b->tile = kind;
+    b->pinned = 1;
     return build_items(b);
 }
 
