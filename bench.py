@@ -3,7 +3,7 @@
 Workload: periodic Taylor-Green vortex on a 4096 x 4096 uniform grid, FP32
 state and arithmetic, nu = 0.01, U0 = 0.01, CFL 0.5, eta = 0.8, s'/s = 1.5.
 One bench step = one time step of the method over the whole grid (one fused
-kernel launch).  The two state buffers (2 x 676 MB) are far larger than L2, so
+kernel launch).  The two state buffers (2 x 692 MB) are far larger than L2, so
 every step streams the state from HBM; no L2 flush is needed.
 
   value      MLUPS (million lattice-node updates per second) of the whole job,
@@ -569,7 +569,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "taylor_green_%dx%d_fp32" % (nx, ny), "nx": nx, "ny": ny, "nu": NU, "U0": U0, "cfl": 0.5,
-                   "eta": 0.8, "s_ratio": 1.5, "l2": "inputs larger than L2 (2 x 676 MB state), no flush",
+                   "eta": 0.8, "s_ratio": 1.5, "l2": "inputs larger than L2 (2 x 692 MB state), no flush",
                    "parallelism": "replicas x%d" % world, "launch": info},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": ncu_traffic_per_launch(), "bytes_per_node": bpn,
