@@ -44,9 +44,10 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_library_links_no_torch(lib):
     # the boundary takes plain pointers; the library must not pull in torch
-    maps = open("/proc/self/maps").read() if os.path.exists("/proc/self/maps") else ""
     out = os.popen("ldd %s" % mdf.LIB_PATH).read()
-    assert "torch" not in out and "c10" not in out
+    # library names only (the load addresses are random hex and may contain "c10")
+    names = [line.split()[0] for line in out.splitlines() if line.strip()]
+    assert names and not any("torch" in n or n.startswith("libc10") for n in names), names
 
 
 def _good():
