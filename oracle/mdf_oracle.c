@@ -63,9 +63,11 @@
  *   - dF/dt enters Step 4 as dt^2/2 w_j dF/dt (Eq. 2.3.24); the h^2/2 term
  *     of the fbar update is dropped (Remark 2).  R, F and dF/dt are set by
  *     the caller (constants or fields) and may change between steps.
- * Parity unpinned: the curvilinear path for non-affine maps (trapezoid) has
- * no closed form to pin it; it is checked only through its affine and
- * separable special cases and grid refinement.
+ * The curvilinear path is pinned on a doubly periodic non-affine map by the
+ * steady periodic flow of Sec. 4.2 (second-order convergence to the closed
+ * form).  Parity unpinned: the one-sided metric differences beside the
+ * walls of a non-affine map (the trapezoid) have no closed form; they are
+ * checked only through the affine scaled map, for which they are exact.
  */
 #include <math.h>
 #include <stdlib.h>

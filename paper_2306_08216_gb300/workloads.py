@@ -89,6 +89,23 @@ def four_roll_mill(n, U0=1e-4, nu=0.01):
     return u, v, np.zeros_like(u), Fx, Fy, grads
 
 
+def distorted_periodic_grid(n, a):
+    """Doubly periodic non-affine grid of n x n nodes on [0, 1)^2:
+    x = xi + a sin(2 pi eta), y = eta + a sin(2 pi xi), xi, eta = i/n
+    (a < 1/(2 pi) keeps the map one-to-one).  Returns X, Y [n, n]."""
+    xi = np.arange(n) / n
+    XI, ETA = np.meshgrid(xi, xi)
+    return XI + a * np.sin(2 * math.pi * ETA), ETA + a * np.sin(2 * math.pi * XI)
+
+
+def periodic_flow_at(X, Y, u0=0.1, nu=0.01):
+    """Eqs. 4.2.1-4.2.2 sampled at arbitrary node coordinates: u, v, Fx, Fy."""
+    tp = 2.0 * math.pi
+    u = u0 * np.sin(tp * X) * np.sin(tp * Y)
+    v = u0 * np.cos(tp * X) * np.cos(tp * Y)
+    return u, v, 8.0 * math.pi ** 2 * nu * u, 8.0 * math.pi ** 2 * nu * v
+
+
 def periodic_flow(nx, ny, u0=0.1, nu=0.01, rho0=1.0):
     """Eqs. 4.2.1-4.2.2 on [0, 1)^2 (nx x ny nodes): steady u, v, p and the force."""
     X, Y = np.meshgrid(periodic_nodes(nx, 1.0), periodic_nodes(ny, 1.0))
