@@ -23,7 +23,9 @@
  *  - Device work is enqueued on the stream set by mdf_set_stream (default:
  *    the legacy default stream) and is asynchronous unless stated.
  *  - A context belongs to the device that was current at mdf_create; calls
- *    must be made with that device current.  Contexts are not thread-safe.
+ *    must be made with that device current.  A context (or batch) is not
+ *    thread-safe: use it from one host thread at a time.  Different contexts
+ *    may be created and stepped from different threads at once.
  */
 #ifndef MDF_H
 #define MDF_H
@@ -249,7 +251,10 @@ mdf_status mdf_load(mdf_ctx *ctx, const char *path);
 
 double mdf_dt(const mdf_ctx *ctx);                 /* time step of Eq. 3.1 */
 long long mdf_steps_done(const mdf_ctx *ctx);
-const char *mdf_last_error(const mdf_ctx *ctx);    /* ctx may be NULL */
+/* The reason for the context's last failed call; with ctx NULL, the reason
+ * the calling thread's last mdf_create failed.  Valid until the next call on
+ * the same context (or thread). */
+const char *mdf_last_error(const mdf_ctx *ctx);
 
 /* Launch geometry of the fused step kernel: info[0] threads per block,
  * info[1] output columns per block, info[2] rows per block, info[3] blocks in
@@ -347,7 +352,7 @@ mdf_status mdf_batch_info(const mdf_batch *batch, long long info[6]);
  * current one (-1 for NULL). */
 mdf_status mdf_batch_set_launch(mdf_batch *batch, int kind);
 int mdf_batch_launch_kind(const mdf_batch *batch);
-const char *mdf_batch_last_error(const mdf_batch *batch);
+const char *mdf_batch_last_error(const mdf_batch *batch); /* NULL: this thread's last failed create */
 
 /* Residual and drift with no allocation at all (the paper has no
  * counterpart; this is a service for callers that may not allocate device

@@ -70,7 +70,7 @@ mdf_status mdf_net_gradient(mdf_net *net, int batch, const float *inputs, const 
 mdf_status mdf_net_train_step(mdf_net *net, int batch, const float *inputs, const float *targets, double lr,
                               double *loss, int on_device);
 
-const char *mdf_net_last_error(const mdf_net *net); /* net may be NULL */
+const char *mdf_net_last_error(const mdf_net *net); /* NULL: this thread's last failed create */
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,7 @@
 
 using namespace mdf;
 
-static char g_create_error[256] = {0};
+static thread_local char g_create_error[256] = {0};
 
 static mdf_status fail(mdf_ctx *c, mdf_status st, const char *fmt, ...) {
     char *dst = c ? c->last_error : g_create_error;
@@ -46,9 +46,9 @@ static bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
 // the environment, the k-th device (or pinned host) allocation made while a
 // context is created fails as if memory had run out, so that every error
 // path of mdf_create can be exercised without touching the GPU's state.
-// The count restarts with every mdf_create; 0 or unset disables it (a debug
-// aid: the counter is shared by all threads).
-static int g_fail_alloc = 0;
+// The count restarts with every mdf_create; 0 or unset disables it.  The
+// counter belongs to the creating thread.
+static thread_local int g_fail_alloc = 0;
 
 static cudaError_t dev_malloc(void **p, size_t bytes) {
     if (g_fail_alloc > 0 && --g_fail_alloc == 0) return cudaErrorMemoryAllocation;

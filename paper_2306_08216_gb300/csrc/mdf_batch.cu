@@ -57,7 +57,7 @@ struct mdf_batch {
     char last_error[256] = {0};
 };
 
-static char g_batch_error[256] = {0};
+static thread_local char g_batch_error[256] = {0};
 
 static mdf_status bfail(mdf_batch *b, mdf_status st, const char *fmt, ...) {
     char *dst = b ? b->last_error : g_batch_error;

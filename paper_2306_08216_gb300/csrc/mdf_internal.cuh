@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace mdf {
 
 // Storage: each of the 10 planes fhat_{alpha,j} (plane k = 5 alpha + j) is
@@ -45,16 +47,17 @@ inline size_t state_buffer_bytes(int storage, long long plane, int rho0 = 0) {
 // One-time per-kernel launch setup (the dynamic shared-memory attribute) is
 // a property of each device: a launcher keeps a bitmask of the devices
 // (0..63) it has set up and redoes the setup on a device it has not seen.
-// Two host threads may both set a kernel up; that is harmless.
-inline bool needs_device_setup(unsigned long long mask) {
+// The mask is atomic, so contexts on different host threads may launch
+// concurrently; two threads may both set a kernel up, which is harmless.
+inline bool needs_device_setup(const std::atomic<unsigned long long> &mask) {
     int d = 0;
     cudaGetDevice(&d);
-    return d >= 64 || !((mask >> d) & 1ull);
+    return d >= 64 || !((mask.load(std::memory_order_acquire) >> d) & 1ull);
 }
-inline void mark_device_setup(unsigned long long &mask) {
+inline void mark_device_setup(std::atomic<unsigned long long> &mask) {
     int d = 0;
     cudaGetDevice(&d);
-    if (d < 64) mask |= 1ull << d;
+    if (d < 64) mask.fetch_or(1ull << d, std::memory_order_release);
 }
 
 // Error codes the kernels raise in StepArgs::err (first one wins).

@@ -704,7 +704,7 @@ template <int NT, int MK, bool PL, bool WALLS, bool RHO0>
 cudaError_t launch_t(const CUtensorMap *tmap, const StepArgs &args, const StepPlan &plan, cudaStream_t stream) {
     auto k = step_kernel<NT, MK, PL, WALLS, RHO0>;
     const int smem = smem_bytes<NT, MK, PL, WALLS, RHO0>();
-    static unsigned long long configured = 0;  // devices set up
+    static std::atomic<unsigned long long> configured{0};  // devices set up
     if (needs_device_setup(configured)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
@@ -728,7 +728,7 @@ cudaError_t batch_launch_t(const BatchItem *items, int nitems, const StepArgs *a
                            int grid, cudaStream_t stream) {
     auto k = batch_kernel<NT, MK, PL, WALLS, RHO0>;
     const int smem = smem_bytes<NT, MK, PL, WALLS, RHO0>();
-    static unsigned long long configured = 0;  // devices set up
+    static std::atomic<unsigned long long> configured{0};  // devices set up
     if (needs_device_setup(configured)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;

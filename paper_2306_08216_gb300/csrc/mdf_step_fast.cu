@@ -298,7 +298,7 @@ template <int NT, int MK, bool FORCED, int ST>
 cudaError_t fast_launch_t(const CUtensorMap *tmap, const StepArgs &args,
                           const StepPlan &plan, cudaStream_t stream) {
     auto k = fast_kernel<NT, MK, FORCED, ST>;
-    static unsigned long long configured = 0;  // devices set up
+    static std::atomic<unsigned long long> configured{0};  // devices set up
     if (needs_device_setup(configured)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem<NT, ST>());
         if (e != cudaSuccess) return e;

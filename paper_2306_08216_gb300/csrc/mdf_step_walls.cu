@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(NT, walls_min_blocks<NT>())
 template <int NT, int MK, bool PL, bool FORCED>
 cudaError_t launch_t(const CUtensorMap *tmap, const StepArgs &args, const StepPlan &plan, cudaStream_t stream) {
     auto k = walls_kernel<NT, MK, PL, FORCED>;
-    static unsigned long long configured = 0;  // devices set up
+    static std::atomic<unsigned long long> configured{0};  // devices set up
     if (needs_device_setup(configured)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, walls_smem<NT>());
         if (e != cudaSuccess) return e;
@@ -402,7 +402,7 @@ template <int NT, int MK, bool PL, bool FORCED>
 cudaError_t batch_launch_ft(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps,
                             int grid, cudaStream_t stream) {
     auto k = walls_batch_kernel<NT, MK, PL, FORCED>;
-    static unsigned long long configured = 0;  // devices set up
+    static std::atomic<unsigned long long> configured{0};  // devices set up
     if (needs_device_setup(configured)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, walls_smem<NT>());
         if (e != cudaSuccess) return e;

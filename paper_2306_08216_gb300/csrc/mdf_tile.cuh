@@ -555,7 +555,7 @@ template <int MK, bool PL, bool WALLS, int ST, bool RHO0 = false>
 cudaError_t tile_launch_t(const StepArgs &args, const StepPlan &plan, cudaStream_t stream) {
     auto k = tile_kernel<kTX, kTY, MK, PL, WALLS, ST, RHO0>;
     constexpr int smem = tile_smem<MK, PL, WALLS, RHO0>();
-    static unsigned long long configured = 0;  // devices set up
+    static std::atomic<unsigned long long> configured{0};  // devices set up
     if (needs_device_setup(configured)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
@@ -578,7 +578,7 @@ template <int MK, bool PL, bool WALLS, int ST>
 cudaError_t tile_batch_launch_t(const BatchItem *items, int nitems, const StepArgs *args, int grid,
                                 cudaStream_t stream) {
     auto k = tile_batch_kernel<kTX, kTY, MK, PL, WALLS, ST>;
-    static unsigned long long configured = 0;  // devices set up
+    static std::atomic<unsigned long long> configured{0};  // devices set up
     if (needs_device_setup(configured)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_smem<MK, PL, WALLS>());
         if (e != cudaSuccess) return e;

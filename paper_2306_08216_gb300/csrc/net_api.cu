@@ -57,7 +57,7 @@ struct mdf_net {
     char last_error[256] = {0};
 };
 
-static char g_net_error[256] = {0};
+static thread_local char g_net_error[256] = {0};
 
 static mdf_status nfail(mdf_net *n, mdf_status st, const char *fmt, ...) {
     char *dst = n ? n->last_error : g_net_error;

@@ -98,6 +98,43 @@ def test_null_arguments(lib):
     assert lib.mdf_steps_done(None) == -1
 
 
+def test_creation_errors_are_per_thread(lib):
+    """mdf_last_error(NULL) reports the calling thread's last failed create:
+    thread A fails, thread B fails with another reason, then A reads A's."""
+    import threading
+
+    gate_a, gate_b = threading.Event(), threading.Event()
+    seen = {}
+
+    def a():
+        g, f, b, p = _good()
+        g.nx = 4
+        h = ctypes.c_void_p()
+        seen["a_st"] = lib.mdf_create(ctypes.byref(g), ctypes.byref(f), ctypes.byref(b), ctypes.byref(p),
+                                      ctypes.byref(h))
+        gate_a.set()
+        gate_b.wait(30)
+        seen["a"] = lib.mdf_last_error(None)
+
+    def b_():
+        gate_a.wait(30)
+        g, f, b, p = _good()
+        f.nu = -1.0
+        h = ctypes.c_void_p()
+        seen["b_st"] = lib.mdf_create(ctypes.byref(g), ctypes.byref(f), ctypes.byref(b), ctypes.byref(p),
+                                      ctypes.byref(h))
+        seen["b"] = lib.mdf_last_error(None)
+        gate_b.set()
+
+    ts = [threading.Thread(target=a), threading.Thread(target=b_)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join(60)
+    assert seen["a_st"] == seen["b_st"] == mdf.MDF_E_INVALID
+    assert b"nx" in seen["a"] and b"nu" in seen["b"], seen
+
+
 def test_16bit_storage_passes_validation_on_every_grid_kind(lib):
     """16-bit storage is valid on curvilinear grids with walls and a power law
     (the tile kernel serves it): validation passes, and without a GPU the
