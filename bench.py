@@ -328,7 +328,8 @@ def storage_benchmark(mdf, W, torch, stream, ref_solver, nx, steps=500, warmup=2
 def rho0_benchmark(mdf, W, torch, stream, nx, steps=300, warmup=20):
     """The Taylor-Green workload with the alpha = 0 distribution of Eq. 2.1.2
     evolved beside alpha = 1, 2 (rho_0 = 1 + 0.1 sin 2 pi x cos 2 pi y; 15
-    FP32 planes, general shared-ring kernel): device-timed MLUPS, the
+    FP32 planes; the kernel the autotuner picks: the periodic register-window
+    march with the scalar lane, or the tile kernel): device-timed MLUPS, the
     fraction of the measured copy bandwidth at 120 B per node, and the
     change of total rho_0 (conserved on a periodic grid without source)."""
     import numpy as np

@@ -125,9 +125,11 @@ enum { MDF_STORAGE_FP32 = 0, MDF_STORAGE_FP16 = 1, MDF_STORAGE_BF16 = 2 };
  * feeds back into neither u nor P, so the alpha = 1, 2 results do not change.
  * Walls: non-equilibrium extrapolation with the wall's rho_0 equal to the
  * interior neighbour's (the paper leaves the alpha = 0 wall condition open).
- * The state grows to 15 FP32 planes (60 B/node) and every grid kind steps
- * on the general (shared-ring) kernel; FP32 storage only, and batches reject
- * it (MDF_E_INVALID).  mdf_init_fields starts it at rho_0 = 1. */
+ * The state grows to 15 FP32 planes (60 B/node); every grid kind has a
+ * kernel with the lane (periodic Newtonian problems the register-window
+ * march, the others the shared-ring march, all of them the tile kernel).
+ * FP32 storage only, and batches reject it (MDF_E_INVALID).
+ * mdf_init_fields starts it at rho_0 = 1. */
 typedef struct {
     double c, cfl, eta, s_ratio;
     int storage;

@@ -63,6 +63,12 @@ __device__ __forceinline__ F2 lds2(const unsigned char *base, int byte_off) {
 __device__ __forceinline__ void sts2(unsigned char *base, int byte_off, F2 a) {
     *reinterpret_cast<unsigned long long *>(base + byte_off) = a.r;
 }
+__device__ __forceinline__ float lds1(const unsigned char *base, int byte_off) {
+    return *reinterpret_cast<const float *>(base + byte_off);
+}
+__device__ __forceinline__ void sts1(unsigned char *base, int byte_off, float v) {
+    *reinterpret_cast<float *>(base + byte_off) = v;
+}
 
 // ------------------------------------------------------------ TMA, mbarrier
 

@@ -188,7 +188,7 @@ cudaError_t tile_batch_launch(const BatchItem *items, int nitems, const StepArgs
 
 // Periodic Newtonian fast path on uniform/separable grids (mdf_step_fast.cu).
 bool fast_path_applies(int metric, int power_law, int walls);
-cudaError_t fast_occupancy(int metric, int storage, int nt, int *occ, int *smem);
+cudaError_t fast_occupancy(int metric, int storage, int rho0, int nt, int *occ, int *smem);
 cudaError_t fast_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
                         cudaStream_t stream);
 

@@ -56,12 +56,6 @@ struct Ring0 {
     static constexpr int ROW = 5 * NT * 4;
     static __device__ __forceinline__ int at(int j, int t) { return (j * NT + t) * 4; }
 };
-__device__ __forceinline__ float lds1(const unsigned char *base, int byte_off) {
-    return *reinterpret_cast<const float *>(base + byte_off);
-}
-__device__ __forceinline__ void sts1(unsigned char *base, int byte_off, float v) {
-    *reinterpret_cast<float *>(base + byte_off) = v;
-}
 
 // Difference weights of one axis for pass 1 (h) and pass 2 (dt):
 // w = -step * k * (a1, a0, am2) with k = c/dx (or c times the metric).

@@ -11,8 +11,9 @@
 // This file instantiates the shared-ring march (mdf_march.cuh) for
 // curvilinear grids and holds the launch planning and dispatch.  Uniform
 // and separable grids run the register-window marches of mdf_step_fast.cu
-// (periodic, Newtonian) and mdf_step_walls.cu (walls and/or power law);
-// with the alpha = 0 distribution every grid runs mdf_step_rho0.cu.  The
+// (periodic, Newtonian; also with the alpha = 0 distribution) and
+// mdf_step_walls.cu (walls and/or power law); with the alpha = 0
+// distribution every other grid runs mdf_step_rho0.cu.  The
 // tile kernel (mdf_tile.cuh) is a candidate plan on every grid and the only
 // one for 16-bit storage off the periodic fast path; the autotuner of
 // mdf_create chooses between the families by timing.
@@ -72,7 +73,7 @@ int step_candidates(int metric, int power_law, int walls, int storage, int rho0,
                     StepPlan *out, int max, cudaError_t *err) {
     int n = 0;
     *err = cudaSuccess;
-    const bool fast = !rho0 && fast_path_applies(metric, power_law, walls);
+    const bool fast = fast_path_applies(metric, power_law, walls);
     const bool wpath = !rho0 && !fast && walls_path_applies(metric, power_law, walls, storage);
     // the shared-ring march keeps FP32 storage; 16-bit storage off the fast
     // path has the tile kernel only
@@ -80,7 +81,7 @@ int step_candidates(int metric, int power_law, int walls, int storage, int rho0,
     const int nts[2] = {128, 256};
     for (int i = 0; march && i < (fast || wpath ? 2 : 1); ++i) {
         int occ = 0, smem = 0;
-        cudaError_t e = fast    ? fast_occupancy(metric, storage, nts[i], &occ, &smem)
+        cudaError_t e = fast    ? fast_occupancy(metric, storage, rho0, nts[i], &occ, &smem)
                         : wpath ? walls_occupancy(metric, power_law, nts[i], &occ, &smem)
                         : rho0  ? rho0_occupancy(metric, power_law, walls, &occ, &smem)
                                 : occupancy(metric, power_law, walls, &occ, &smem);
@@ -132,8 +133,8 @@ cudaError_t step_launch(const CUtensorMap *tmap, const StepArgs &args, int metri
     const int power_law = args.power_law;
     const int walls = (args.xwall || args.ywall) ? 1 : 0;
     if (plan.kind == PLAN_TILE) return tile_launch(args, metric, plan, stream);
-    if (args.rho0) return rho0_launch(tmap, args, metric, plan, stream);
     if (fast_path_applies(metric, power_law, walls)) return fast_launch(tmap, args, metric, plan, stream);
+    if (args.rho0) return rho0_launch(tmap, args, metric, plan, stream);
     if (walls_path_applies(metric, power_law, walls, args.storage))
         return walls_launch(tmap, args, metric, plan, stream);
     MDF_MARCH_DISPATCH(false, launch_t, tmap, args, plan, stream)

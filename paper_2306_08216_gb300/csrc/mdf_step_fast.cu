@@ -23,6 +23,13 @@
 //       f of pops 1,3 -> exchange buffer, of pops 2,4 -> register window.
 // The exchange buffers are double-buffered by row parity, which is what lets
 // a single barrier per row order every shared-memory hand-off.
+//
+// The alpha = 0 distribution (template flag RHO0, FP32 storage, 128 threads)
+// rides along as a scalar lane with the same stages, windows and exchange
+// rows: relaxed in S2 with the node's u, v; streamed in S1/S3 and recovered
+// in S3 with the u, v of the alpha = 1, 2 fbar of its node; streamed in S0;
+// source w_j R in both streaming steps (Eq. 2.1.2 with ubar_0 = rho_0,
+// E_0 = 0).  Nothing of it flows back into alpha = 1, 2 (Remark 1).
 #include "mdf_device.cuh"
 
 namespace mdf {
@@ -32,8 +39,16 @@ namespace {
 using namespace dev;
 
 // Rows of fhat in flight: four slots still leave two blocks of 256 threads
-// per SM and measured 0.4 % faster than three at 4096^2.
+// per SM and measured 0.4 % faster than three at 4096^2.  With the alpha = 0
+// lane (15 planes per row) three slots keep three blocks of 128 per SM.
 constexpr int FAST_SLOTS = 4;
+constexpr int FAST_SLOTS_RHO0 = 3;
+constexpr int RHO0_NT = 128;
+
+template <bool RHO0>
+__host__ __device__ constexpr int fast_slots() {
+    return RHO0 ? FAST_SLOTS_RHO0 : FAST_SLOTS;
+}
 
 __device__ __forceinline__ F2 pair_of(unsigned long long bits) {
     F2 a;
@@ -44,6 +59,16 @@ __device__ __forceinline__ F2 pair_of(unsigned long long bits) {
 struct W3 {
     F2 w1, w0, w2;
 };
+// The same weights for the scalar alpha = 0 lane.
+struct W1 {
+    float w1, w0, w2;
+};
+__device__ __forceinline__ float lo(F2 p) {
+    float x, y;
+    split2(p, x, y);
+    return x;
+}
+__device__ __forceinline__ W1 lo(const W3 &w) { return W1{lo(w.w1), lo(w.w0), lo(w.w2)}; }
 
 __device__ __forceinline__ W3 weights(float k, float step, const StepArgs &a) {
     W3 w;
@@ -68,19 +93,26 @@ __device__ __forceinline__ F2 force_at_d(const StepArgs &a, int row, int X, F2 f
     return factor * mk2(a.Fxdp[fi], a.Fydp[fi]);
 }
 
-template <int NT, int MK, bool FORCED, int ST>
-__global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
+template <int NT, int MK, bool FORCED, int ST, bool RHO0>
+__global__ void __launch_bounds__(NT, RHO0 ? 3 : (NT <= 128 ? 4 : 2))
     fast_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
-    // one TMA row: 10 FP32 planes, or u, v, P and 4 planes of 16-bit pairs
-    constexpr int TROW = (ST == STORAGE_FP32 ? NPLANES : DEV_PLANES) * NT * 4;
-    constexpr int PROW = 5 * NT * 8;        // one fhat^+ ring row: 5 pairs x NT
-    constexpr int XROW = 2 * NT * 8;        // one exchange row: pops 1, 3 x NT
+    constexpr int SLOTS = fast_slots<RHO0>();
+    // one TMA row: 10 FP32 planes (15 with alpha = 0), or u, v, P and 4
+    // planes of 16-bit pairs
+    constexpr int TROW = (RHO0 ? RHO0_PLANES : ST == STORAGE_FP32 ? NPLANES : DEV_PLANES) * NT * 4;
+    constexpr int PROW = 5 * NT * 8;             // one fhat^+ ring row: 5 pairs x NT
+    constexpr int XROW = 2 * NT * 8;             // one exchange row: pops 1, 3 x NT
+    constexpr int P0ROW = RHO0 ? 5 * NT * 4 : 0;  // the same two for alpha = 0 (scalars)
+    constexpr int X0ROW = RHO0 ? 2 * NT * 4 : 0;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *tma = smem;
-    unsigned char *ringP = tma + FAST_SLOTS * TROW;
+    unsigned char *ringP = tma + SLOTS * TROW;
     unsigned char *xB0 = ringP + RING * PROW;  // fbar^+ of pops 1, 3 of row p (two buffers)
     unsigned char *xF0 = xB0 + 2 * XROW;       // f(t+h) of pops 1, 3 of row q (two buffers)
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(xF0 + 2 * XROW);
+    unsigned char *ringP0 = xF0 + 2 * XROW;    // alpha = 0: fhat^+ ring, exchange rows
+    unsigned char *xB00 = ringP0 + RING * P0ROW;
+    unsigned char *xF00 = xB00 + 2 * X0ROW;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(xF00 + 2 * X0ROW);
     __shared__ int s_abort;
 
     const int t = threadIdx.x;
@@ -95,7 +127,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
 
     if (t == 0) {
         s_abort = 0;
-        for (int i = 0; i < FAST_SLOTS; ++i) mbar_init(&mbar[i], 1);
+        for (int i = 0; i < SLOTS; ++i) mbar_init(&mbar[i], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -103,7 +135,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
         mbar_expect_tx(&mbar[slot], TROW);
         tma_load_row(&tmap, &mbar[slot], tma + slot * TROW, x0, wrap(rowBase + it, a.ny));
     };
-    int issued = min(FAST_SLOTS, nIt);
+    int issued = min(SLOTS, nIt);
     if (t == 0)
         for (int i = 0; i < issued; ++i) load_row(i, i);
 
@@ -117,6 +149,12 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
         wxd = weights(kx, a.dt, a);
     }
     const F2 zero = splat(0.0f);
+    // alpha = 0: the x weights and the rates of the three local maps
+    const W1 wxh1 = lo(wxh), wxd1 = lo(wxd);
+    const float mKp0 = lo(pair_of(a.pmKp)), Dp0 = lo(pair_of(a.pDp));
+    const float mKb0 = lo(pair_of(a.pmKb)), Db0 = lo(pair_of(a.pDb));
+    const float mKk0 = lo(pair_of(a.pmKk)), Dk0 = lo(pair_of(a.pDk));
+    const float hw0 = a.h * 0.2f, dw0 = a.dt * 0.2f;
     const bool calc = t >= 2 && t < NT - 2;   // forms fbar and f
     const bool outc = t >= 4 && t < NT - 4 && X < a.nx;  // forms outputs
 
@@ -125,10 +163,13 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
     F2 D013[5][3];  // fbar of pops 0, 1, 3 (x part done)
     F2 FY[5][2];    // f(t+h) of pops 2, 4
     F2 XF[5][2];    // pass-2 x increments of pops 1, 3
+    float BY0[5][2], D0[5][3], FY0[5][2], XF0[5][2];  // the same windows for alpha = 0
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
         BY[s][0] = BY[s][1] = FY[s][0] = FY[s][1] = XF[s][0] = XF[s][1] = zero;
         D013[s][0] = D013[s][1] = D013[s][2] = zero;
+        BY0[s][0] = BY0[s][1] = FY0[s][0] = FY0[s][1] = XF0[s][0] = XF0[s][1] = 0.0f;
+        D0[s][0] = D0[s][1] = D0[s][2] = 0.0f;
     }
 
     int tslot = 0;
@@ -145,6 +186,9 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
             unsigned char *xB = xB0 + (it & 1) * XROW;
             const unsigned char *xFp = xF0 + ((it & 1) ^ 1) * XROW;
             unsigned char *xF = xF0 + (it & 1) * XROW;
+            unsigned char *xB_0 = xB00 + (it & 1) * X0ROW;
+            const unsigned char *xFp_0 = xF00 + ((it & 1) ^ 1) * X0ROW;
+            unsigned char *xF_0 = xF00 + (it & 1) * X0ROW;
             // ---------------------------------------------- S0: output row r = p - 5
             if (it >= 9 && outc) {
                 // slot k of every window and of the ring holds row r
@@ -170,11 +214,32 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
                                         wy.w2);
                 if (ST == STORAGE_FP32) store_node<true>(a, r, X, out);
                 else store_node_dev<ST, true>(a, r, X, out);
+                if (RHO0) {
+                    // Step 4 on alpha = 0: fhat^+ - dt c.grad f + dt w_j R
+                    const unsigned char *P0r = ringP0 + k * P0ROW;
+                    float out0[5];
+#pragma unroll
+                    for (int j = 0; j < 5; ++j) out0[j] = lds1(P0r, (j * NT + t) * 4);
+                    if (forced && a.r_mode) {
+                        const float sR = dw0 * source_at(a, r, X);
+#pragma unroll
+                        for (int j = 0; j < 5; ++j) out0[j] += sR;
+                    }
+                    out0[1] += XF0[k][0];
+                    out0[3] += XF0[k][1];
+                    const W1 wy1 = lo(wy);
+                    out0[2] = stream1<false>(out0[2], FY0[s4][0], FY0[k][0], FY0[s1][0], FY0[s2][0], false, wy1.w1,
+                                             wy1.w0, wy1.w2);
+                    out0[4] = stream1<false>(out0[4], FY0[s1][1], FY0[k][1], FY0[s4][1], FY0[s3][1], false, wy1.w1,
+                                             wy1.w0, wy1.w2);
+                    store_node0<true>(a, r, X, out0);
+                }
             }
             // ---------------------------------------------- S2: row p
             F2 own1, own3;
+            float own01 = 0.0f, own03 = 0.0f;
             {
-                const bool ok = mbar_wait_bounded(&mbar[tslot], (uint32_t)((it / FAST_SLOTS) & 1));
+                const bool ok = mbar_wait_bounded(&mbar[tslot], (uint32_t)((it / SLOTS) & 1));
                 if (!ok) atomicExch(&s_abort, 1);
                 const float *src = reinterpret_cast<const float *>(tma + tslot * TROW);
                 F2 g[5], n[5], o[5];
@@ -185,6 +250,25 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
                                        ? moments2r(g, c, a.rk_hat * source_at(a, wrap(p, a.ny), X))
                                        : moments2(g, c);
                     noneq2(g, m, inv2c, n);
+                    if (RHO0) {
+                        // Step 1 on alpha = 0 with u, v of this node and the same rates
+                        float g0[5], n0[5], q0[5];
+#pragma unroll
+                        for (int j = 0; j < 5; ++j) g0[j] = src[(NPLANES + j) * NT + t];
+                        noneq0(g0, m.u, m.v, inv2c, n0);
+                        relax0(g0, n0, mKp0, Dp0, q0);
+                        unsigned char *dP0 = ringP0 + k * P0ROW;
+#pragma unroll
+                        for (int j = 0; j < 5; ++j) sts1(dP0, (j * NT + t) * 4, q0[j]);
+                        relax0(g0, n0, mKb0, Db0, q0);
+                        sts1(xB_0, t * 4, q0[1]);
+                        sts1(xB_0, (NT + t) * 4, q0[3]);
+                        own01 = q0[1];
+                        own03 = q0[3];
+                        BY0[k][0] = q0[2];
+                        BY0[k][1] = q0[4];
+                        D0[k][0] = q0[0];
+                    }
                 } else {
                     // fhat = feq(u, v, P) + n: the stored macroscopic fields
                     // give the equilibrium directly
@@ -221,7 +305,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
                 load_row(issued, tslot);
                 ++issued;
             }
-            tslot = (tslot == FAST_SLOTS - 1) ? 0 : tslot + 1;
+            tslot = (tslot == SLOTS - 1) ? 0 : tslot + 1;
             // ---------------------------------------------- S1: pass-2 x increments of row p-3
             if (it >= 5 && outc) {
                 const F2 f1p1 = lds2(xFp, (t + 1) * 8), f1 = lds2(xFp, t * 8);
@@ -230,6 +314,14 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
                 const F2 f3p1 = lds2(xFp, (NT + t + 1) * 8), f3p2 = lds2(xFp, (NT + t + 2) * 8);
                 XF[s3][0] = stream2<false>(zero, f1p1, f1, f1m1, f1m2, false, wxd.w1, wxd.w0, wxd.w2);
                 XF[s3][1] = stream2<false>(zero, f3m1, f3, f3p1, f3p2, false, wxd.w1, wxd.w0, wxd.w2);
+                if (RHO0) {
+                    XF0[s3][0] = stream1<false>(0.0f, lds1(xFp_0, (t + 1) * 4), lds1(xFp_0, t * 4),
+                                                lds1(xFp_0, (t - 1) * 4), lds1(xFp_0, (t - 2) * 4), false, wxd1.w1,
+                                                wxd1.w0, wxd1.w2);
+                    XF0[s3][1] = stream1<false>(0.0f, lds1(xFp_0, (NT + t - 1) * 4), lds1(xFp_0, (NT + t) * 4),
+                                                lds1(xFp_0, (NT + t + 1) * 4), lds1(xFp_0, (NT + t + 2) * 4), false,
+                                                wxd1.w1, wxd1.w0, wxd1.w2);
+                }
             }
             // ---------------------------------------------- S3
             if (calc) {
@@ -245,6 +337,20 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
                                             lds2(xB, (t - 2) * 8), false, wxh.w1, wxh.w0, wxh.w2);
                 D013[k][2] = stream2<false>(b3, lds2(xB, (NT + t - 1) * 8), own3, lds2(xB, (NT + t + 1) * 8),
                                             lds2(xB, (NT + t + 2) * 8), false, wxh.w1, wxh.w0, wxh.w2);
+                if (RHO0) {
+                    // the same on alpha = 0, with h w_j R
+                    float b01 = own01, b03 = own03;
+                    if (forced && a.r_mode) {
+                        const float sR = hw0 * source_at(a, wrap(p, a.ny), X);
+                        D0[k][0] += sR;
+                        b01 += sR;
+                        b03 += sR;
+                    }
+                    D0[k][1] = stream1<false>(b01, lds1(xB_0, (t + 1) * 4), own01, lds1(xB_0, (t - 1) * 4),
+                                              lds1(xB_0, (t - 2) * 4), false, wxh1.w1, wxh1.w0, wxh1.w2);
+                    D0[k][2] = stream1<false>(b03, lds1(xB_0, (NT + t - 1) * 4), own03, lds1(xB_0, (NT + t + 1) * 4),
+                                              lds1(xB_0, (NT + t + 2) * 4), false, wxh1.w1, wxh1.w0, wxh1.w2);
+                }
                 if (it >= 4) {
                     // row q = p - 2 (slot s2); fbar^+ rows q-2..q+2 -> slots s4, s3, s2, s1, k
                     const int qw = wrap(p - 2, a.ny);
@@ -273,71 +379,99 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2)
                     sts2(xF, (NT + t) * 8, f[3]);
                     FY[s2][0] = f[2];
                     FY[s2][1] = f[4];
+                    if (RHO0) {
+                        // Steps 2-3 on alpha = 0, recovered with u, v of the alpha = 1, 2 fbar
+                        float by02 = BY0[s2][0], by04 = BY0[s2][1];
+                        if (forced && a.r_mode) {
+                            const float sRq = hw0 * source_at(a, qw, X);
+                            by02 += sRq;
+                            by04 += sRq;
+                        }
+                        const W1 wy1 = lo(wy);
+                        float fb0[5], n0[5], f0[5];
+                        fb0[0] = D0[s2][0];
+                        fb0[1] = D0[s2][1];
+                        fb0[3] = D0[s2][2];
+                        fb0[2] = stream1<false>(by02, BY0[s1][0], BY0[s2][0], BY0[s3][0], BY0[s4][0], false, wy1.w1,
+                                                wy1.w0, wy1.w2);
+                        fb0[4] = stream1<false>(by04, BY0[s3][1], BY0[s2][1], BY0[s1][1], BY0[k][1], false, wy1.w1,
+                                                wy1.w0, wy1.w2);
+                        noneq0(fb0, m.u, m.v, inv2c, n0);
+                        relax0(fb0, n0, mKk0, Dk0, f0);
+                        sts1(xF_0, t * 4, f0[1]);
+                        sts1(xF_0, (NT + t) * 4, f0[3]);
+                        FY0[s2][0] = f0[2];
+                        FY0[s2][1] = f0[4];
+                    }
                 }
             }
         }
     }
     if (s_abort) {
         if (t == 0) {
-            for (int it = issued - FAST_SLOTS; it < issued; ++it) {
+            for (int it = issued - SLOTS; it < issued; ++it) {
                 if (it < 0) continue;
-                mbar_wait_bounded(&mbar[it % FAST_SLOTS], (uint32_t)((it / FAST_SLOTS) & 1));
+                mbar_wait_bounded(&mbar[it % SLOTS], (uint32_t)((it / SLOTS) & 1));
             }
             atomicCAS(a.err, DEVERR_NONE, DEVERR_TMA_TIMEOUT);
         }
     }
 }
 
-template <int NT, int ST>
+template <int NT, int ST, bool RHO0>
 constexpr int fast_smem() {
-    return FAST_SLOTS * (ST == STORAGE_FP32 ? NPLANES : DEV_PLANES) * NT * 4 +
-           RING * 5 * NT * 8 + 4 * (2 * NT * 8) + FAST_SLOTS * 8;
+    return fast_slots<RHO0>() * (RHO0 ? RHO0_PLANES : ST == STORAGE_FP32 ? NPLANES : DEV_PLANES) * NT * 4 +
+           RING * 5 * NT * 8 + 4 * (2 * NT * 8) + (RHO0 ? RING * 5 * NT * 4 + 4 * (2 * NT * 4) : 0) +
+           fast_slots<RHO0>() * 8;
 }
 
-template <int NT, int MK, bool FORCED, int ST>
+template <int NT, int MK, bool FORCED, int ST, bool RHO0>
 cudaError_t fast_launch_t(const CUtensorMap *tmap, const StepArgs &args,
                           const StepPlan &plan, cudaStream_t stream) {
-    auto k = fast_kernel<NT, MK, FORCED, ST>;
+    auto k = fast_kernel<NT, MK, FORCED, ST, RHO0>;
+    constexpr int smem = fast_smem<NT, ST, RHO0>();
     static std::atomic<unsigned long long> configured{0};  // devices set up
     if (needs_device_setup(configured)) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, fast_smem<NT, ST>());
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         mark_device_setup(configured);
     }
-    k<<<dim3(plan.gx, plan.gy), NT, fast_smem<NT, ST>(), stream>>>(*tmap, args);
+    k<<<dim3(plan.gx, plan.gy), NT, smem, stream>>>(*tmap, args);
     return cudaGetLastError();
 }
 
-template <int NT, int MK, int ST>
+template <int NT, int MK, int ST, bool RHO0>
 cudaError_t fast_occupancy_t(int *occ, int *smem) {
     // both force variants have the same shared memory; take the smaller occupancy
     int o1 = 0, o2 = 0;
-    *smem = fast_smem<NT, ST>();
-    cudaError_t e =
-        cudaFuncSetAttribute(fast_kernel<NT, MK, false, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
+    *smem = fast_smem<NT, ST, RHO0>();
+    cudaError_t e = cudaFuncSetAttribute(fast_kernel<NT, MK, false, ST, RHO0>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fast_kernel<NT, MK, true, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
+        e = cudaFuncSetAttribute(fast_kernel<NT, MK, true, ST, RHO0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 *smem);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, fast_kernel<NT, MK, false, ST>, NT, *smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, fast_kernel<NT, MK, false, ST, RHO0>, NT, *smem);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, fast_kernel<NT, MK, true, ST>, NT, *smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, fast_kernel<NT, MK, true, ST, RHO0>, NT, *smem);
     *occ = o1 < o2 ? o1 : o2;
     return e;
 }
 
-template <int NT, int MK, int ST>
+template <int NT, int MK, int ST, bool RHO0>
 cudaError_t fast_launch_f(const CUtensorMap *tmap, const StepArgs &args,
                           const StepPlan &plan, cudaStream_t stream) {
-    return (args.force_mode || args.force_mode_d || args.r_mode) ? fast_launch_t<NT, MK, true, ST>(tmap, args, plan, stream)
-                           : fast_launch_t<NT, MK, false, ST>(tmap, args, plan, stream);
+    return (args.force_mode || args.force_mode_d || args.r_mode)
+               ? fast_launch_t<NT, MK, true, ST, RHO0>(tmap, args, plan, stream)
+               : fast_launch_t<NT, MK, false, ST, RHO0>(tmap, args, plan, stream);
 }
 
 template <int NT, int MK>
 cudaError_t fast_occupancy_s(int storage, int *occ, int *smem) {
     switch (storage) {
-        case STORAGE_FP16: return fast_occupancy_t<NT, MK, STORAGE_FP16>(occ, smem);
-        case STORAGE_BF16: return fast_occupancy_t<NT, MK, STORAGE_BF16>(occ, smem);
-        default: return fast_occupancy_t<NT, MK, STORAGE_FP32>(occ, smem);
+        case STORAGE_FP16: return fast_occupancy_t<NT, MK, STORAGE_FP16, false>(occ, smem);
+        case STORAGE_BF16: return fast_occupancy_t<NT, MK, STORAGE_BF16, false>(occ, smem);
+        default: return fast_occupancy_t<NT, MK, STORAGE_FP32, false>(occ, smem);
     }
 }
 
@@ -345,9 +479,9 @@ template <int NT, int MK>
 cudaError_t fast_launch_s(const CUtensorMap *tmap, const StepArgs &args,
                           const StepPlan &plan, cudaStream_t stream) {
     switch (args.storage) {
-        case STORAGE_FP16: return fast_launch_f<NT, MK, STORAGE_FP16>(tmap, args, plan, stream);
-        case STORAGE_BF16: return fast_launch_f<NT, MK, STORAGE_BF16>(tmap, args, plan, stream);
-        default: return fast_launch_f<NT, MK, STORAGE_FP32>(tmap, args, plan, stream);
+        case STORAGE_FP16: return fast_launch_f<NT, MK, STORAGE_FP16, false>(tmap, args, plan, stream);
+        case STORAGE_BF16: return fast_launch_f<NT, MK, STORAGE_BF16, false>(tmap, args, plan, stream);
+        default: return fast_launch_f<NT, MK, STORAGE_FP32, false>(tmap, args, plan, stream);
     }
 }
 
@@ -357,7 +491,15 @@ bool fast_path_applies(int metric, int power_law, int walls) {
     return !walls && !power_law && (metric == METRIC_UNIFORM || metric == METRIC_SEPARABLE);
 }
 
-cudaError_t fast_occupancy(int metric, int storage, int nt, int *occ, int *smem) {
+cudaError_t fast_occupancy(int metric, int storage, int rho0, int nt, int *occ, int *smem) {
+    if (rho0) {
+        // the alpha = 0 lane: FP32 storage, 128 threads only
+        *occ = 0;
+        *smem = 0;
+        if (nt != RHO0_NT || storage != STORAGE_FP32) return cudaSuccess;
+        return metric == METRIC_UNIFORM ? fast_occupancy_t<RHO0_NT, METRIC_UNIFORM, STORAGE_FP32, true>(occ, smem)
+                                        : fast_occupancy_t<RHO0_NT, METRIC_SEPARABLE, STORAGE_FP32, true>(occ, smem);
+    }
     if (nt == 256)
         return metric == METRIC_UNIFORM ? fast_occupancy_s<256, METRIC_UNIFORM>(storage, occ, smem)
                                         : fast_occupancy_s<256, METRIC_SEPARABLE>(storage, occ, smem);
@@ -367,6 +509,12 @@ cudaError_t fast_occupancy(int metric, int storage, int nt, int *occ, int *smem)
 
 cudaError_t fast_launch(const CUtensorMap *tmap, const StepArgs &args, int metric,
                         const StepPlan &plan, cudaStream_t stream) {
+    if (args.rho0) {
+        if (plan.NT != RHO0_NT || args.storage != STORAGE_FP32) return cudaErrorInvalidConfiguration;
+        return metric == METRIC_UNIFORM
+                   ? fast_launch_f<RHO0_NT, METRIC_UNIFORM, STORAGE_FP32, true>(tmap, args, plan, stream)
+                   : fast_launch_f<RHO0_NT, METRIC_SEPARABLE, STORAGE_FP32, true>(tmap, args, plan, stream);
+    }
     if (plan.NT == 256)
         return metric == METRIC_UNIFORM ? fast_launch_s<256, METRIC_UNIFORM>(tmap, args, plan, stream)
                                         : fast_launch_s<256, METRIC_SEPARABLE>(tmap, args, plan, stream);

@@ -180,6 +180,68 @@ def test_both_kernel_families_against_oracle(plan, grid):
     check(g, o, U0)
 
 
+def periodic_case(grid, forced, nx=300, ny=90, nu=0.01, u0=0.05):
+    """The periodic flow of Sec. 4.2 on [0, 1) x [0, ny/nx), uniform or with
+    smoothly stretched periodic y nodes; forced: its body force as a field,
+    a constant force rate and a source field R."""
+    ly = ny / nx
+    kw = dict(nu=nu, lx=1.0, ly=ly)
+    X, Y = np.meshgrid(W.periodic_nodes(nx, 1.0), W.periodic_nodes(ny, ly))
+    if grid == "separable":
+        j = np.arange(ny)
+        y = ly * (j / ny + 0.02 * np.sin(2 * np.pi * j / ny) / (2 * np.pi))
+        kw.update(grid="separable", x=W.periodic_nodes(nx, 1.0), y=y)
+        X, Y = np.meshgrid(W.periodic_nodes(nx, 1.0), y)
+    u, v, Fx, Fy = W.periodic_flow_at(X, Y / ly, u0, nu)
+    if forced:
+        kw.update(force=(Fx, Fy), force_rate=(2e-4, -1e-4),
+                  source=0.01 * np.sin(2 * math.pi * X) * np.cos(2 * math.pi * Y / ly))
+    rho = 1 + 0.1 * np.sin(2 * math.pi * X) * np.cos(2 * math.pi * Y / ly)
+    return kw, u, v, rho
+
+
+@pytest.mark.parametrize("forced", [False, True])
+@pytest.mark.parametrize("grid", ["uniform", "separable"])
+def test_periodic_register_march_against_oracle(grid, forced):
+    """The lane on the periodic register-window march (128 threads): three
+    strips of 120 columns (the last ragged) and bands of 37 rows (the last
+    ragged), 300 steps against the oracle; forced adds a force field, a force
+    rate and a source field to both streaming steps."""
+    nx, ny, u0 = 300, 90, 0.05
+    kw, u, v, rho = periodic_case(grid, forced, nx, ny, u0=u0)
+    g, o = both(nx, ny, **kw)
+    g.set_launch(128, 37)
+    assert g.launch_info()["kernel"] == "march" and g.launch_info()["threads"] == 128
+    z = np.zeros((ny, nx))
+    for s in (g, o):
+        if forced:
+            s.init(z, z, z)
+        else:
+            s.init(u, v, z)
+        s.init_rho0(rho)
+    g.step(300)
+    o.step(300)
+    check(g, o, u0)
+
+
+@pytest.mark.parametrize("forced", [False, True])
+def test_no_feedback_on_the_periodic_register_march_bitwise(forced):
+    """Remark 1 on the periodic register-window march: the same plan with and
+    without the lane gives the alpha = 1, 2 state to the bit."""
+    nx, ny = 300, 90
+    kw, u, v, rho = periodic_case("uniform", forced, nx, ny)
+    a = mdf.Solver(nx, ny, **kw)
+    b = mdf.Solver(nx, ny, rho0=True, **kw)
+    z = np.zeros((ny, nx))
+    for s in (a, b):
+        s.set_launch(128, 37)
+        s.init(u, v, z)
+    b.init_rho0(rho)
+    a.step(200)
+    b.step(200)
+    np.testing.assert_array_equal(a.state(), b.state())
+
+
 def test_state_roundtrip_and_checkpoint(tmp_path):
     n = 24
     g = mdf.Solver(n, n, nu=0.01, walls=(True, True), u_wall=(0, 0, 0, 0.1), rho0=True)
@@ -218,7 +280,8 @@ def test_bytes_routing_and_rejections():
 
 def test_large_periodic_grid_sampled():
     """1024^2 Taylor-Green flow with a rho_0 pattern, several strips and
-    bands per block row, against the oracle on the full grid (3 steps)."""
+    bands per block row, against the oracle on the full grid (3 steps), in
+    the plan the autotuner picks."""
     n, U0 = 1024, 0.01
     kw = dict(nu=0.01, lx=2 * math.pi, ly=2 * math.pi)
     g, o = both(n, n, **kw)
