@@ -15,6 +15,7 @@
 #include <time.h>
 
 #include <chrono>
+#include <new>
 #include <thread>
 
 #include "mdf_ctx.cuh"
@@ -300,7 +301,9 @@ static mdf_status create_ctx(const mdf_grid *grid, const mdf_fluid *fluid, const
         const char *fa = getenv("MDF_FAIL_ALLOC");
         g_fail_alloc = fa ? atoi(fa) : 0;
     }
-    mdf_ctx *c = new mdf_ctx();
+    // host allocations never throw across the C ABI
+    mdf_ctx *c = new (std::nothrow) mdf_ctx();
+    if (!c) return fail(nullptr, MDF_E_NOMEM, "host allocation of the context failed");
     c->nx = grid->nx;
     c->ny = grid->ny;
     c->kind = grid->kind;

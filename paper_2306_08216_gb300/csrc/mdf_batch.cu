@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <new>
 #include <vector>
 
 #include "mdf_ctx.cuh"
@@ -94,7 +95,12 @@ static void free_batch(mdf_batch *b) {
 
 // Upload the per-problem argument tables (both parities) from the contexts.
 static mdf_status upload_args(mdf_batch *b) {
-    std::vector<StepArgs> args(b->count);
+    std::vector<StepArgs> args;
+    try {
+        args.resize(b->count);
+    } catch (const std::bad_alloc &) {
+        return bfail(b, MDF_E_NOMEM, "host allocation of the argument table failed");
+    }
     for (int p = 0; p < 2; ++p) {
         for (int i = 0; i < b->count; ++i) {
             mdf_ctx *c = b->ctx[i];
@@ -181,19 +187,23 @@ static mdf_status build_items(mdf_batch *b) {
         b->H[i] = H;
     }
     std::vector<int> order;
-    for (int i = 0; i < count; ++i)
-        if (b->active[i]) order.push_back(i);
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        return (long long)b->ctx[x]->nx * b->ctx[x]->ny > (long long)b->ctx[y]->nx * b->ctx[y]->ny;
-    });
     std::vector<BatchItem> items;
-    for (int i : order) {
-        mdf_ctx *c = b->ctx[i];
-        const int tw = b->tile ? TILE_X : W, th = b->tile ? TILE_Y : b->H[i];
-        const int gx = (c->nx + tw - 1) / tw;
-        const int gy = (c->ny + th - 1) / th;
-        for (int by = 0; by < gy; ++by)
-            for (int bx = 0; bx < gx; ++bx) items.push_back(BatchItem{i, bx, by, 0});
+    try {
+        for (int i = 0; i < count; ++i)
+            if (b->active[i]) order.push_back(i);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return (long long)b->ctx[x]->nx * b->ctx[x]->ny > (long long)b->ctx[y]->nx * b->ctx[y]->ny;
+        });
+        for (int i : order) {
+            mdf_ctx *c = b->ctx[i];
+            const int tw = b->tile ? TILE_X : W, th = b->tile ? TILE_Y : b->H[i];
+            const int gx = (c->nx + tw - 1) / tw;
+            const int gy = (c->ny + th - 1) / th;
+            for (int by = 0; by < gy; ++by)
+                for (int bx = 0; bx < gx; ++bx) items.push_back(BatchItem{i, bx, by, 0});
+        }
+    } catch (const std::bad_alloc &) {
+        return bfail(b, MDF_E_NOMEM, "host allocation of the work items failed");
     }
     b->nitems = (int)items.size();
     b->grid = std::min(b->nitems, std::max(1, b->tile ? b->occ_tile : b->occ) * b->num_sms);
@@ -268,7 +278,9 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
             return bfail(nullptr, MDF_E_INVALID,
                          "problem %d differs from problem 0 in grid kind, fluid model or wall/periodic type", i);
     }
-    mdf_batch *b = new mdf_batch();
+    // host allocations never throw across the C ABI
+    mdf_batch *b = new (std::nothrow) mdf_batch();
+    if (!b) return bfail(nullptr, MDF_E_NOMEM, "host allocation of the batch failed");
     b->count = count;
     b->metric = metric;
     b->power_law = power_law;
@@ -284,6 +296,16 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
         }                                                   \
     } while (0)
 #define BCKE(call) BCKC(([&]() -> mdf_status { BCK(b, call); return MDF_OK; })())
+    try {
+        b->ctx.reserve(count);
+        b->H.resize(count);
+        b->seen_version.resize(count);
+        b->active.assign(count, 1);
+        for (int p = 0; p < 2; ++p) b->h_maps[p].resize(count);
+    } catch (const std::bad_alloc &) {
+        bfail(b, MDF_E_NOMEM, "host allocation of the batch tables failed");
+        BCKC(MDF_E_NOMEM);
+    }
     for (int i = 0; i < count; ++i) {
         mdf_ctx *c = nullptr;
         mdf_status s = ctx_create_untuned(&grids[i], &fluids[i], &bcs[i], params ? &params[i] : nullptr, &c);
@@ -299,10 +321,6 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
     BCKE(cudaGetDevice(&dev));
     BCKE(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
     b->num_sms = num_sms;
-    b->H.resize(count);
-    b->seen_version.resize(count);
-    b->active.assign(count, 1);
-    for (int p = 0; p < 2; ++p) b->h_maps[p].resize(count);
     for (int i = 0; i < count; ++i) {
         CUtensorMap m[2];
         BCKC(ctx_encode_maps(b->ctx[i], b->nt, m));

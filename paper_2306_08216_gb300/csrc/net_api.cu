@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <new>
 #include <vector>
 
 #include "../../include/mdf_net.h"
@@ -80,7 +81,12 @@ template <typename T>
 static mdf_status nalloc(mdf_net *n, T **p, size_t count) {
     void *q = nullptr;
     NCK(n, cudaMalloc(&q, count * sizeof(T)));
-    n->allocs.push_back(q);
+    try {
+        n->allocs.push_back(q);
+    } catch (const std::bad_alloc &) {
+        cudaFree(q);
+        return nfail(n, MDF_E_NOMEM, "host allocation failed");
+    }
     *p = static_cast<T *>(q);
     return MDF_OK;
 }
@@ -304,7 +310,9 @@ mdf_status mdf_net_create(int resolution, int max_batch, mdf_net **out) {
     if (resolution < 8 || resolution % 8) return nfail(nullptr, MDF_E_INVALID, "resolution must be a multiple of 8");
     if (max_batch < 1 || (long long)max_batch * resolution * resolution > (1ll << 28))
         return nfail(nullptr, MDF_E_INVALID, "max_batch must be >= 1 and max_batch R^2 <= 2^28");
-    mdf_net *n = new mdf_net();
+    // host allocations never throw across the C ABI
+    mdf_net *n = new (std::nothrow) mdf_net();
+    if (!n) return nfail(nullptr, MDF_E_NOMEM, "host allocation of the network failed");
     n->R = resolution;
     n->Bmax = max_batch;
 #define NCKC(call)                                       \

@@ -76,6 +76,7 @@ def _good():
     lambda g, f, b, p: (setattr(f, "power_law", 1), setattr(f, "K", 0.0)),
     lambda g, f, b, p: (setattr(f, "power_law", 1), setattr(f, "K", 1.0), setattr(f, "n", 1.0),
                         setattr(f, "nu_min", 2.0), setattr(f, "nu_max", 1.0)),
+    lambda g, f, b, p: (setattr(g, "nx", 65536), setattr(g, "ny", 32769)),  # nx * ny > 2^31
     lambda g, f, b, p: setattr(p, "storage", 3),          # unknown storage mode
     lambda g, f, b, p: setattr(p, "storage", -1),
     # 16-bit storage with the alpha = 0 distribution
