@@ -184,6 +184,22 @@ mdf_status mdf_set_force_rate(mdf_ctx *ctx, int mode, double dfx, double dfy,
  * (4) like the body force. */
 mdf_status mdf_set_source(mdf_ctx *ctx, int mode, double r, const float *R, int on_device);
 
+/* Metric coefficients of a curvilinear grid given by the caller, in place
+ * of those mdf_create forms from second-order differences of the node
+ * coordinates (the coordinate transformation of the body-fitted path; the
+ * paper leaves open how the coefficients are obtained, so exact derivatives
+ * of an analytic mapping may be passed).  xi_x, xi_y, eta_x, eta_y: FP64,
+ * row-major [ny][nx], derivatives of the computational coordinates per unit
+ * node index (xi = i, eta = j) with respect to x and y; copied.  The time
+ * step keeps the value Eq. 3.1 gave from the node coordinates.  Enqueued on
+ * the context's stream: steps enqueued later use the new coefficients
+ * (synchronise a batch that holds the context first).  Host input is
+ * checked for finite values and the call waits for the upload.  Errors:
+ * MDF_E_INVALID (not a curvilinear grid, NULL arrays, non-finite values),
+ * MDF_E_NOMEM, MDF_E_CUDA. */
+mdf_status mdf_set_metrics(mdf_ctx *ctx, const double *xi_x, const double *xi_y, const double *eta_x,
+                           const double *eta_y, int on_device);
+
 /* Initial state fhat = feq(u, v, p) (Sec. 4: distributions start at
  * equilibrium); wall nodes take the wall velocity.  Resets the step count
  * and the residual snapshot.  With params->rho0 set, the alpha = 0

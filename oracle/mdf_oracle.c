@@ -644,6 +644,21 @@ int orc_set_source(orc_ctx *o, int mode, double r, const double *R) {
     return 0;
 }
 
+/* Metric coefficients xi_x, xi_y, eta_x, eta_y given by the caller (for
+ * instance the exact derivatives of an analytic mapping) instead of the
+ * second-order differences of the node coordinates; curvilinear grids only.
+ * The time step keeps the value Eq. 3.1 gave from the node coordinates. */
+int orc_set_metrics(orc_ctx *o, const double *xi_x, const double *xi_y, const double *eta_x, const double *eta_y) {
+    if (!o->xi_x || o->p.grid_kind != 2) return -1;
+    for (long n = 0; n < o->N; ++n) {
+        o->xi_x[n] = xi_x[n];
+        o->xi_y[n] = xi_y[n];
+        o->eta_x[n] = eta_x[n];
+        o->eta_y[n] = eta_y[n];
+    }
+    return 0;
+}
+
 int orc_last_status(void) { return g_last_status; }
 double orc_dt(const orc_ctx *o) { return o->dt; }
 double orc_cs2(const orc_ctx *o) { return o->cs2; }

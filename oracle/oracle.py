@@ -88,6 +88,8 @@ def lib():
             getattr(L, fn).argtypes = [ctypes.c_void_p, _D]
         L.orc_set_source.restype = ctypes.c_int
         L.orc_set_source.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _D]
+        L.orc_set_metrics.restype = ctypes.c_int
+        L.orc_set_metrics.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
         _lib = L
     return _lib
 
@@ -220,6 +222,15 @@ class Oracle:
             st = lib().orc_set_source(self._h, 2, 0.0, _ptr(a))
         if st != 0:
             raise ValueError("the source term needs a Newtonian fluid")
+
+    def set_metrics(self, xi_x, xi_y, eta_x, eta_y):
+        """Metric coefficients of a curvilinear grid given by the caller (ny x nx
+        each) in place of those differenced from the node coordinates."""
+        a = [np.ascontiguousarray(m, dtype=np.float64).ravel() for m in (xi_x, xi_y, eta_x, eta_y)]
+        if any(m.size != self.nx * self.ny for m in a):
+            raise ValueError("metric arrays must have ny x nx entries")
+        if lib().orc_set_metrics(self._h, *(_ptr(m) for m in a)) != 0:
+            raise ValueError("given metrics need a curvilinear grid")
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -642,6 +642,39 @@ mdf_status mdf_set_source(mdf_ctx *c, int mode, double r, const float *R, int on
     return MDF_OK;
 }
 
+mdf_status mdf_set_metrics(mdf_ctx *c, const double *xi_x, const double *xi_y, const double *eta_x,
+                           const double *eta_y, int on_device) {
+    if (!c) return MDF_E_INVALID;
+    if (c->kind != MDF_GRID_CURVILINEAR) return fail(c, MDF_E_INVALID, "given metrics need a curvilinear grid");
+    if (!xi_x || !xi_y || !eta_x || !eta_y) return fail(c, MDF_E_INVALID, "xi_x, xi_y, eta_x, eta_y are required");
+    const size_t N = (size_t)c->nx * c->ny;
+    const double *in[4] = {xi_x, xi_y, eta_x, eta_y};
+    if (!on_device) {
+        for (int k = 0; k < 4; ++k)
+            for (size_t i = 0; i < N; ++i)
+                if (!isfinite(in[k][i])) return fail(c, MDF_E_INVALID, "metric coefficients must be finite");
+    }
+    double *d = nullptr;
+    const double *m[4] = {xi_x, xi_y, eta_x, eta_y};
+    if (!on_device) {
+        CK(c, cudaMalloc(&d, 4 * N * sizeof(double)));
+        for (int k = 0; k < 4; ++k) {
+            const cudaError_t e = cudaMemcpyAsync(d + k * N, in[k], N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+            if (e != cudaSuccess) {
+                cudaFree(d);
+                return fail(c, MDF_E_CUDA, "metric upload: %s", cudaGetErrorString(e));
+            }
+            m[k] = d + k * N;
+        }
+    }
+    cudaError_t e = aux_metrics_given(c->aux, m, c->prm.c, c->mxx, c->mxy, c->mex, c->mey, c->stream);
+    mdf_status st = MDF_OK;
+    if (e != cudaSuccess) st = fail(c, MDF_E_CUDA, "metric kernel: %s", cudaGetErrorString(e));
+    else if (!on_device) st = wait_stream(c, 0);  // the host copies and the scratch are released below
+    if (d) cudaFree(d);
+    return st;
+}
+
 mdf_status mdf_init_fields(mdf_ctx *c, const float *u, const float *v, const float *p, int on_device) {
     if (!c) return MDF_E_INVALID;
     if (!u || !v || !p) return fail(c, MDF_E_INVALID, "u, v, p are required");

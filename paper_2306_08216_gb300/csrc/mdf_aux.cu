@@ -340,6 +340,27 @@ __global__ void metric_kernel(AuxArgs a, Coords cd, double c, float *mxx, float 
     }
 }
 
+// Metric planes from coefficients given per node (FP64, [ny][nx], per unit
+// node index), in the padded layout of metric_kernel: periodic images in the
+// ghost columns of a periodic x axis, zeros beyond x walls.
+__global__ void metric_given_kernel(AuxArgs a, const double *xix, const double *xiy, const double *etx,
+                                    const double *ety, double c, float *mxx, float *mxy, float *mex, float *mey) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (col >= a.pitch) return;
+    const int X = col - GHOST;
+    const long long o = (long long)j * a.pitch + col;
+    if (a.xwall && (X < 0 || X >= a.nx)) {
+        mxx[o] = mxy[o] = mex[o] = mey[o] = 0.0f;
+        return;
+    }
+    const long long n = (long long)j * a.nx + (a.xwall ? X : wrapi(X, a.nx));
+    mxx[o] = (float)(c * xix[n]);
+    mxy[o] = (float)(c * xiy[n]);
+    mex[o] = (float)(c * etx[n]);
+    mey[o] = (float)(c * ety[n]);
+}
+
 // Separable grid: c*xi_x per storage column, c*eta_y per row, and the
 // spacing minima, from 1-D node coordinates (FP64).
 __global__ void metric1d_kernel(AuxArgs a, const double *xc, const double *yc, double c, float *kxv, float *kyv,
@@ -614,6 +635,13 @@ cudaError_t aux_metrics2d(const AuxArgs &a, const double *X, const double *Y, do
                           float *mex, float *mey, double *edge_min, cudaStream_t st) {
     Coords cd{X, Y, a.nx, a.ny, a.xwall, a.ywall, a.lx, a.ly};
     metric_kernel<<<rows_grid(a.pitch, a.ny, 128), 128, 0, st>>>(a, cd, c, mxx, mxy, mex, mey, edge_min);
+    return cudaGetLastError();
+}
+
+cudaError_t aux_metrics_given(const AuxArgs &a, const double *const m[4], double c, float *mxx, float *mxy, float *mex,
+                              float *mey, cudaStream_t st) {
+    metric_given_kernel<<<rows_grid(a.pitch, a.ny, 128), 128, 0, st>>>(a, m[0], m[1], m[2], m[3], c, mxx, mxy, mex,
+                                                                       mey);
     return cudaGetLastError();
 }
 

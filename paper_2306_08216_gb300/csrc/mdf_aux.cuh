@@ -37,6 +37,8 @@ cudaError_t aux_axpy_field(const AuxArgs &a, const float *F, float f0, const flo
                            cudaStream_t st);
 cudaError_t aux_metrics2d(const AuxArgs &a, const double *X, const double *Y, double c, float *mxx, float *mxy,
                           float *mex, float *mey, double *edge_min, cudaStream_t st);
+cudaError_t aux_metrics_given(const AuxArgs &a, const double *const m[4], double c, float *mxx, float *mxy, float *mex,
+                              float *mey, cudaStream_t st);
 cudaError_t aux_metrics1d(const AuxArgs &a, const double *xc, const double *yc, double c, float *kxv, float *kyv,
                           double *edge_min, cudaStream_t st);
 cudaError_t aux_fields(const AuxArgs &a, const float *f, const FieldPtrs &dst, cudaStream_t st);

@@ -71,6 +71,8 @@ _SIGNATURES = [
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("mdf_set_source", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
                                       ctypes.c_int]),
+    ("mdf_set_metrics", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_int]),
     ("mdf_init_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_int]),
     ("mdf_init_rho0", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -304,6 +306,16 @@ class Solver:
             a = _Arr(R, self.nx * self.ny)
             _check(lib().mdf_set_source(self._h, 2, 0.0, a.ptr, a.on_device), self._h)
             self.synchronize()
+
+    def set_metrics(self, xi_x, xi_y, eta_x, eta_y):
+        """Metric coefficients of a curvilinear grid (FP64, ny x nx each, per
+        unit node index) in place of those differenced from the coordinates."""
+        n = self.nx * self.ny
+        arrs = [np.ascontiguousarray(m, dtype=np.float64).ravel() for m in (xi_x, xi_y, eta_x, eta_y)]
+        for a in arrs:
+            assert a.size == n, "expected %d elements, got %d" % (n, a.size)
+        ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in arrs]
+        _check(lib().mdf_set_metrics(self._h, *ptrs, 0), self._h)
 
     def init(self, u, v, p):
         n = self.nx * self.ny

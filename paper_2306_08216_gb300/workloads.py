@@ -52,6 +52,21 @@ def trapezoid_grid(nx, ny, bottom=0.5, top=1.0, height=1.0):
     return X, Y
 
 
+def trapezoid_metrics(nx, ny, bottom=0.5, top=1.0, height=1.0):
+    """Exact metric coefficients of trapezoid_grid per unit node index:
+    x_i = 2 half/(nx - 1), x_j = (top - bottom)(xi - 1/2)/(ny - 1), y_i = 0,
+    y_j = height/(ny - 1), inverted.  Returns xi_x, xi_y, eta_x, eta_y."""
+    xi = np.arange(nx, dtype=np.float64) / (nx - 1)
+    et = np.arange(ny, dtype=np.float64) / (ny - 1)
+    XI, ET = np.meshgrid(xi, et)
+    half = 0.5 * (bottom + (top - bottom) * ET)
+    x_i = 2.0 * half / (nx - 1)
+    x_j = (top - bottom) * (XI - 0.5) / (ny - 1)
+    y_j = np.full_like(XI, height / (ny - 1))
+    J = x_i * y_j
+    return y_j / J, -x_j / J, np.zeros_like(XI), x_i / J
+
+
 def taylor_green(n, U0=0.01, length=2.0 * math.pi):
     """u = -U0 cos x sin y, v = U0 sin x cos y, p = -(U0^2/4)(cos 2x + cos 2y)
     on the periodic square [0, L)^2 with L = 2 pi (k = 2 pi / L)."""
@@ -96,6 +111,22 @@ def distorted_periodic_grid(n, a):
     xi = np.arange(n) / n
     XI, ETA = np.meshgrid(xi, xi)
     return XI + a * np.sin(2 * math.pi * ETA), ETA + a * np.sin(2 * math.pi * XI)
+
+
+def distorted_periodic_metrics(n, a):
+    """Exact metric coefficients of distorted_periodic_grid(n, a) per unit
+    node index (the computational coordinates step by one per node):
+    xi_x, xi_y, eta_x, eta_y [n, n] from the derivatives of the mapping,
+    x_i = 1/n, x_j = (2 pi a/n) cos(2 pi eta), y_i = (2 pi a/n) cos(2 pi xi),
+    y_j = 1/n, and the inverse of the Jacobian matrix."""
+    xi = np.arange(n) / n
+    XI, ETA = np.meshgrid(xi, xi)
+    x_i = np.full((n, n), 1.0 / n)
+    x_j = (2 * math.pi * a / n) * np.cos(2 * math.pi * ETA)
+    y_i = (2 * math.pi * a / n) * np.cos(2 * math.pi * XI)
+    y_j = np.full((n, n), 1.0 / n)
+    J = x_i * y_j - x_j * y_i
+    return y_j / J, -x_j / J, -y_i / J, x_i / J
 
 
 def periodic_flow_at(X, Y, u0=0.1, nu=0.01):

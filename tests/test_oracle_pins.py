@@ -413,6 +413,37 @@ def test_curvilinear_non_affine_grid_converges_at_second_order():
     assert errs[64] < 2.5 * uniform, (errs, uniform)
 
 
+def test_given_exact_metrics_converge_at_second_order():
+    """Metric coefficients given by the caller (orc_set_metrics): the exact
+    derivatives of the distorted periodic map of the test above.  The
+    periodic flow of Sec. 4.2 then converges at second order from 32^2 to
+    64^2 as with the differenced metrics, to an error of the same size; the
+    same run with the cross terms xi_y, eta_x left out (the metrics of
+    another grid) keeps an O(1) error, so the given values are the ones the
+    step uses."""
+    nu, u0, c, a = 0.01, 0.01, 4.0, 0.06
+
+    def run(n, metrics):
+        X, Y = W.distorted_periodic_grid(n, a)
+        u, v, Fx, Fy = W.periodic_flow_at(X, Y, u0, nu)
+        o = Oracle(n, n, nu=nu, grid="curvilinear", x=X, y=Y, lx=1.0, ly=1.0, c=c, force=(Fx, Fy))
+        if metrics is not None:
+            o.set_metrics(*metrics)
+        z = np.zeros_like(u)
+        o.init(z, z, z)
+        o.step(int(round(8.0 / o.dt)))
+        return gre_vel(o.fields(), u, v)
+
+    errs = {n: run(n, W.distorted_periodic_metrics(n, a)) for n in (32, 64)}
+    order = math.log2(errs[32] / errs[64])
+    assert order > 1.8, (errs, order)
+    differenced = run(64, None)
+    assert errs[64] < 1.5 * differenced, (errs, differenced)
+    xx, xy, ex, ey = W.distorted_periodic_metrics(64, a)
+    wrong = run(64, (xx, 0 * xy, 0 * ex, ey))
+    assert wrong > 20 * errs[64], (wrong, errs)
+
+
 def test_stretched_poiseuille():
     """tanh-clustered nodes across the channel (beta = 1.5)."""
     ny, nx, nu, F = 33, 8, 0.01, 1e-4
