@@ -233,7 +233,10 @@ __device__ __forceinline__ float power_law_nu(float g, const StepArgs &a) {
     // exact at the root, so the step may use the fast approximate quotient
     float l = (lnK + (n - 1.0f) * lng) * a.inv_n;
     l = fminf(fmaxf(l, lmin), lmax);
-#pragma unroll
+    // kept rolled: the call sits in five-fold unrolled marches, and the
+    // unrolled loop's thirty copies cost instruction-cache misses (1 % on
+    // the 512-cavity batch)
+#pragma unroll 1
     for (int it = 0; it < 6; ++it) {
         const float e = __expf(l);
         const float F = l - lnK - (n - 1.0f) * (lng - __logf(e + a.a_pl));
