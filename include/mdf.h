@@ -247,6 +247,17 @@ mdf_status mdf_fields(mdf_ctx *ctx, unsigned mask, float *const *out, int on_dev
  * the previous snapshot (r is then set to NaN). */
 mdf_status mdf_residual(mdf_ctx *ctx, double *residual, double drift[2]);
 
+/* mdf_residual in two halves, so that a march can enqueue its next steps
+ * before it reads the last check: mdf_residual_start enqueues the reductions
+ * of the current state against the snapshot (and takes the new snapshot) on
+ * the context's stream and returns; mdf_residual_finish waits (bounded) for
+ * exactly that work, not for steps enqueued after it, and returns what
+ * mdf_residual would have returned at the start.  One residual may be
+ * pending at a time: a second start, or a finish with none pending, is
+ * MDF_E_STATE. */
+mdf_status mdf_residual_start(mdf_ctx *ctx);
+mdf_status mdf_residual_finish(mdf_ctx *ctx, double *residual, double drift[2]);
+
 /* Copy of the state fhat as FP32 [2][5][ny][nx] (alpha, j, y, x). */
 mdf_status mdf_get_distributions(mdf_ctx *ctx, float *out, int on_device);
 /* Replace the state by `in` (same layout). */

@@ -76,6 +76,8 @@ static void free_ctx(mdf_ctx *c) {
     if (c->h_result) cudaFreeHost(c->h_result);
     for (int p = 0; p < 2; ++p)
         if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
+    if (c->ev_wait) cudaEventDestroy(c->ev_wait);
+    if (c->ev_res) cudaEventDestroy(c->ev_res);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->cstream) cudaStreamDestroy(c->cstream);
@@ -140,35 +142,43 @@ static mdf_status ensure_scratch(mdf_ctx *c, size_t bytes) {
     return MDF_OK;
 }
 
-static mdf_status wait_stream(mdf_ctx *c, double timeout_s) {
+// Bounded host wait for an event recorded on the context's stream.  Polls
+// without sleeping for the first 2 ms (the work behind a residual check of
+// a small grid ends within microseconds, and a sleeping thread wakes tens of
+// microseconds late), then every 20 us up to the limit.
+static mdf_status wait_event(mdf_ctx *c, cudaEvent_t ev, double timeout_s) {
     if (timeout_s <= 0) timeout_s = 60.0;
-    cudaEvent_t ev;
-    CK(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    cudaError_t e = cudaEventRecord(ev, c->stream);
-    if (e != cudaSuccess) {
-        cudaEventDestroy(ev);
-        return fail(c, MDF_E_CUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
-    }
-    auto t0 = std::chrono::steady_clock::now();
+    const auto t0 = std::chrono::steady_clock::now();
     while (true) {
-        e = cudaEventQuery(ev);
-        if (e == cudaSuccess) break;
-        if (e != cudaErrorNotReady) {
-            cudaEventDestroy(ev);
-            return fail(c, MDF_E_CUDA, "stream work failed: %s", cudaGetErrorString(e));
-        }
-        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (el > timeout_s) {
-            cudaEventDestroy(ev);
-            return fail(c, MDF_E_TIMEOUT, "stream did not finish within %.1f s", timeout_s);
-        }
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return MDF_OK;
+        if (e != cudaErrorNotReady) return fail(c, MDF_E_CUDA, "stream work failed: %s", cudaGetErrorString(e));
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) return fail(c, MDF_E_TIMEOUT, "stream did not finish within %.1f s", timeout_s);
+        if (el > 2e-3) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
-    cudaEventDestroy(ev);
-    int h_err = 0;
-    CK(c, cudaMemcpy(&h_err, c->err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (h_err != 0) return fail(c, MDF_E_TIMEOUT, "a bounded device wait gave up (code %d)", h_err);
+}
+
+// The device error word comes back in the same ordered stream as the work,
+// into pinned memory (h_result[6]), so a wait is the only round trip.
+static int *pinned_err(mdf_ctx *c) { return reinterpret_cast<int *>(c->h_result + 6); }
+
+static mdf_status check_device_error(mdf_ctx *c) {
+    const int herr = *pinned_err(c);
+    if (herr != 0) return fail(c, MDF_E_TIMEOUT, "a bounded device wait gave up (code %d)", herr);
     return MDF_OK;
+}
+
+static mdf_status wait_stream(mdf_ctx *c, double timeout_s) {
+    if (!c->ev_wait || !c->h_result || !c->err) {  // part-built context
+        CK(c, cudaStreamSynchronize(c->stream));
+        return MDF_OK;
+    }
+    CK(c, cudaMemcpyAsync(pinned_err(c), c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaEventRecord(c->ev_wait, c->stream));
+    const mdf_status st = wait_event(c, c->ev_wait, timeout_s);
+    if (st != MDF_OK) return st;
+    return check_device_error(c);
 }
 
 // Launch-plan autotuner: time every candidate plan (march block size and
@@ -356,6 +366,8 @@ static mdf_status create_ctx(const mdf_grid *grid, const mdf_fluid *fluid, const
     CKE(cudaMemset(c->err, 0, sizeof(int)));
     CKE(dev_malloc(&c->result, 8 * sizeof(double)));
     CKE(host_malloc(reinterpret_cast<void **>(&c->h_result), 8 * sizeof(double)));
+    CKE(cudaEventCreateWithFlags(&c->ev_wait, cudaEventDisableTiming));
+    CKE(cudaEventCreateWithFlags(&c->ev_res, cudaEventDisableTiming));
 
     AuxArgs &x = c->aux;
     x.nx = c->nx; x.ny = c->ny; x.pitch = c->pitch; x.plane = c->plane;
@@ -797,16 +809,31 @@ mdf_status mdf_fields(mdf_ctx *c, unsigned mask, float *const *out, int on_devic
     return MDF_OK;
 }
 
-mdf_status mdf_residual(mdf_ctx *c, double *residual, double drift[2]) {
+mdf_status mdf_residual_start(mdf_ctx *c) {
     if (!c) return MDF_E_INVALID;
-    MdfRange rr("mdf_residual");
+    if (c->res_pending) return fail(c, MDF_E_STATE, "a residual is already pending (mdf_residual_finish)");
+    MdfRange rr("mdf_residual_start");
     CK(c, aux_residual(c->aux, c->buf[c->cur], c->snap_u, c->snap_v, c->partials, c->result, c->stream));
     CK(c, cudaMemcpyAsync(c->h_result, c->result, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    mdf_status s = wait_stream(c, 0);
+    CK(c, cudaMemcpyAsync(pinned_err(c), c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaEventRecord(c->ev_res, c->stream));
+    c->res_window = c->steps - c->snap_step;
+    c->snap_step = c->steps;
+    c->res_pending = true;
+    return MDF_OK;
+}
+
+mdf_status mdf_residual_finish(mdf_ctx *c, double *residual, double drift[2]) {
+    if (!c) return MDF_E_INVALID;
+    if (!c->res_pending) return fail(c, MDF_E_STATE, "no residual pending (mdf_residual_start)");
+    MdfRange rr("mdf_residual_finish");
+    mdf_status s = wait_event(c, c->ev_res, 0);
+    c->res_pending = false;
+    if (s != MDF_OK) return s;
+    s = check_device_error(c);
     if (s != MDF_OK) return s;
     const double *r = c->h_result;
-    const long long window = c->steps - c->snap_step;
-    c->snap_step = c->steps;
+    const long long window = c->res_window;
     const double val = window > 0 ? sqrt(r[0]) / ((double)window * sqrt(r[1])) : NAN;
     if (residual) *residual = val;
     if (drift) { drift[0] = r[2]; drift[1] = r[3]; }
@@ -814,6 +841,14 @@ mdf_status mdf_residual(mdf_ctx *c, double *residual, double drift[2]) {
         return fail(c, MDF_E_DIVERGED, "non-finite velocity at %.0f nodes", r[4]);
     if (window <= 0) return fail(c, MDF_E_STATE, "no step since the previous residual");
     return MDF_OK;
+}
+
+mdf_status mdf_residual(mdf_ctx *c, double *residual, double drift[2]) {
+    if (!c) return MDF_E_INVALID;
+    MdfRange rr("mdf_residual");
+    const mdf_status s = mdf_residual_start(c);
+    if (s != MDF_OK) return s;
+    return mdf_residual_finish(c, residual, drift);
 }
 
 mdf_status mdf_get_distributions(mdf_ctx *c, float *out, int on_device) {

@@ -43,8 +43,15 @@ struct mdf_ctx {
     double fx = 0, fy = 0;
     float *snap_u = nullptr, *snap_v = nullptr;
     long long snap_step = 0;
+    // h_result: pinned, 8 doubles: [0..4] the residual sums, [6] holds the
+    // copy of the device error word that every host wait brings back
     double *partials = nullptr, *result = nullptr, *h_result = nullptr;
     int *err = nullptr;
+    cudaEvent_t ev_wait = nullptr;  // recorded by every host wait on `stream`
+    // a residual enqueued by mdf_residual_start and not yet collected
+    cudaEvent_t ev_res = nullptr;
+    bool res_pending = false;
+    long long res_window = 0;
     float *scratch = nullptr;  // dense staging for host transfers
     size_t scratch_bytes = 0;
     CUtensorMap tmap[2];

@@ -82,6 +82,8 @@ _SIGNATURES = [
     ("mdf_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("mdf_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
     ("mdf_residual", ctypes.c_int, [ctypes.c_void_p, _D, _D]),
+    ("mdf_residual_start", ctypes.c_int, [ctypes.c_void_p]),
+    ("mdf_residual_finish", ctypes.c_int, [ctypes.c_void_p, _D, _D]),
     ("mdf_get_distributions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("mdf_set_distributions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("mdf_synchronize", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
@@ -395,6 +397,18 @@ class Solver:
         st = lib().mdf_residual(self._h, ctypes.byref(r), d)
         if st not in (MDF_OK,):
             _check(st, self._h)
+        return r.value, (d[0], d[1])
+
+    def residual_start(self):
+        """Enqueue a residual check; collect it with residual_finish()."""
+        _check(lib().mdf_residual_start(self._h), self._h)
+
+    def residual_finish(self):
+        """(r, (sum u, sum v)) of the check residual_start() enqueued; waits
+        for that work only.  Raises MdfError on divergence."""
+        r = ctypes.c_double()
+        d = (ctypes.c_double * 2)()
+        _check(lib().mdf_residual_finish(self._h, ctypes.byref(r), d), self._h)
         return r.value, (d[0], d[1])
 
     def save(self, path):

@@ -98,6 +98,8 @@ def test_null_arguments(lib):
     assert lib.mdf_last_error(None)
     assert lib.mdf_steps_done(None) == -1
     assert lib.mdf_set_metrics(None, None, None, None, None, 0) == mdf.MDF_E_INVALID
+    assert lib.mdf_residual_start(None) == mdf.MDF_E_INVALID
+    assert lib.mdf_residual_finish(None, None, None) == mdf.MDF_E_INVALID
 
 
 def test_creation_errors_are_per_thread(lib):

@@ -233,6 +233,32 @@ def test_residual_and_drift_follow_their_definition():
     assert e.value.status == mdf.MDF_E_STATE
 
 
+def test_residual_in_two_halves_equals_the_synchronous_residual():
+    """mdf_residual_start / _finish with steps enqueued in between return the
+    residual and drift of the state at the start, equal to the bit to
+    mdf_residual on a twin run; the next window is measured from that
+    snapshot; a second start or a finish with none pending is MDF_E_STATE."""
+    n = 33
+    kw = dict(nu=0.01, walls=(True, True), u_wall=(0, 0, 0, 0.1))
+    a, b = mdf.Solver(n, n, **kw), mdf.Solver(n, n, **kw)
+    for s in (a, b):
+        s.init(*W.zeros(n, n))
+        s.step(50)
+    ra = a.residual()
+    b.residual_start()
+    with pytest.raises(mdf.MdfError) as e:
+        b.residual_start()
+    assert e.value.status == mdf.MDF_E_STATE
+    b.step(50)
+    rb = b.residual_finish()
+    assert ra == rb
+    a.step(50)
+    assert a.residual() == b.residual()
+    with pytest.raises(mdf.MdfError) as e:
+        b.residual_finish()
+    assert e.value.status == mdf.MDF_E_STATE
+
+
 def test_divergence_is_reported():
     """Table 2: nu = 1e-3, F = 0.1 on 32 x 32 diverges; the library reports it."""
     n = 32
