@@ -371,14 +371,17 @@ mdf_status mdf_batch_problem(mdf_batch *batch, int index, mdf_ctx **ctx);
 /* info[0] problems, [1] work items, [2] blocks per launch, [3] blocks per
  * SM, [4] nodes in all problems, [5] steps taken. */
 mdf_status mdf_batch_info(const mdf_batch *batch, long long info[6]);
-/* Kernel family of the batch step: 0 marches (work items are strips x bands
- * of each problem), 1 tiles (work items are the 16 x 16 tiles of each
- * problem, the tile kernel of mdf_set_launch).  mdf_batch_create times both
- * and keeps the marches unless the tiles are more than 10 % faster, and
- * mdf_batch_set_active times them again over the problems that remain
- * (FP32 batches); mdf_batch_set_launch fixes the choice for good (waits for
- * the batch's streams; MDF_E_INVALID for another kind).  mdf_batch_launch_kind returns the
- * current one (-1 for NULL). */
+/* Kernel of the batch step: 0 marches (work items are strips x bands of
+ * each problem), 1 tiles (work items are the 16 x 16 tiles of each
+ * problem, the tile kernel of mdf_set_launch), 2 marches in rolled form
+ * (uniform and separable grids: the same values as 0 from a body a fifth
+ * the size, faster on a full GPU, slower on a few small problems).
+ * mdf_batch_create times them and keeps the faster march unless the tiles
+ * are more than 10 % faster, and mdf_batch_set_active times them again over
+ * the problems that remain (FP32 batches); mdf_batch_set_launch fixes the
+ * choice for good (waits for the batch's streams; MDF_E_INVALID for another
+ * kind, a kind that does not fit or does not apply).
+ * mdf_batch_launch_kind returns the current one (-1 for NULL). */
 mdf_status mdf_batch_set_launch(mdf_batch *batch, int kind);
 int mdf_batch_launch_kind(const mdf_batch *batch);
 const char *mdf_batch_last_error(const mdf_batch *batch); /* NULL: this thread's last failed create */

@@ -39,6 +39,7 @@ struct mdf_batch {
     int nt = 0;                                    // block size of the march kernel (strips of nt - 8 columns)
     int nitems = 0, grid = 0, occ = 0, smem = 0;
     int tile = 0, occ_tile = 0, smem_tile = 0;     // tile mode: one work item per 16 x 16 tile
+    int roll = 0;                                  // march mode: the rolled register-window march
     int pinned = 0;                                // mode set by mdf_batch_set_launch (no re-timing)
     int storage = 0;                               // StorageKind of every problem (16-bit: tile mode only)
     int forced = 0;                                // some problem has a force, force rate or source
@@ -136,7 +137,7 @@ static cudaError_t launch_one(mdf_batch *b, int parity, cudaStream_t st) {
         return tile_batch_launch(b->d_items, b->nitems, b->d_args[parity], b->metric, b->power_law, b->walls,
                                  b->storage, b->grid, st);
     return batch_launch(b->d_items, b->nitems, b->d_args[parity], b->d_maps[parity], b->metric, b->power_law,
-                        b->walls, b->grid, b->forced, st);
+                        b->walls, b->grid, b->forced, b->roll, st);
 }
 
 static mdf_status launch_steps(mdf_batch *b, cudaStream_t st, int n) {
@@ -223,21 +224,39 @@ static mdf_status build_items(mdf_batch *b) {
     return MDF_OK;
 }
 
-// Time a few steps of each kernel family over the active problems (their
-// current buffers are read and the other ones written, so the states are
-// unchanged; the batch's streams must be idle) and keep the march unless the
-// tiles are more than 10 % faster.  Run at creation and whenever the active
+// Time a few steps of each kernel over the active problems (their current
+// buffers are read and the other ones written, so the states are unchanged;
+// the batch's streams must be idle): the register-window march unrolled or
+// rolled (the same values; the faster is kept: the rolled one wins on a
+// full GPU, where the unrolled body misses the instruction cache, the
+// unrolled one on a few small problems, where row latency decides), and
+// the tile kernel, kept only when more than 10 % faster than the better
+// march (its last bits differ).  Run at creation and whenever the active
 // set changes: a batch whose remaining problems are few and small steps
 // faster by tiles than by the long serial bands of a march.
 static mdf_status choose_kernel(mdf_batch *b) {
+    struct Mode {
+        int tile, roll;
+    };
+    Mode modes[3];
+    int nm = 0;
+    modes[nm++] = Mode{0, 0};
+    if (b->metric != METRIC_CURVILINEAR) modes[nm++] = Mode{0, 1};
+    if (b->occ_tile >= 1) modes[nm++] = Mode{1, 0};
+    if (nm == 1) {
+        b->tile = 0;
+        b->roll = 0;
+        return build_items(b);
+    }
     cudaEvent_t e0, e1;
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));
-    float best[2] = {1e30f, 1e30f};
+    float best[3] = {1e30f, 1e30f, 1e30f};
     const int parity = b->cur;
     for (int pass = 0; pass < 2; ++pass)
-        for (int k = 0; k < 2; ++k) {
-            b->tile = k;
+        for (int m = 0; m < nm; ++m) {
+            b->tile = modes[m].tile;
+            b->roll = modes[m].roll;
             mdf_status s = build_items(b);
             if (s != MDF_OK) return s;
             BCK(b, launch_one(b, parity, b->stream));
@@ -247,11 +266,17 @@ static mdf_status choose_kernel(mdf_batch *b) {
             BCK(b, cudaEventSynchronize(e1));
             float ms = 0.0f;
             BCK(b, cudaEventElapsedTime(&ms, e0, e1));
-            best[k] = std::min(best[k], ms);
+            best[m] = std::min(best[m], ms);
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->tile = best[1] < 0.9f * best[0] ? 1 : 0;
+    int pick = 0;
+    for (int m = 1; m < nm; ++m)
+        if (!modes[m].tile && best[m] < best[pick]) pick = m;
+    for (int m = 1; m < nm; ++m)
+        if (modes[m].tile && best[m] < 0.9f * best[pick]) pick = m;
+    b->tile = modes[pick].tile;
+    b->roll = modes[pick].roll;
     return build_items(b);
 }
 
@@ -339,7 +364,7 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
         if (b->occ_tile < 1) BCKC(bfail(b, MDF_E_INVALID, "the tile kernel does not fit"));
         b->tile = 1;
         BCKC(build_items(b));
-    } else if (b->occ_tile >= 1) {
+    } else {
         BCKC(choose_kernel(b));
     }
     BCKE(cudaMallocHost(&b->h_res, (size_t)count * 5 * sizeof(double)));
@@ -446,7 +471,7 @@ mdf_status mdf_batch_set_active(mdf_batch *b, int index, int active) {
     if (s != MDF_OK) return s;
     s = upload_args(b);
     if (s != MDF_OK) return s;
-    if (!b->pinned && b->storage == MDF_STORAGE_FP32 && b->occ_tile >= 1 && b->nitems > 0) s = choose_kernel(b);
+    if (!b->pinned && b->storage == MDF_STORAGE_FP32 && b->nitems > 0) s = choose_kernel(b);
     return s;
 }
 
@@ -495,18 +520,22 @@ mdf_status mdf_batch_info(const mdf_batch *b, long long info[6]) {
 
 mdf_status mdf_batch_set_launch(mdf_batch *b, int kind) {
     if (!b) return MDF_E_INVALID;
-    if (kind != 0 && kind != 1) return bfail(b, MDF_E_INVALID, "kind must be 0 (march) or 1 (tile)");
+    if (kind < 0 || kind > 2)
+        return bfail(b, MDF_E_INVALID, "kind must be 0 (march), 1 (tile) or 2 (rolled march)");
     if (kind == 1 && b->occ_tile < 1) return bfail(b, MDF_E_INVALID, "the tile kernel does not fit");
-    if (kind == 0 && b->storage != MDF_STORAGE_FP32)
+    if (kind != 1 && b->storage != MDF_STORAGE_FP32)
         return bfail(b, MDF_E_INVALID, "the marches of a batch keep FP32 storage");
+    if (kind == 2 && b->metric == METRIC_CURVILINEAR)
+        return bfail(b, MDF_E_INVALID, "the rolled march serves uniform and separable grids");
     BCK(b, cudaStreamSynchronize(b->stream));
     BCK(b, cudaStreamSynchronize(b->cstream));
-    b->tile = kind;
+    b->tile = kind == 1 ? 1 : 0;
+    b->roll = kind == 2 ? 1 : 0;
     b->pinned = 1;
     return build_items(b);
 }
 
-int mdf_batch_launch_kind(const mdf_batch *b) { return b ? b->tile : -1; }
+int mdf_batch_launch_kind(const mdf_batch *b) { return b ? (b->tile ? 1 : (b->roll ? 2 : 0)) : -1; }
 
 const char *mdf_batch_last_error(const mdf_batch *b) { return b ? b->last_error : g_batch_error; }
 

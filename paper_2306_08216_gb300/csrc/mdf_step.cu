@@ -122,9 +122,9 @@ cudaError_t batch_occupancy(int metric, int power_law, int walls, int *nt, int *
 }
 
 cudaError_t batch_launch(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps, int metric,
-                         int power_law, int walls, int grid, int forced, cudaStream_t stream) {
+                         int power_law, int walls, int grid, int forced, int roll, cudaStream_t stream) {
     if (metric != METRIC_CURVILINEAR)
-        return walls_batch_launch(items, nitems, args, maps, metric, power_law, grid, forced, stream);
+        return walls_batch_launch(items, nitems, args, maps, metric, power_law, grid, forced, roll, stream);
     MDF_CURVI_DISPATCH(batch_launch_t, items, nitems, args, maps, grid, stream)
 }
 

@@ -23,6 +23,9 @@
 // thread of the adjacent interior column), pops 2 and 4 of a wall row to the
 // register window of the same column (south: when row 1 is formed; north:
 // from row ny-2 through a one-row shared buffer, one iteration later).
+#include <algorithm>
+#include <type_traits>
+
 #include "mdf_device.cuh"
 
 namespace mdf {
@@ -62,6 +65,25 @@ __device__ __forceinline__ F2 force_d(const StepArgs &a, int row, int X, F2 fact
     return factor * mk2(a.Fxdp[fi], a.Fydp[fi]);
 }
 
+// Rotate a register window by one row for the rolled march.  Its window
+// slots follow the slot formula of the unrolled march with the slot of the
+// newest row p fixed at 0: row p - a sits in slot (5 - a) mod 5 (row p - 1 in
+// slot 4, ..., row p - 4 in slot 1, and slot 0 before the write of row p
+// still holds row p - 5).  Advancing p moves every row to the slot below it
+// (modulo 5): new[i] = old[(i + 1) mod 5].
+template <typename T, int N>
+__device__ __forceinline__ void rot5(T (&w)[5][N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const T w0 = w[0][i];
+        w[0][i] = w[1][i];
+        w[1][i] = w[2][i];
+        w[2][i] = w[3][i];
+        w[3][i] = w[4][i];
+        w[4][i] = w0;
+    }
+}
+
 template <int NT>
 constexpr int walls_smem() {
     return TMA_SLOTS * NPLANES * NT * 4 + RING * 5 * NT * 8 + 4 * (2 * NT * 8) + 2 * NT * 8 + TMA_SLOTS * 8;
@@ -69,7 +91,12 @@ constexpr int walls_smem() {
 
 // One block's march over strip bx, band by.  FORCED: body force, force rate
 // or source present (read at run time); otherwise those terms are compiled out.
-template <int NT, int MK, bool PL, bool FORCED>
+// ROLL: the march loop is not unrolled and the register windows rotate by
+// one row per iteration (rot5); otherwise it is unrolled by five and every
+// window slot is a compile-time index.  The two compute the same values; the
+// rolled body is a fifth of the size (fewer instruction-cache misses on a
+// full GPU), the unrolled one has the shorter row latency (small batches).
+template <int NT, int MK, bool PL, bool FORCED, bool ROLL>
 __device__ __forceinline__ void march_walls(const CUtensorMap *tmap, const StepArgs &a, int bx, int by,
                                             unsigned char *smem, int *abort_flag) {
     constexpr int TROW = NPLANES * NT * 4;  // one TMA row: 10 FP32 planes
@@ -139,13 +166,14 @@ __device__ __forceinline__ void march_walls(const CUtensorMap *tmap, const StepA
 
     int tslot = 0;
     bool aborted = false;
-    for (int it0 = 0; it0 < nIt && !aborted; it0 += 5) {
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const int it = it0 + k;
-            if (it >= nIt) break;
+    // One row iteration: window slot K of row p (and of row p - 5 before its
+    // write), slots s1..s4 of rows p-1..p-4, row ps of the fhat^+ ring.
+    // Returns false when the block aborts.
+    auto row = [&](const int it, auto kc, const int ps) -> bool {
+        constexpr int k = decltype(kc)::value;
+        constexpr int s1 = (k + 4) % 5, s2 = (k + 3) % 5, s3 = (k + 2) % 5, s4 = (k + 1) % 5;
+        {
             const int p = rowBase + it;
-            const int s1 = (k + 4) % 5, s2 = (k + 3) % 5, s3 = (k + 2) % 5, s4 = (k + 1) % 5;
             unsigned char *xB = xB0 + (it & 1) * XROW;
             const unsigned char *xFp = xF0 + ((it & 1) ^ 1) * XROW;
             unsigned char *xF = xF0 + (it & 1) * XROW;
@@ -153,7 +181,7 @@ __device__ __forceinline__ void march_walls(const CUtensorMap *tmap, const StepA
             if (it >= 9 && outc) {
                 const int r = p - 5;  // in [y0, y1): a row of the domain
                 if (!(ywall && (r == 0 || r == a.ny - 1))) {
-                    const unsigned char *Pr = ringP + k * PROW;
+                    const unsigned char *Pr = ringP + ps * PROW;
                     F2 out[5];
 #pragma unroll
                     for (int j = 0; j < 5; ++j) out[j] = lds2(Pr, (j * NT + t) * 8);
@@ -219,7 +247,7 @@ __device__ __forceinline__ void march_walls(const CUtensorMap *tmap, const StepA
                     RK[k][1] = Rr.rk;
                 }
                 relax2(g, n, n13, n24, mKp, Dp, o);
-                unsigned char *dP = ringP + k * PROW;
+                unsigned char *dP = ringP + ps * PROW;
 #pragma unroll
                 for (int j = 0; j < 5; ++j) sts2(dP, (j * NT + t) * 8, o[j]);
                 relax2(g, n, n13, n24, mKb, Db, o);
@@ -232,10 +260,7 @@ __device__ __forceinline__ void march_walls(const CUtensorMap *tmap, const StepA
                 D013[k][0] = o[0];
             }
             // one barrier per row (exchange rows double-buffered by row parity)
-            if (__syncthreads_or(s_abort)) {
-                aborted = true;
-                break;
-            }
+            if (__syncthreads_or(s_abort)) return false;
             if (t == 0 && issued < nIt) {
                 fence_proxy_async();
                 load_row(issued, tslot);
@@ -323,7 +348,38 @@ __device__ __forceinline__ void march_walls(const CUtensorMap *tmap, const StepA
                 }
             }
         }
+        return true;
+    };
+    using std::integral_constant;
+    if (ROLL) {
+        int pslot = 0;  // it mod 5
+#pragma unroll 1
+        for (int it = 0; it < nIt; ++it) {
+            if (!row(it, integral_constant<int, 0>{}, pslot)) {
+                aborted = true;
+                break;
+            }
+            rot5(BY);
+            rot5(D013);
+            rot5(FY);
+            rot5(XF);
+            rot5(RK);
+            pslot = pslot == 4 ? 0 : pslot + 1;
+        }
+    } else {
+        for (int it0 = 0; it0 < nIt && !aborted; it0 += 5) {
+            if (!row(it0, integral_constant<int, 0>{}, 0)) { aborted = true; break; }
+            if (it0 + 1 >= nIt) break;
+            if (!row(it0 + 1, integral_constant<int, 1>{}, 1)) { aborted = true; break; }
+            if (it0 + 2 >= nIt) break;
+            if (!row(it0 + 2, integral_constant<int, 2>{}, 2)) { aborted = true; break; }
+            if (it0 + 3 >= nIt) break;
+            if (!row(it0 + 3, integral_constant<int, 3>{}, 3)) { aborted = true; break; }
+            if (it0 + 4 >= nIt) break;
+            if (!row(it0 + 4, integral_constant<int, 4>{}, 4)) { aborted = true; break; }
+        }
     }
+    (void)aborted;
     if (s_abort) {
         if (t == 0) {
             for (int it = issued - TMA_SLOTS; it < issued; ++it) {
@@ -353,12 +409,13 @@ __global__ void __launch_bounds__(NT, walls_min_blocks<NT>())
     walls_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_abort;
-    march_walls<NT, MK, PL, FORCED>(&tmap, a, blockIdx.x, blockIdx.y, smem, &s_abort);
+    march_walls<NT, MK, PL, FORCED, false>(&tmap, a, blockIdx.x, blockIdx.y, smem, &s_abort);
 }
 
 // Persistent batch form: block b takes work items b, b + gridDim.x, ...
-// FORCED if any problem of the batch has a force, force rate or source.
-template <int NT, int MK, bool PL, bool FORCED>
+// FORCED if any problem of the batch has a force, force rate or source;
+// ROLL selects the rolled march (see march_walls).
+template <int NT, int MK, bool PL, bool FORCED, bool ROLL>
 __global__ void __launch_bounds__(NT, walls_min_blocks<NT>())
     walls_batch_kernel(const BatchItem *__restrict__ items, int nitems, const StepArgs *__restrict__ args,
                        const CUtensorMap *__restrict__ maps) {
@@ -366,7 +423,8 @@ __global__ void __launch_bounds__(NT, walls_min_blocks<NT>())
     __shared__ int s_abort;
     for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
         const BatchItem item = items[w];
-        march_walls<NT, MK, PL, FORCED>(&maps[item.problem], args[item.problem], item.bx, item.by, smem, &s_abort);
+        march_walls<NT, MK, PL, FORCED, ROLL>(&maps[item.problem], args[item.problem], item.bx, item.by, smem,
+                                              &s_abort);
         if (s_abort) break;
     }
 }
@@ -398,10 +456,10 @@ cudaError_t occupancy_t(int *occ, int *smem) {
     return e;
 }
 
-template <int NT, int MK, bool PL, bool FORCED>
+template <int NT, int MK, bool PL, bool FORCED, bool ROLL>
 cudaError_t batch_launch_ft(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps,
                             int grid, cudaStream_t stream) {
-    auto k = walls_batch_kernel<NT, MK, PL, FORCED>;
+    auto k = walls_batch_kernel<NT, MK, PL, FORCED, ROLL>;
     static std::atomic<unsigned long long> configured{0};  // devices set up
     if (needs_device_setup(configured)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, walls_smem<NT>());
@@ -414,26 +472,34 @@ cudaError_t batch_launch_ft(const BatchItem *items, int nitems, const StepArgs *
 
 template <int NT, int MK, bool PL>
 cudaError_t batch_launch_t(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps, int grid,
-                           int forced, cudaStream_t stream) {
-    if (forced) return batch_launch_ft<NT, MK, PL, true>(items, nitems, args, maps, grid, stream);
-    return batch_launch_ft<NT, MK, PL, false>(items, nitems, args, maps, grid, stream);
+                           int forced, int roll, cudaStream_t stream) {
+    if (forced) {
+        if (roll) return batch_launch_ft<NT, MK, PL, true, true>(items, nitems, args, maps, grid, stream);
+        return batch_launch_ft<NT, MK, PL, true, false>(items, nitems, args, maps, grid, stream);
+    }
+    if (roll) return batch_launch_ft<NT, MK, PL, false, true>(items, nitems, args, maps, grid, stream);
+    return batch_launch_ft<NT, MK, PL, false, false>(items, nitems, args, maps, grid, stream);
+}
+
+// Occupancy of one batch kernel variant.
+template <int NT, int MK, bool PL, bool FORCED, bool ROLL>
+cudaError_t batch_occupancy_v(int smem, int *occ) {
+    auto k = walls_batch_kernel<NT, MK, PL, FORCED, ROLL>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, NT, smem);
+    return e;
 }
 
 template <int NT, int MK, bool PL>
 cudaError_t batch_occupancy_t(int *occ, int *smem) {
-    // both force variants have the same shared memory; take the smaller occupancy
-    int o1 = 0, o2 = 0;
+    // every variant has the same shared memory; take the smallest occupancy
+    int o[4] = {0, 0, 0, 0};
     *smem = walls_smem<NT>();
-    cudaError_t e = cudaFuncSetAttribute(walls_batch_kernel<NT, MK, PL, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(walls_batch_kernel<NT, MK, PL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 *smem);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, walls_batch_kernel<NT, MK, PL, false>, NT, *smem);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, walls_batch_kernel<NT, MK, PL, true>, NT, *smem);
-    *occ = o1 < o2 ? o1 : o2;
+    cudaError_t e = batch_occupancy_v<NT, MK, PL, false, false>(*smem, &o[0]);
+    if (e == cudaSuccess) e = batch_occupancy_v<NT, MK, PL, true, false>(*smem, &o[1]);
+    if (e == cudaSuccess) e = batch_occupancy_v<NT, MK, PL, false, true>(*smem, &o[2]);
+    if (e == cudaSuccess) e = batch_occupancy_v<NT, MK, PL, true, true>(*smem, &o[3]);
+    *occ = std::min(std::min(o[0], o[1]), std::min(o[2], o[3]));
     return e;
 }
 
@@ -488,8 +554,8 @@ cudaError_t walls_batch_occupancy(int metric, int power_law, int *nt, int *occ, 
 }
 
 cudaError_t walls_batch_launch(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps,
-                               int metric, int power_law, int grid, int forced, cudaStream_t stream) {
-    MDF_WALLS_DISPATCH(kWallsBatchNT, batch_launch_t, items, nitems, args, maps, grid, forced, stream)
+                               int metric, int power_law, int grid, int forced, int roll, cudaStream_t stream) {
+    MDF_WALLS_DISPATCH(kWallsBatchNT, batch_launch_t, items, nitems, args, maps, grid, forced, roll, stream)
 }
 
 }  // namespace mdf

@@ -527,9 +527,10 @@ class Batch:
         v = (ctypes.c_longlong * 6)()
         self._chk(lib().mdf_batch_info(self._h, v))
         d = dict(zip(["problems", "work_items", "blocks", "blocks_per_sm", "nodes", "steps"], list(v)))
-        d["kernel"] = "tile" if lib().mdf_batch_launch_kind(self._h) == 1 else "march"
+        d["kernel"] = {0: "march", 1: "tile", 2: "march_rolled"}[lib().mdf_batch_launch_kind(self._h)]
         return d
 
     def set_launch(self, kernel):
-        """kernel: "march" (strips x bands per problem) or "tile" (16 x 16 tiles)."""
-        self._chk(lib().mdf_batch_set_launch(self._h, {"march": 0, "tile": 1}[kernel]))
+        """kernel: "march" (strips x bands per problem), "march_rolled" (the same
+        march in rolled form) or "tile" (16 x 16 tiles)."""
+        self._chk(lib().mdf_batch_set_launch(self._h, {"march": 0, "tile": 1, "march_rolled": 2}[kernel]))

@@ -32,10 +32,12 @@ def cavity(n, re, n_index=None, u0=0.1, m=None):
     return kw
 
 
-SOLO_PLAN = {"march": (128, 8), "tile": (0, 0)}  # the single-problem plan each batch kernel shares
+# the single-problem plan each batch kernel shares its values with (the
+# rolled march computes what the unrolled one does)
+SOLO_PLAN = {"march": (128, 8), "march_rolled": (128, 8), "tile": (0, 0)}
 
 
-@pytest.mark.parametrize("kernel", ["march", "tile"])
+@pytest.mark.parametrize("kernel", ["march", "march_rolled", "tile"])
 def test_batch_of_power_law_cavities_equals_solo_runs_bitwise(kernel):
     probs = [cavity(65, 400, 0.6), cavity(33, 100, 1.0), cavity(47, 250, 1.4, m=39), cavity(130, 1000, 0.9)]
     batch = mdf.Batch(probs)
@@ -118,7 +120,7 @@ def _solo_state(kw, steps, kernel):
     return solo.state()
 
 
-@pytest.mark.parametrize("kernel", ["march", "tile"])
+@pytest.mark.parametrize("kernel", ["march", "march_rolled", "tile"])
 def test_retired_problems_freeze_and_resume_bitwise(kernel):
     """A retired problem keeps its state while the others advance; re-admitted
     after an odd number of batch steps (its buffers swap roles), it continues
@@ -144,3 +146,13 @@ def test_retired_problems_freeze_and_resume_bitwise(kernel):
         batch.set_active(i, False)
     batch.step(10)  # nothing left to step
     np.testing.assert_array_equal(batch.problem(2).state(), _solo(probs[2], 92))
+
+
+def test_rolled_march_rejected_on_curvilinear_batches():
+    X, Y = W.trapezoid_grid(33, 33)
+    batch = mdf.Batch([dict(nx=33, ny=33, nu=0.01, grid="curvilinear", x=X, y=Y, walls=(True, True),
+                            u_wall=(0, 0, 0, 0.1))])
+    with pytest.raises(mdf.MdfError) as e:
+        batch.set_launch("march_rolled")
+    assert e.value.status == mdf.MDF_E_INVALID
+    assert batch.info()["kernel"] in ("march", "tile")

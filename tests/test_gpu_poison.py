@@ -70,7 +70,7 @@ def test_poisoned_storage_is_never_read(name):
             np.testing.assert_array_equal(a, b, err_msg="%s %s" % (name, plan))
 
 
-@pytest.mark.parametrize("kernel", ["march", "tile"])
+@pytest.mark.parametrize("kernel", ["march", "march_rolled", "tile"])
 def test_poisoned_batch(kernel):
     probs = [dict(nx=n, ny=n, nu=0.004, **LID, **PL) for n in (45, 33, 70)]
     states = []
