@@ -311,6 +311,25 @@ __device__ __forceinline__ float stream1(float base, float pf, float p0, float p
     return fmaf(w1, pf - pb1, fmaf(w0, d0, fmaf(w2, dfar, base)));
 }
 
+// Rotate a register window by one row for a rolled march (the register-
+// window marches that keep their loop rolled).  Its window slots follow the slot formula of the unrolled march with the slot of the
+// newest row p fixed at 0: row p - a sits in slot (5 - a) mod 5 (row p - 1 in
+// slot 4, ..., row p - 4 in slot 1, and slot 0 before the write of row p
+// still holds row p - 5).  Advancing p moves every row to the slot below it
+// (modulo 5): new[i] = old[(i + 1) mod 5].
+template <typename T, int N>
+__device__ __forceinline__ void rot5(T (&w)[5][N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const T w0 = w[0][i];
+        w[0][i] = w[1][i];
+        w[1][i] = w[2][i];
+        w[2][i] = w[3][i];
+        w[3][i] = w[4][i];
+        w[4][i] = w0;
+    }
+}
+
 __device__ __forceinline__ int wrap(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;

@@ -30,6 +30,8 @@
 // in S3 with the u, v of the alpha = 1, 2 fbar of its node; streamed in S0;
 // source w_j R in both streaming steps (Eq. 2.1.2 with ubar_0 = rho_0,
 // E_0 = 0).  Nothing of it flows back into alpha = 1, 2 (Remark 1).
+#include <type_traits>
+
 #include "mdf_device.cuh"
 
 namespace mdf {
@@ -174,14 +176,14 @@ __global__ void __launch_bounds__(NT, RHO0 ? 3 : (NT <= 128 ? 4 : 2))
 
     int tslot = 0;
     bool aborted = false;
-    for (int it0 = 0; it0 < nIt && !aborted; it0 += 5) {
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const int it = it0 + k;
-            if (it >= nIt) break;
+    // One row iteration: window slot k of row p (row p-5 shares it), slots
+    // s1..s4 of rows p-1 .. p-4, row ps of the fhat^+ rings.  Returns false
+    // when the block aborts.
+    auto row = [&](const int it, auto kc, const int ps) -> bool {
+        constexpr int k = decltype(kc)::value;
+        constexpr int s1 = (k + 4) % 5, s2 = (k + 3) % 5, s3 = (k + 2) % 5, s4 = (k + 1) % 5;
+        {
             const int p = rowBase + it;
-            // slots of rows p-1 .. p-4 (row p-5 shares slot k with row p)
-            const int s1 = (k + 4) % 5, s2 = (k + 3) % 5, s3 = (k + 2) % 5, s4 = (k + 1) % 5;
             // exchange buffers of this iteration (fbar^+) and of the previous one (f)
             unsigned char *xB = xB0 + (it & 1) * XROW;
             const unsigned char *xFp = xF0 + ((it & 1) ^ 1) * XROW;
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(NT, RHO0 ? 3 : (NT <= 128 ? 4 : 2))
             if (it >= 9 && outc) {
                 // slot k of every window and of the ring holds row r
                 const int r = p - 5;
-                const unsigned char *Pr = ringP + k * PROW;
+                const unsigned char *Pr = ringP + ps * PROW;
                 F2 out[5];
 #pragma unroll
                 for (int j = 0; j < 5; ++j) out[j] = lds2(Pr, (j * NT + t) * 8);
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(NT, RHO0 ? 3 : (NT <= 128 ? 4 : 2))
                 else store_node_dev<ST, true>(a, r, X, out);
                 if (RHO0) {
                     // Step 4 on alpha = 0: fhat^+ - dt c.grad f + dt w_j R
-                    const unsigned char *P0r = ringP0 + k * P0ROW;
+                    const unsigned char *P0r = ringP0 + ps * P0ROW;
                     float out0[5];
 #pragma unroll
                     for (int j = 0; j < 5; ++j) out0[j] = lds1(P0r, (j * NT + t) * 4);
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(NT, RHO0 ? 3 : (NT <= 128 ? 4 : 2))
                         for (int j = 0; j < 5; ++j) g0[j] = src[(NPLANES + j) * NT + t];
                         noneq0(g0, m.u, m.v, inv2c, n0);
                         relax0(g0, n0, mKp0, Dp0, q0);
-                        unsigned char *dP0 = ringP0 + k * P0ROW;
+                        unsigned char *dP0 = ringP0 + ps * P0ROW;
 #pragma unroll
                         for (int j = 0; j < 5; ++j) sts1(dP0, (j * NT + t) * 4, q0[j]);
                         relax0(g0, n0, mKb0, Db0, q0);
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(NT, RHO0 ? 3 : (NT <= 128 ? 4 : 2))
                 }
                 const F2 n13 = n[1] - n[3], n24 = n[2] - n[4];
                 relax2(g, n, n13, n24, pair_of(a.pmKp), pair_of(a.pDp), o);
-                unsigned char *dP = ringP + k * PROW;
+                unsigned char *dP = ringP + ps * PROW;
 #pragma unroll
                 for (int j = 0; j < 5; ++j) sts2(dP, (j * NT + t) * 8, o[j]);
                 relax2(g, n, n13, n24, pair_of(a.pmKb), pair_of(a.pDb), o);
@@ -296,10 +298,7 @@ __global__ void __launch_bounds__(NT, RHO0 ? 3 : (NT <= 128 ? 4 : 2))
             // One barrier per row: the exchange rows are double-buffered, so
             // the buffers written before this barrier are read only after it,
             // and those read after it are rewritten only after the next one.
-            if (__syncthreads_or(s_abort)) {
-                aborted = true;
-                break;
-            }
+            if (__syncthreads_or(s_abort)) return false;
             if (t == 0 && issued < nIt) {
                 fence_proxy_async();
                 load_row(issued, tslot);
@@ -406,7 +405,25 @@ __global__ void __launch_bounds__(NT, RHO0 ? 3 : (NT <= 128 ? 4 : 2))
                 }
             }
         }
+        return true;
+    };
+    // The march, unrolled by five so that every window slot is a
+    // compile-time index.  (A rolled form whose windows rotate by one row,
+    // as the batched wall march has, measured 3.5 % slower on the alpha = 0
+    // variant at 4096^2.)
+    using std::integral_constant;
+    for (int it0 = 0; it0 < nIt && !aborted; it0 += 5) {
+        if (!row(it0, integral_constant<int, 0>{}, 0)) { aborted = true; break; }
+        if (it0 + 1 >= nIt) break;
+        if (!row(it0 + 1, integral_constant<int, 1>{}, 1)) { aborted = true; break; }
+        if (it0 + 2 >= nIt) break;
+        if (!row(it0 + 2, integral_constant<int, 2>{}, 2)) { aborted = true; break; }
+        if (it0 + 3 >= nIt) break;
+        if (!row(it0 + 3, integral_constant<int, 3>{}, 3)) { aborted = true; break; }
+        if (it0 + 4 >= nIt) break;
+        if (!row(it0 + 4, integral_constant<int, 4>{}, 4)) { aborted = true; break; }
     }
+    (void)aborted;
     if (s_abort) {
         if (t == 0) {
             for (int it = issued - SLOTS; it < issued; ++it) {

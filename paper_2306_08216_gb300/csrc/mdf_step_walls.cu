@@ -65,25 +65,6 @@ __device__ __forceinline__ F2 force_d(const StepArgs &a, int row, int X, F2 fact
     return factor * mk2(a.Fxdp[fi], a.Fydp[fi]);
 }
 
-// Rotate a register window by one row for the rolled march.  Its window
-// slots follow the slot formula of the unrolled march with the slot of the
-// newest row p fixed at 0: row p - a sits in slot (5 - a) mod 5 (row p - 1 in
-// slot 4, ..., row p - 4 in slot 1, and slot 0 before the write of row p
-// still holds row p - 5).  Advancing p moves every row to the slot below it
-// (modulo 5): new[i] = old[(i + 1) mod 5].
-template <typename T, int N>
-__device__ __forceinline__ void rot5(T (&w)[5][N]) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-        const T w0 = w[0][i];
-        w[0][i] = w[1][i];
-        w[1][i] = w[2][i];
-        w[2][i] = w[3][i];
-        w[3][i] = w[4][i];
-        w[4][i] = w0;
-    }
-}
-
 template <int NT>
 constexpr int walls_smem() {
     return TMA_SLOTS * NPLANES * NT * 4 + RING * 5 * NT * 8 + 4 * (2 * NT * 8) + 2 * NT * 8 + TMA_SLOTS * 8;
