@@ -175,6 +175,12 @@ def test_batch_rejects_rho0(lib):
     assert b"rho_0" in lib.mdf_batch_last_error(None)
 
 
+def test_empty_batch_rejected(lib):
+    h = ctypes.c_void_p()
+    assert lib.mdf_batch_create(0, None, None, None, None, ctypes.byref(h)) == mdf.MDF_E_INVALID
+    assert b"count" in lib.mdf_batch_last_error(None)
+
+
 def test_launch_kind_calls_reject_null(lib):
     assert lib.mdf_launch_kind(None) == -1
     assert lib.mdf_batch_launch_kind(None) == -1

@@ -75,6 +75,30 @@ def test_small_and_ragged_grids(nx, ny, walls):
     assert maxabs(sg, so) <= 2e-6 * U
 
 
+def test_zero_and_negative_step_counts():
+    """mdf_step(0) changes nothing and mdf_step(-1) is MDF_E_INVALID with the
+    state untouched; a batch behaves the same."""
+    g = mdf.Solver(20, 20, nu=0.01, walls=(True, True), u_wall=(0, 0, 0, 0.1))
+    g.init(*W.zeros(20, 20))
+    g.step(7)
+    s0 = g.state()
+    g.step(0)
+    np.testing.assert_array_equal(g.state(), s0)
+    with pytest.raises(mdf.MdfError) as e:
+        g.step(-1)
+    assert e.value.status == mdf.MDF_E_INVALID
+    np.testing.assert_array_equal(g.state(), s0)
+    assert g.steps == 7
+    b = mdf.Batch([dict(nx=20, ny=20, nu=0.01, walls=(True, True), u_wall=(0, 0, 0, 0.1))])
+    b.step(3)
+    t0 = b.problem(0).state()
+    b.step(0)
+    np.testing.assert_array_equal(b.problem(0).state(), t0)
+    with pytest.raises(mdf.MdfError):
+        b.step(-2)
+    assert b.info()["steps"] == 3
+
+
 def test_set_state_roundtrip_and_single_step():
     nx, ny = 70, 33
     g, o = pair(nx, ny, nu=0.01, lx=1.3, ly=1.0)
