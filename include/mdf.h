@@ -342,7 +342,9 @@ typedef struct mdf_batch mdf_batch;
  * Each problem starts at rest.  MDF_E_INVALID if the problems cannot share
  * one kernel variant, any problem is invalid (see mdf_create), the storage
  * modes differ or a problem asks for the alpha = 0 distribution.  A batch in
- * 16-bit storage steps in tile mode (see mdf_batch_set_launch). */
+ * 16-bit storage steps with the rolled march or the tile kernel on uniform
+ * and separable grids, with the tile kernel on curvilinear ones (see
+ * mdf_batch_set_launch). */
 mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *fluids, const mdf_bc *bcs,
                             const mdf_params *params, mdf_batch **out);
 void mdf_batch_destroy(mdf_batch *batch);
@@ -375,7 +377,8 @@ mdf_status mdf_batch_info(const mdf_batch *batch, long long info[6]);
  * each problem), 1 tiles (work items are the 16 x 16 tiles of each
  * problem, the tile kernel of mdf_set_launch), 2 marches in rolled form
  * (uniform and separable grids: the same values as 0 from a body a fifth
- * the size, faster on a full GPU, slower on a few small problems).
+ * the size, faster on a full GPU, slower on a few small problems; the only
+ * march form with 16-bit storage).
  * mdf_batch_create times them and keeps the faster march unless the tiles
  * are more than 10 % faster, and mdf_batch_set_active times them again over
  * the problems that remain (FP32 batches); mdf_batch_set_launch fixes the

@@ -137,7 +137,7 @@ static cudaError_t launch_one(mdf_batch *b, int parity, cudaStream_t st) {
         return tile_batch_launch(b->d_items, b->nitems, b->d_args[parity], b->metric, b->power_law, b->walls,
                                  b->storage, b->grid, st);
     return batch_launch(b->d_items, b->nitems, b->d_args[parity], b->d_maps[parity], b->metric, b->power_law,
-                        b->walls, b->grid, b->forced, b->roll, st);
+                        b->walls, b->grid, b->forced, b->roll, b->storage, st);
 }
 
 static mdf_status launch_steps(mdf_batch *b, cudaStream_t st, int n) {
@@ -240,12 +240,13 @@ static mdf_status choose_kernel(mdf_batch *b) {
     };
     Mode modes[3];
     int nm = 0;
-    modes[nm++] = Mode{0, 0};
+    if (b->storage == MDF_STORAGE_FP32) modes[nm++] = Mode{0, 0};
     if (b->metric != METRIC_CURVILINEAR) modes[nm++] = Mode{0, 1};
     if (b->occ_tile >= 1) modes[nm++] = Mode{1, 0};
+    if (nm == 0) return bfail(b, MDF_E_INVALID, "no batch kernel serves this problem set");
     if (nm == 1) {
-        b->tile = 0;
-        b->roll = 0;
+        b->tile = modes[0].tile;
+        b->roll = modes[0].roll;
         return build_items(b);
     }
     cudaEvent_t e0, e1;
@@ -270,11 +271,13 @@ static mdf_status choose_kernel(mdf_batch *b) {
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int pick = 0;
-    for (int m = 1; m < nm; ++m)
-        if (!modes[m].tile && best[m] < best[pick]) pick = m;
-    for (int m = 1; m < nm; ++m)
-        if (modes[m].tile && best[m] < 0.9f * best[pick]) pick = m;
+    // the better march, then the tiles if more than 10 % faster than it (or
+    // the tiles alone)
+    int pick = -1;
+    for (int m = 0; m < nm; ++m)
+        if (!modes[m].tile && (pick < 0 || best[m] < best[pick])) pick = m;
+    for (int m = 0; m < nm; ++m)
+        if (modes[m].tile && (pick < 0 || best[m] < 0.9f * best[pick])) pick = m;
     b->tile = modes[pick].tile;
     b->roll = modes[pick].roll;
     return build_items(b);
@@ -342,7 +345,7 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
         b->nodes += (long long)c->nx * c->ny;
     }
     int num_sms = 0, dev = 0;
-    BCKE(batch_occupancy(metric, power_law, walls, &b->nt, &b->occ, &b->smem));
+    BCKE(batch_occupancy(metric, power_law, walls, storage, &b->nt, &b->occ, &b->smem));
     BCKE(cudaGetDevice(&dev));
     BCKE(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
     b->num_sms = num_sms;
@@ -359,8 +362,8 @@ mdf_status mdf_batch_create(int count, const mdf_grid *grids, const mdf_fluid *f
     }
     BCKC(upload_args(b));
     BCKE(tile_batch_occupancy(metric, power_law, walls, storage, &b->occ_tile, &b->smem_tile));
-    if (storage != MDF_STORAGE_FP32) {
-        // the marches of a batch keep FP32 storage
+    if (storage != MDF_STORAGE_FP32 && metric == METRIC_CURVILINEAR) {
+        // the curvilinear march keeps FP32 storage
         if (b->occ_tile < 1) BCKC(bfail(b, MDF_E_INVALID, "the tile kernel does not fit"));
         b->tile = 1;
         BCKC(build_items(b));
@@ -471,7 +474,8 @@ mdf_status mdf_batch_set_active(mdf_batch *b, int index, int active) {
     if (s != MDF_OK) return s;
     s = upload_args(b);
     if (s != MDF_OK) return s;
-    if (!b->pinned && b->storage == MDF_STORAGE_FP32 && b->nitems > 0) s = choose_kernel(b);
+    if (!b->pinned && (b->storage == MDF_STORAGE_FP32 || b->metric != METRIC_CURVILINEAR) && b->nitems > 0)
+        s = choose_kernel(b);
     return s;
 }
 
@@ -523,8 +527,8 @@ mdf_status mdf_batch_set_launch(mdf_batch *b, int kind) {
     if (kind < 0 || kind > 2)
         return bfail(b, MDF_E_INVALID, "kind must be 0 (march), 1 (tile) or 2 (rolled march)");
     if (kind == 1 && b->occ_tile < 1) return bfail(b, MDF_E_INVALID, "the tile kernel does not fit");
-    if (kind != 1 && b->storage != MDF_STORAGE_FP32)
-        return bfail(b, MDF_E_INVALID, "the marches of a batch keep FP32 storage");
+    if (kind == 0 && b->storage != MDF_STORAGE_FP32)
+        return bfail(b, MDF_E_INVALID, "with 16-bit storage the march of a batch runs in rolled form (kind 2)");
     if (kind == 2 && b->metric == METRIC_CURVILINEAR)
         return bfail(b, MDF_E_INVALID, "the rolled march serves uniform and separable grids");
     BCK(b, cudaStreamSynchronize(b->stream));

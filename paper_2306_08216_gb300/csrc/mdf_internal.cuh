@@ -152,11 +152,12 @@ int step_pitch(int nx, int W);
 struct BatchItem {
     int problem, bx, by, pad;
 };
-cudaError_t batch_occupancy(int metric, int power_law, int walls, int *nt, int *occ, int *smem);
-// roll: the rolled form of the register-window march (uniform and separable
-// grids; ignored on curvilinear grids).
+// storage: the batch's storage mode (16-bit: uniform and separable grids
+// only, rolled form).  roll: the rolled form of the register-window march
+// (uniform and separable grids; ignored on curvilinear grids).
+cudaError_t batch_occupancy(int metric, int power_law, int walls, int storage, int *nt, int *occ, int *smem);
 cudaError_t batch_launch(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps, int metric,
-                         int power_law, int walls, int grid, int forced, int roll, cudaStream_t stream);
+                         int power_law, int walls, int grid, int forced, int roll, int storage, cudaStream_t stream);
 
 // Walls and/or power law on uniform/separable grids, FP32 storage, in the
 // register-window form of the fast path (mdf_step_walls.cu).
@@ -164,9 +165,15 @@ bool walls_path_applies(int metric, int power_law, int walls, int storage);
 cudaError_t walls_occupancy(int metric, int power_law, int nt, int *occ, int *smem);
 cudaError_t walls_launch(const CUtensorMap *tmap, const StepArgs &args, int metric, const StepPlan &plan,
                          cudaStream_t stream);
-cudaError_t walls_batch_occupancy(int metric, int power_law, int *nt, int *occ, int *smem);
+cudaError_t walls_batch_occupancy(int metric, int power_law, int storage, int *nt, int *occ, int *smem);
 cudaError_t walls_batch_launch(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps,
-                               int metric, int power_law, int grid, int forced, int roll, cudaStream_t stream);
+                               int metric, int power_law, int grid, int forced, int roll, int storage,
+                               cudaStream_t stream);
+// The 16-bit batched wall march (FP16/BF16 storage, rolled form only).
+cudaError_t walls_batch_occupancy16(int metric, int power_law, int storage, int *occ, int *smem);
+cudaError_t walls_batch_launch16(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps,
+                                 int metric, int power_law, int grid, int forced, int roll, int storage,
+                                 cudaStream_t stream);
 
 // The shared-ring march with the alpha = 0 distribution (planes 10..14) on
 // every grid kind, FP32 storage (mdf_step_rho0.cu).

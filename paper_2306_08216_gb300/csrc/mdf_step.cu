@@ -115,16 +115,16 @@ int step_candidates(int metric, int power_law, int walls, int storage, int rho0,
     return n;
 }
 
-cudaError_t batch_occupancy(int metric, int power_law, int walls, int *nt, int *occ, int *smem) {
-    if (metric != METRIC_CURVILINEAR) return walls_batch_occupancy(metric, power_law, nt, occ, smem);
+cudaError_t batch_occupancy(int metric, int power_law, int walls, int storage, int *nt, int *occ, int *smem) {
+    if (metric != METRIC_CURVILINEAR) return walls_batch_occupancy(metric, power_law, storage, nt, occ, smem);
     *nt = kMarchNT;
     MDF_CURVI_DISPATCH(batch_occupancy_t, occ, smem)
 }
 
 cudaError_t batch_launch(const BatchItem *items, int nitems, const StepArgs *args, const CUtensorMap *maps, int metric,
-                         int power_law, int walls, int grid, int forced, int roll, cudaStream_t stream) {
+                         int power_law, int walls, int grid, int forced, int roll, int storage, cudaStream_t stream) {
     if (metric != METRIC_CURVILINEAR)
-        return walls_batch_launch(items, nitems, args, maps, metric, power_law, grid, forced, roll, stream);
+        return walls_batch_launch(items, nitems, args, maps, metric, power_law, grid, forced, roll, storage, stream);
     MDF_CURVI_DISPATCH(batch_launch_t, items, nitems, args, maps, grid, stream)
 }
 

@@ -98,15 +98,23 @@ def test_cavity_400_steps_against_oracle_and_fp32(mode):
     assert du <= (2e-3 if mode == "fp16" else 2e-2) * U0
 
 
-@pytest.mark.parametrize("mode", MODES)
-def test_batch_equals_solo_runs_bitwise(mode):
+def batch_problems(mode):
     probs = []
     for side, re, ni in [(65, 400, 0.6), (33, 100, 1.0), (47, 250, 1.4)]:
         K = 0.1 ** (2 - ni) / re
         probs.append(dict(nx=side, ny=side, nu=K * 0.1 ** (ni - 1), walls=(True, True), u_wall=(0, 0, 0, 0.1),
                           power_law=(K, ni, K * 0.1 ** (ni - 1) / 20, K * 0.1 ** (ni - 1) * 20), storage=mode))
+    return probs
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_equals_solo_runs_bitwise(mode):
+    """In tile mode a 16-bit batch computes what the same problems compute
+    alone (single 16-bit problems with walls step on the tile kernel)."""
+    probs = batch_problems(mode)
     batch = mdf.Batch(probs)
-    assert batch.info()["kernel"] == "tile"
+    assert batch.info()["kernel"] in ("tile", "march_rolled")
+    batch.set_launch("tile")
     batch.step(40)
     for i, kw in enumerate(probs):
         kw = dict(kw)
@@ -115,8 +123,61 @@ def test_batch_equals_solo_runs_bitwise(mode):
         solo.init(*W.zeros(nx, ny))
         solo.step(40)
         np.testing.assert_array_equal(batch.problem(i).state(), solo.state())
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_rolled_march_against_oracle(mode):
+    """The rolled wall/power-law march with 16-bit storage (batches on
+    uniform grids): every problem within the N-step bound of the oracle,
+    N 15 u_r max|n| plus the 5e-7 U0 of the FP32 path; the tile-mode batch
+    within the same bound."""
+    probs = batch_problems(mode)
+    steps, U0 = 120, 0.1
+    states = {}
+    for kind in ("march_rolled", "tile"):
+        b = mdf.Batch(probs)
+        b.set_launch(kind)
+        assert b.info()["kernel"] == kind
+        b.step(steps)
+        states[kind] = [b.problem(i).state() for i in range(len(probs))]
+    for i, kw in enumerate(probs):
+        kw = dict(kw)
+        nx, ny = kw.pop("nx"), kw.pop("ny")
+        kw.pop("storage")
+        o = Oracle(nx, ny, **kw)
+        o.init(*W.zeros(nx, ny))
+        o.step(steps)
+        nmax = noneq_max(o)
+        bound = 5e-7 * U0 + steps * 15 * UNIT_ROUNDOFF[mode] * nmax
+        for kind, st in states.items():
+            err = maxabs(st[i], o.state())
+            assert err <= bound, (kind, i, err, bound)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_rolled_march_poisoned_equals_clean(mode):
+    """NaN in every storage element no valid result may read (row padding,
+    ghost columns beside x walls) changes nothing in the 16-bit rolled march."""
+    probs = batch_problems(mode)
+    out = []
+    for poison in (False, True):
+        b = mdf.Batch(probs)
+        b.set_launch("march_rolled")
+        if poison:
+            for i in range(len(probs)):
+                b.problem(i).debug_poison()
+        b.step(40)
+        b.step(3)
+        out.append([b.problem(i).state() for i in range(len(probs))])
+    for a, c in zip(*out):
+        assert np.isfinite(c).all()
+        np.testing.assert_array_equal(a, c)
+
+
+def test_16bit_batch_rejects_the_unrolled_march():
+    b = mdf.Batch(batch_problems("fp16"))
     with pytest.raises(mdf.MdfError) as e:
-        batch.set_launch("march")
+        b.set_launch("march")
     assert e.value.status == mdf.MDF_E_INVALID
 
 
