@@ -165,6 +165,8 @@ static int *pinned_err(mdf_ctx *c) { return reinterpret_cast<int *>(c->h_result 
 
 static mdf_status check_device_error(mdf_ctx *c) {
     const int herr = *pinned_err(c);
+    if (herr == DEVERR_INDEX)
+        return fail(c, MDF_E_CUDA, "the debug build's index check skipped a global access outside its buffer");
     if (herr != 0) return fail(c, MDF_E_TIMEOUT, "a bounded device wait gave up (code %d)", herr);
     return MDF_OK;
 }

@@ -147,9 +147,36 @@ __device__ __forceinline__ Mom2 moments2r(const F2 g[5], float c, float pr) {
     return m;
 }
 
+// Index checks of the debug build (-DMDF_DEBUG): a global access outside
+// its buffer is skipped and raises DEVERR_INDEX in the error word (no trap,
+// the context stays usable); the release build compiles them out.
+__device__ __forceinline__ bool index_ok(const StepArgs &a, long long e, long long limit) {
+#ifdef MDF_DEBUG
+    if (e >= 0 && e < limit) return true;
+    atomicCAS(a.err, DEVERR_NONE, DEVERR_INDEX);
+    return false;
+#else
+    (void)a;
+    (void)e;
+    (void)limit;
+    return true;
+#endif
+}
+// An element of the state buffer (every plane of the storage mode).
+__device__ __forceinline__ bool state_index_ok(const StepArgs &a, long long e) {
+    return index_ok(a, e, (long long)state_planes(a.storage, a.rho0) * a.plane);
+}
+// A pair of padded field planes (force, force rate) at element e.
+__device__ __forceinline__ F2 field_pair(const StepArgs &a, const float *fx, const float *fy, long long e) {
+    if (!index_ok(a, e, a.plane)) return splat(0.0f);
+    return mk2(fx[e], fy[e]);
+}
+
 // Source R of Eq. 2.1.1 at storage element (row, X) (constant or padded field).
 __device__ __forceinline__ float source_at(const StepArgs &a, int row, int X) {
-    return a.r_mode == 1 ? a.Rc : a.Rp[(long long)row * a.pitch + GHOST + X];
+    if (a.r_mode == 1) return a.Rc;
+    const long long e = (long long)row * a.pitch + GHOST + X;
+    return index_ok(a, e, a.plane) ? a.Rp[e] : 0.0f;
 }
 
 // Non-equilibrium part n = g - feq (Eq. 2.2.5 on D2Q5 with w_j = 1/5 and
@@ -345,8 +372,8 @@ __device__ __forceinline__ void store_node(const StepArgs &a, int row, int X, co
     for (int j = 0; j < 5; ++j) split2(v[j], lo[j], hi[j]);
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
-        a.fout[j * a.plane + base] = lo[j];
-        a.fout[(5 + j) * a.plane + base] = hi[j];
+        if (state_index_ok(a, j * a.plane + base)) a.fout[j * a.plane + base] = lo[j];
+        if (state_index_ok(a, (5 + j) * a.plane + base)) a.fout[(5 + j) * a.plane + base] = hi[j];
     }
     if (XPER) {
         // a node can be the image of a ghost on both sides when nx < 2 GHOST
@@ -354,16 +381,16 @@ __device__ __forceinline__ void store_node(const StepArgs &a, int row, int X, co
             const long long b2 = base + a.nx;
 #pragma unroll
             for (int j = 0; j < 5; ++j) {
-                a.fout[j * a.plane + b2] = lo[j];
-                a.fout[(5 + j) * a.plane + b2] = hi[j];
+                if (state_index_ok(a, j * a.plane + b2)) a.fout[j * a.plane + b2] = lo[j];
+                if (state_index_ok(a, (5 + j) * a.plane + b2)) a.fout[(5 + j) * a.plane + b2] = hi[j];
             }
         }
         if (X >= a.nx - GHOST) {
             const long long b2 = base - a.nx;
 #pragma unroll
             for (int j = 0; j < 5; ++j) {
-                a.fout[j * a.plane + b2] = lo[j];
-                a.fout[(5 + j) * a.plane + b2] = hi[j];
+                if (state_index_ok(a, j * a.plane + b2)) a.fout[j * a.plane + b2] = lo[j];
+                if (state_index_ok(a, (5 + j) * a.plane + b2)) a.fout[(5 + j) * a.plane + b2] = hi[j];
             }
         }
     }
@@ -379,14 +406,19 @@ template <bool XPER>
 __device__ __forceinline__ void store_node0(const StepArgs &a, int row, int X, const float v[5]) {
     const long long base = (long long)row * a.pitch + GHOST + X;
 #pragma unroll
-    for (int j = 0; j < 5; ++j) a.fout[(NPLANES + j) * a.plane + base] = v[j];
+    for (int j = 0; j < 5; ++j)
+        if (state_index_ok(a, (NPLANES + j) * a.plane + base)) a.fout[(NPLANES + j) * a.plane + base] = v[j];
     if (XPER) {
         if (X < GHOST)
 #pragma unroll
-            for (int j = 0; j < 5; ++j) a.fout[(NPLANES + j) * a.plane + base + a.nx] = v[j];
+            for (int j = 0; j < 5; ++j)
+                if (state_index_ok(a, (NPLANES + j) * a.plane + base + a.nx))
+                    a.fout[(NPLANES + j) * a.plane + base + a.nx] = v[j];
         if (X >= a.nx - GHOST)
 #pragma unroll
-            for (int j = 0; j < 5; ++j) a.fout[(NPLANES + j) * a.plane + base - a.nx] = v[j];
+            for (int j = 0; j < 5; ++j)
+                if (state_index_ok(a, (NPLANES + j) * a.plane + base - a.nx))
+                    a.fout[(NPLANES + j) * a.plane + base - a.nx] = v[j];
     }
 }
 
@@ -443,11 +475,12 @@ __device__ __forceinline__ void dev_store_at(const StepArgs &a, long long e, flo
                                              const unsigned w[4]) {
     float *fp = a.fout;
     unsigned *wp = reinterpret_cast<unsigned *>(fp);
-    fp[e] = u;
-    fp[a.plane + e] = v;
-    fp[2 * a.plane + e] = P;
+    if (state_index_ok(a, e)) fp[e] = u;
+    if (state_index_ok(a, a.plane + e)) fp[a.plane + e] = v;
+    if (state_index_ok(a, 2 * a.plane + e)) fp[2 * a.plane + e] = P;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) wp[(DEV_FPLANES + j) * a.plane + e] = w[j];
+    for (int j = 0; j < 4; ++j)
+        if (state_index_ok(a, (DEV_FPLANES + j) * a.plane + e)) wp[(DEV_FPLANES + j) * a.plane + e] = w[j];
 }
 
 // Output of one node (5 pairs of fhat) in a 16-bit layout: moments and

@@ -37,7 +37,7 @@ constexpr int NSCALE_EXP = 12;
 
 // 32-bit planes of one state buffer (FP32 storage with the alpha = 0
 // distribution: 15 planes).
-inline int state_planes(int storage, int rho0 = 0) {
+__host__ __device__ inline int state_planes(int storage, int rho0 = 0) {
     return storage == STORAGE_FP32 ? (rho0 ? RHO0_PLANES : NPLANES) : DEV_PLANES;
 }
 inline size_t state_buffer_bytes(int storage, long long plane, int rho0 = 0) {
@@ -60,8 +60,10 @@ inline void mark_device_setup(std::atomic<unsigned long long> &mask) {
     if (d < 64) mask.fetch_or(1ull << d, std::memory_order_release);
 }
 
-// Error codes the kernels raise in StepArgs::err (first one wins).
-enum DeviceError { DEVERR_NONE = 0, DEVERR_TMA_TIMEOUT = 1 };
+// Error codes the kernels raise in StepArgs::err (first one wins):
+// a bounded TMA wait that gave up, or (debug build, -DMDF_DEBUG) a global
+// access outside its buffer, which is skipped instead of made.
+enum DeviceError { DEVERR_NONE = 0, DEVERR_TMA_TIMEOUT = 1, DEVERR_INDEX = 2 };
 
 struct StepArgs {
     float *fout;            // output state (same layout as the input)

@@ -282,7 +282,7 @@ __device__ __forceinline__ void march(const CUtensorMap *tmap, const StepArgs &a
                 if (a.force_mode_d == 1) fF = dw * mk2(a.Fxd, a.Fyd);
                 else if (a.force_mode_d == 2) {
                     const long long fi = (long long)r * a.pitch + GHOST + X;
-                    fF = dw * mk2(a.Fxdp[fi], a.Fydp[fi]);
+                    fF = dw * field_pair(a, a.Fxdp, a.Fydp, fi);
                 }
                 F2 out[5];
 #pragma unroll
@@ -507,7 +507,7 @@ __device__ __forceinline__ void march(const CUtensorMap *tmap, const StepArgs &a
                     if (a.force_mode == 1) fF = hw * mk2(a.Fx, a.Fy);
                     else if (a.force_mode == 2) {
                         const long long fi = (long long)qw * a.pitch + GHOST + X;
-                        fF = hw * mk2(a.Fxp[fi], a.Fyp[fi]);
+                        fF = hw * field_pair(a, a.Fxp, a.Fyp, fi);
                     }
                     // Step 2 (pass 1): fbar = fbar^+ - h c.grad fbar^+ + h w F
                     F2 fb[5];

@@ -249,7 +249,8 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, uns
                 const long long s =
                     (long long)axis_index(Y, a.ny, ywall) * a.pitch + GHOST + axis_index(X, a.nx, xwall);
 #pragma unroll
-                for (int k = 0; k < NW; ++k) raw[q][k] = a.fin[k * a.plane + s];
+                for (int k = 0; k < NW; ++k)
+                    if (state_index_ok(a, k * a.plane + s)) raw[q][k] = a.fin[k * a.plane + s];
             }
         }
     }
@@ -354,7 +355,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, int bx, int by, uns
         if (a.force_mode == 1) fF = hw * mk2(a.Fx, a.Fy);
         else if (a.force_mode == 2) {
             const long long fi = (long long)Yw * a.pitch + GHOST + Xw;
-            fF = hw * mk2(a.Fxp[fi], a.Fyp[fi]);
+            fF = hw * field_pair(a, a.Fxp, a.Fyp, fi);
         }
         // Step 2 (pass 1): fbar = fbar^+ - h c.grad fbar^+ + h w F
         F2 fb[5];
@@ -466,7 +467,7 @@ __device__ __forceinline__ void tile_output(const StepArgs &a, int X, int Y, int
     if (a.force_mode_d == 1) fF = dw * mk2(a.Fxd, a.Fyd);
     else if (a.force_mode_d == 2) {
         const long long fi = (long long)Y * a.pitch + GHOST + X;
-        fF = dw * mk2(a.Fxdp[fi], a.Fydp[fi]);
+        fF = dw * field_pair(a, a.Fxdp, a.Fydp, fi);
     }
     F2 out[5];
 #pragma unroll

@@ -63,13 +63,13 @@ __device__ __forceinline__ F2 force_h(const StepArgs &a, int row, int X, F2 fact
     if (a.force_mode == 0) return splat(0.0f);
     if (a.force_mode == 1) return factor * mk2(a.Fx, a.Fy);
     const long long fi = (long long)row * a.pitch + GHOST + X;
-    return factor * mk2(a.Fxp[fi], a.Fyp[fi]);
+    return factor * field_pair(a, a.Fxp, a.Fyp, fi);
 }
 __device__ __forceinline__ F2 force_d(const StepArgs &a, int row, int X, F2 factor) {
     if (a.force_mode_d == 0) return splat(0.0f);
     if (a.force_mode_d == 1) return factor * mk2(a.Fxd, a.Fyd);
     const long long fi = (long long)row * a.pitch + GHOST + X;
-    return factor * mk2(a.Fxdp[fi], a.Fydp[fi]);
+    return factor * field_pair(a, a.Fxdp, a.Fydp, fi);
 }
 
 // One TMA row: 10 FP32 planes, or u, v, P and 4 planes of 16-bit pairs.

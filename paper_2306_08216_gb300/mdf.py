@@ -16,7 +16,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmdf.so")
+# MDF_DEBUG_LIBRARY=1 loads the debug build (libmdf_debug.so, index checks)
+LIB_PATH = os.path.join(HERE, "libmdf_debug.so" if os.environ.get("MDF_DEBUG_LIBRARY") == "1" else "libmdf.so")
 
 MDF_OK, MDF_E_INVALID, MDF_E_CUDA, MDF_E_NOMEM, MDF_E_DIVERGED, MDF_E_TIMEOUT, MDF_E_STATE = range(7)
 STATUS_NAMES = {0: "MDF_OK", 1: "MDF_E_INVALID", 2: "MDF_E_CUDA", 3: "MDF_E_NOMEM",
@@ -139,7 +140,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError("libmdf.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+            raise ImportError("%s is not built; run __graft_entry__.build()" % LIB_PATH)
         L = ctypes.CDLL(LIB_PATH)
         for name, res, args in _SIGNATURES:
             fn = getattr(L, name)
