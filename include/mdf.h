@@ -194,7 +194,9 @@ mdf_status mdf_set_source(mdf_ctx *ctx, int mode, double r, const float *R, int 
  * step keeps the value Eq. 3.1 gave from the node coordinates.  Enqueued on
  * the context's stream: steps enqueued later use the new coefficients
  * (synchronise a batch that holds the context first).  Host input is
- * checked for finite values and the call waits for the upload.  Errors:
+ * checked for finite values and the call waits for the upload; device
+ * input (on_device = 1) is read on the stream, so it must stay valid until
+ * the stream has passed this call.  Errors:
  * MDF_E_INVALID (not a curvilinear grid, NULL arrays, non-finite values),
  * MDF_E_NOMEM, MDF_E_CUDA. */
 mdf_status mdf_set_metrics(mdf_ctx *ctx, const double *xi_x, const double *xi_y, const double *eta_x,
