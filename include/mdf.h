@@ -10,8 +10,10 @@
  * (Eq. 3.1.0), the MRT collision of Eq. 2.2.4 with s0 = s3 = s4 = s',
  * s1 = s2 = s (Sec. 3.1), the linear equilibrium of Eq. 2.2.5, the mixed
  * central/upwind differences of Eqs. 2.2.12-2.2.13 and the time step of
- * Eq. 3.1.  The state is the two distributions fhat_{j,alpha}, alpha = u, v
- * (the alpha = 0 equation is not evolved, Remark 1).
+ * Eq. 3.1.  The state is the two distributions fhat_{j,alpha}, alpha = u, v;
+ * the alpha = 0 distribution (rho_0, Eq. 2.1.2), which feeds back into
+ * neither u nor P (Remark 1), is evolved beside them when
+ * mdf_params.rho0 is set.
  *
  * Conventions shared by every entry point:
  *  - Every call returns an mdf_status; the library never aborts, exits or

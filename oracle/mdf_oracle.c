@@ -65,9 +65,12 @@
  *     the caller (constants or fields) and may change between steps.
  * The curvilinear path is pinned on a doubly periodic non-affine map by the
  * steady periodic flow of Sec. 4.2 (second-order convergence to the closed
- * form).  Parity unpinned: the one-sided metric differences beside the
- * walls of a non-affine map (the trapezoid) have no closed form; they are
- * checked only through the affine scaled map, for which they are exact.
+ * form); the differenced metrics, one-sided ones at walls included, equal
+ * the analytic ones on the bilinear trapezoid and on a biquadratic map
+ * (both differences are exact there).  The wall reading is pinned by plane
+ * Couette flow against each of the four walls, uniform flow through a box
+ * of moving walls (corners between two moving walls), mirror equivariance
+ * and the wall-node identities the reading implies.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -655,6 +658,19 @@ int orc_set_metrics(orc_ctx *o, const double *xi_x, const double *xi_y, const do
         o->xi_y[n] = xi_y[n];
         o->eta_x[n] = eta_x[n];
         o->eta_y[n] = eta_y[n];
+    }
+    return 0;
+}
+
+/* Copies of the metric coefficients the step uses (curvilinear grids): the
+ * differenced ones of orc_create or those given by orc_set_metrics. */
+int orc_get_metrics(const orc_ctx *o, double *xi_x, double *xi_y, double *eta_x, double *eta_y) {
+    if (!o->xi_x || o->p.grid_kind != 2) return -1;
+    for (long n = 0; n < o->N; ++n) {
+        xi_x[n] = o->xi_x[n];
+        xi_y[n] = o->xi_y[n];
+        eta_x[n] = o->eta_x[n];
+        eta_y[n] = o->eta_y[n];
     }
     return 0;
 }

@@ -90,6 +90,8 @@ def lib():
         L.orc_set_source.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _D]
         L.orc_set_metrics.restype = ctypes.c_int
         L.orc_set_metrics.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
+        L.orc_get_metrics.restype = ctypes.c_int
+        L.orc_get_metrics.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
         _lib = L
     return _lib
 
@@ -231,6 +233,14 @@ class Oracle:
             raise ValueError("metric arrays must have ny x nx entries")
         if lib().orc_set_metrics(self._h, *(_ptr(m) for m in a)) != 0:
             raise ValueError("given metrics need a curvilinear grid")
+
+    def metrics(self):
+        """The metric coefficients xi_x, xi_y, eta_x, eta_y (ny x nx each) the
+        step uses on a curvilinear grid."""
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        if lib().orc_get_metrics(self._h, *(_ptr(m) for m in out)) != 0:
+            raise ValueError("metrics exist only on a curvilinear grid")
+        return tuple(out)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -600,3 +600,195 @@ def test_rho0_does_not_feed_back():
     np.testing.assert_array_equal(states[0], states[1])
     # mass of rho_0 is kept by the walls (zero-gradient NEE reading)
     assert abs(r.mean() - 1.0) < 1e-3
+
+
+# ------------------------------------- moving walls and corners (Secs. 4.3-4.4)
+
+# Tangential wall speeds of the Couette cases: (walls, u_wall, v_wall, moving side).
+_COUETTE = {
+    "west": ((True, False), (0, 0, 0, 0), (1, 0, 0, 0)),
+    "east": ((True, False), (0, 0, 0, 0), (0, 1, 0, 0)),
+    "south": ((False, True), (0, 0, 1, 0), (0, 0, 0, 0)),
+    "north": ((False, True), (0, 0, 0, 1), (0, 0, 0, 0)),
+}
+
+
+@pytest.mark.parametrize("side", ["west", "east", "south", "north"])
+def test_plane_couette_from_rest_for_each_moving_wall(side):
+    """Non-equilibrium extrapolation with a moving wall (named in Secs. 4.3
+    and 4.4): plane Couette flow between one moving and one resting wall,
+    periodic along them.  The steady state is linear in the wall-normal
+    coordinate with a uniform pressure; the mixed stencil (Eqs. 2.2.12-2.2.13)
+    and the linear extrapolation beyond a wall are exact on linear data, so
+    the oracle started from rest must reach it to rounding.  The derived
+    fields of Eqs. 2.4.1-2.4.5 then have closed forms as well: one velocity
+    gradient of +-U/H, S_xy = +-U/(2H), sigma_xy = 2 nu S_xy, Omega_xy and
+    the vorticity.  A dropped or sign-flipped wall velocity, the wrong wall's
+    velocity or a wrong interior neighbour fails this case."""
+    U, n, m, nu = 0.1, 17, 5, 0.1
+    walls, uw, vw = _COUETTE[side]
+    uw = tuple(U * a for a in uw)
+    vw = tuple(U * a for a in vw)
+    nx, ny = (n, m) if walls[0] else (m, n)
+    o = Oracle(nx, ny, nu=nu, walls=walls, u_wall=uw, v_wall=vw)
+    o.init(*W.zeros(nx, ny))
+    o.step(3000)
+    f = o.fields()
+    s = W.wall_nodes(n, 1.0)  # H = 1
+    zero = np.zeros((ny, nx))
+    if side in ("south", "north"):
+        prof = s if side == "north" else 1.0 - s
+        ue, ve = np.broadcast_to((U * prof)[:, None], (ny, nx)), zero
+        g = {"dudy": (U if side == "north" else -U), "dudx": 0.0, "dvdx": 0.0, "dvdy": 0.0}
+    else:
+        prof = s if side == "east" else 1.0 - s
+        ue, ve = zero, np.broadcast_to((U * prof)[None, :], (ny, nx))
+        g = {"dvdx": (U if side == "east" else -U), "dudx": 0.0, "dudy": 0.0, "dvdy": 0.0}
+    assert np.abs(f["u"] - ue).max() <= 1e-12 * U
+    assert np.abs(f["v"] - ve).max() <= 1e-12 * U
+    assert np.ptp(f["P"]) <= 1e-14
+    for k, val in g.items():
+        assert np.abs(f[k] - val).max() <= 1e-10 * U, k
+    sxy = 0.5 * (g["dudy"] + g["dvdx"])
+    assert np.abs(f["Sxy"] - sxy).max() <= 1e-10 * U
+    assert np.abs(f["sigma_xy"] - 2.0 * nu * sxy).max() <= 1e-10 * U * nu
+    assert np.abs(f["Omega_xy"] - 0.5 * (g["dudy"] - g["dvdx"])).max() <= 1e-10 * U
+    assert np.abs(f["vorticity"] - (g["dvdx"] - g["dudy"])).max() <= 1e-10 * U
+    assert np.abs(f["div"]).max() <= 1e-10 * U
+
+
+def test_uniform_flow_through_a_box_of_moving_walls():
+    """All four walls move with the same velocity (U, V), normal and
+    tangential parts both nonzero, so the corners sit between two moving
+    walls.  Uniform flow (U, V) at uniform pressure is the exact solution;
+    started from rest, the oracle must reach it at every node, corners
+    included, to rounding (a wrong sign or velocity at any wall or corner
+    branch leaves an O(U) error)."""
+    n, U, V = 21, 0.05, 0.03
+    o = Oracle(n, n, nu=0.05, walls=(True, True), u_wall=(U,) * 4, v_wall=(V,) * 4, rho0=True)
+    o.init(*W.zeros(n, n))
+    o.step(4000)
+    f = o.fields()
+    assert np.abs(f["u"] - U).max() <= 1e-12 * U
+    assert np.abs(f["v"] - V).max() <= 1e-12 * U
+    assert np.ptp(f["P"]) <= 1e-14
+    # the alpha = 0 distribution (Eq. 2.1.2, no source) settles to a uniform
+    # rho_0 carried by the uniform flow, inflow walls included (its level
+    # moves during the start-up: the zero-gradient wall reading passes the
+    # neighbour's rho_0 through an inflow wall)
+    assert np.ptp(o.rho0()) <= 1e-12
+
+
+def _wall_neighbour(x, y, nx, ny):
+    """Interior neighbour of a wall node of a closed box: wall-normal on the
+    sides, diagonal at the corners."""
+    return (1 if x == 0 else nx - 2 if x == nx - 1 else x,
+            1 if y == 0 else ny - 2 if y == ny - 1 else y)
+
+
+def test_wall_nodes_carry_wall_velocity_and_neighbour_nonequilibrium():
+    """The reading of non-equilibrium extrapolation, checked on the state the
+    oracle returns (not on its code path): after steps from a random state
+    with a different velocity on each of the four walls, every wall node has
+    its wall's velocity (the corners the west/east wall's), the pressure of
+    its interior neighbour (wall-normal; diagonal at corners), and the same
+    non-equilibrium part fhat - feq as that neighbour, with feq of Eq. 2.2.5
+    computed here independently of the oracle; the same holds for the
+    alpha = 0 distribution, whose wall rho_0 is the neighbour's."""
+    nx, ny = 19, 15
+    uw, vw = (0.01, -0.02, 0.03, 0.1), (0.04, -0.05, 0.02, -0.01)
+    o = Oracle(nx, ny, nu=0.005, walls=(True, True), u_wall=uw, v_wall=vw, eta=0.7, rho0=True)
+    o.init(*W.random_fields(nx, ny, 0.05, 21))
+    o.init_rho0(1.0 + W.random_fields(nx, ny, 0.1, 22)[2])
+    o.step(25)
+    fh = o.state()
+    feq, u, v, P = numpy_equilibrium(fh, o.cs2)
+    ne = fh - feq
+    # alpha = 0: feq_{j,0} = w_j (rho_0 + c_j.(rho_0 u)/cs^2) (Eq. 2.2.5 with
+    # ubar_0 = rho_0, E_0 = 0); the wall's rho_0 is the neighbour's
+    r = o.rho0_state()
+    rho = r.sum(axis=0)
+    req = np.stack([0.2 * (rho + (CX[j] * rho * u + CY[j] * rho * v) / o.cs2) for j in range(5)])
+    ne0 = r - req
+    checked = 0
+    for y in range(ny):
+        for x in range(nx):
+            if 0 < x < nx - 1 and 0 < y < ny - 1:
+                continue
+            side = 0 if x == 0 else 1 if x == nx - 1 else 2 if y == 0 else 3
+            xn, yn = _wall_neighbour(x, y, nx, ny)
+            assert abs(u[y, x] - uw[side]) <= 1e-15 and abs(v[y, x] - vw[side]) <= 1e-15, (x, y)
+            assert abs(P[y, x] - P[yn, xn]) <= 1e-15, (x, y)
+            np.testing.assert_allclose(ne[:, :, y, x], ne[:, :, yn, xn], rtol=0, atol=1e-15)
+            assert abs(rho[y, x] - rho[yn, xn]) <= 1e-14, (x, y)
+            np.testing.assert_allclose(ne0[:, y, x], ne0[:, yn, xn], rtol=0, atol=1e-14)
+            checked += 1
+    assert checked == 2 * (nx + ny) - 4
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_mirror_equivariance_with_four_moving_walls(axis):
+    """A closed box with a different velocity (tangential and normal parts)
+    on every wall and a random interior: the mirror image of the initial
+    state and of the wall velocities evolves into the mirror image of the
+    solution, corners included (the corner rule maps onto itself under both
+    mirrors).  Any asymmetric slip at one wall -- a neighbour index off by one,
+    one side's velocity used at another, an upwind point on the wrong side --
+    breaks it."""
+    nx, ny = 17, 13
+    uw, vw = (0.01, -0.02, 0.03, 0.1), (0.04, -0.05, 0.02, -0.01)
+    u, v, p = W.random_fields(nx, ny, 0.05, 8)
+    kw = dict(nu=0.004, walls=(True, True), eta=0.6)
+    a = Oracle(nx, ny, u_wall=uw, v_wall=vw, **kw)
+    a.init(u, v, p)
+    a.step(30)
+    if axis == "x":  # x -> -x: west <-> east, u -> -u
+        mir = lambda f: f[:, ::-1]
+        uw2, vw2 = (-uw[1], -uw[0], -uw[2], -uw[3]), (vw[1], vw[0], vw[2], vw[3])
+        su, sv = -1.0, 1.0
+    else:  # y -> -y: south <-> north, v -> -v
+        mir = lambda f: f[::-1, :]
+        uw2, vw2 = (uw[0], uw[1], uw[3], uw[2]), (-vw[0], -vw[1], -vw[3], -vw[2])
+        su, sv = 1.0, -1.0
+    b = Oracle(nx, ny, u_wall=uw2, v_wall=vw2, **kw)
+    b.init(su * mir(u), sv * mir(v), mir(p))
+    b.step(30)
+    fa, fb = a.fields(), b.fields()
+    np.testing.assert_allclose(fb["u"], su * mir(fa["u"]), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(fb["v"], sv * mir(fa["v"]), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(fb["P"], mir(fa["P"]), rtol=0, atol=1e-15)
+
+
+def _metrics_per_index(x_xi, x_eta, y_xi, y_eta, nx, ny):
+    """Metric coefficients per unit node index from the derivatives of a
+    map on the unit square (xi = i/(nx-1), eta = j/(ny-1))."""
+    x_i, x_j, y_i, y_j = x_xi / (nx - 1), x_eta / (ny - 1), y_xi / (nx - 1), y_eta / (ny - 1)
+    J = x_i * y_j - x_j * y_i
+    return y_j / J, -x_j / J, -y_i / J, x_i / J
+
+
+@pytest.mark.parametrize("grid", ["trapezoid", "biquadratic"])
+def test_differenced_metrics_are_exact_on_low_order_maps(grid):
+    """Coordinate transformation (keyword only; the reading: second-order
+    differences of the node coordinates, central inside, one-sided at
+    walls).  Both are exact on maps that are at most quadratic along each
+    computational axis, so on such maps the metric coefficients the oracle
+    derives must equal the analytic ones to rounding at every node, the
+    wall rows and columns included: the bilinear trapezoid of the cavity
+    runs, and a biquadratic map (x = xi + 0.1 xi^2 + 0.05 eta^2,
+    y = eta + 0.08 eta^2 + 0.04 xi^2), on which a first-order or wrongly
+    weighted one-sided difference is not exact."""
+    nx, ny = 37, 29
+    if grid == "trapezoid":
+        X, Y = W.trapezoid_grid(nx, ny)
+        exact = W.trapezoid_metrics(nx, ny)
+    else:
+        XI, ETA = np.meshgrid(np.arange(nx) / (nx - 1), np.arange(ny) / (ny - 1))
+        X = XI + 0.1 * XI ** 2 + 0.05 * ETA ** 2
+        Y = ETA + 0.08 * ETA ** 2 + 0.04 * XI ** 2
+        exact = _metrics_per_index(1 + 0.2 * XI, 0.1 * ETA, 0.08 * XI, 1 + 0.16 * ETA, nx, ny)
+    o = Oracle(nx, ny, nu=0.01, grid="curvilinear", x=X, y=Y, walls=(True, True), u_wall=(0, 0, 0, 0.1))
+    got = o.metrics()
+    scale = np.abs(exact[0]).max()
+    for name, g, e in zip(("xi_x", "xi_y", "eta_x", "eta_y"), got, exact):
+        assert np.abs(g - e).max() <= 1e-12 * scale, name
