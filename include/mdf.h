@@ -395,26 +395,40 @@ const char *mdf_batch_last_error(const mdf_batch *batch); /* NULL: this thread's
 
 /* Residual and drift with no allocation at all (the paper has no
  * counterpart; this is a service for callers that may not allocate device
- * memory -- inside stream capture, under an allocator that owns all device
- * memory, or in a loop that must not risk an allocation or the implicit
- * device synchronisation of cudaMalloc/cudaFree).
+ * memory -- under an allocator that owns all device memory and forbids side
+ * allocations, or in a loop that must not risk an allocation failure or the
+ * implicit device synchronisation of cudaMalloc/cudaFree).
  *   fhat            device, FP32 [2][5][ny][nx] (the layout of
  *                   mdf_get_distributions with on_device = 1)
  *   u_prev, v_prev  device, FP32 [ny][nx], velocity `window` steps earlier
  *                   (e.g. from mdf_fields with on_device = 1); not modified
  *   window          steps between u_prev/v_prev and fhat (>= 1)
- *   cuda_stream     stream to enqueue on (NULL = legacy stream); asynchronous
+ *   cuda_stream     stream of the current device to enqueue on (NULL =
+ *                   legacy stream); asynchronous
  *   out             device, 4 doubles: residual as defined for mdf_residual,
- *                   sum of u, sum of v, count of non-finite nodes
+ *                   sum of u, sum of v, count of non-finite nodes, where u, v
+ *                   are the FP32 sums of the five fhat of each distribution.
+ *                   For a context with FP32 storage that is the velocity
+ *                   mdf_residual uses.  With FP16/BF16 storage mdf_residual
+ *                   reads the stored FP32 u, v, while the fhat that
+ *                   mdf_get_distributions rebuilds (feq + non-equilibrium
+ *                   part) sum to them only up to FP32 rounding (a few ulp of
+ *                   |u|), so the two residuals differ by about that rounding
+ *                   divided by window * |U| and this one levels off near
+ *                   1e-7 / window instead of falling to zero at a steady
+ *                   state.
  * The only scratch is a fixed array of 160 KiB of device memory that the
  * library holds on every GPU that loads it, so nx * ny may not exceed
  * 16,777,216 (4096 x 4096): larger fields, NULL pointers or window < 1
  * return MDF_E_INVALID before anything is enqueued.  The first call on a
- * device looks up that array's device address (once per device); make that
- * first call outside any stream capture.  All calls share the one array, so
- * calls that may run at the same time on the GPU (other streams, other host
- * threads) race; serialise them.  Allocates nothing: no cudaMalloc, cudaFree
- * or allocating library call on any path. */
+ * device looks up that array's device address (once per device, with that
+ * device current) and keeps it; make that first call before any stream
+ * capture, and make no call on a device after cudaDeviceReset of it (the
+ * kept address is no longer valid).  All calls share the one array, which
+ * keeps the last call's partial sums (every call overwrites the slots it
+ * reads), so calls that may run at the same time on the GPU (other streams,
+ * other host threads) race; serialise them.  Allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library call on any path. */
 mdf_status mdf_residual_noalloc(const float *fhat, const float *u_prev, const float *v_prev, int nx, int ny,
                                 long long window, void *cuda_stream, double *out);
 

@@ -2,11 +2,10 @@
 // allocation of any kind.
 //
 // Who needs this: code that runs where device memory may not be allocated --
-// inside a region that must not call cudaMalloc/cudaFree (those calls
-// synchronise the device and are illegal while a stream is being captured),
-// under an allocator that owns all device memory and forbids side
-// allocations, or in a real-time loop that must not risk an allocation
-// failure or an implicit device-wide synchronisation.  Such a caller passes
+// under an allocator (a framework's caching allocator, a memory pool sized at
+// start-up) that owns all device memory and forbids side allocations, or in a
+// real-time loop that must not risk an allocation failure or the implicit
+// device-wide synchronisation of cudaMalloc/cudaFree.  Such a caller passes
 // its own inputs and outputs; the only scratch this path uses is the
 // file-scope array below, which the CUDA loader places in device memory when
 // the library is loaded (every GPU that loads the library holds it until the
@@ -33,7 +32,10 @@ constexpr long long kMaxNodes = (long long)kMaxBlocks * kThreads * kPerThread;
 
 static __device__ __align__(256) double g_partials[kMaxBlocks * 5];
 
-// Device address of g_partials for each device, resolved once per device.
+// Device address of g_partials for each device, resolved once per device
+// (the first call on that device, with it current).  A device reset
+// (cudaDeviceReset) unloads the module, so the cached address is not valid
+// afterwards; the header says so.
 constexpr int kMaxDevices = 64;
 double *g_partials_addr[kMaxDevices] = {nullptr};
 std::mutex g_setup_mutex;
@@ -113,6 +115,9 @@ extern "C" mdf_status mdf_residual_noalloc(const float *fhat, const float *u_pre
     if (!fhat || !u_prev || !v_prev || !out || nx < 1 || ny < 1 || window < 1) return MDF_E_INVALID;
     const long long N = (long long)nx * ny;
     if (N > kMaxNodes) return MDF_E_INVALID;  // larger than the static scratch serves
+    // an error left by an earlier, unrelated call on this thread is not this
+    // call's failure: clear it before the launches are checked
+    (void)cudaGetLastError();
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MDF_E_CUDA;
     double *partials = nullptr;
@@ -128,6 +133,7 @@ extern "C" mdf_status mdf_residual_noalloc(const float *fhat, const float *u_pre
     const int nblocks = (int)((N + (long long)kThreads * kPerThread - 1) / ((long long)kThreads * kPerThread));
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     norms_partial_kernel<<<nblocks, kThreads, 0, st>>>(fhat, u_prev, v_prev, N, partials);
+    if (cudaGetLastError() != cudaSuccess) return MDF_E_CUDA;
     norms_final_kernel<<<1, 1024, 0, st>>>(partials, nblocks, window, out);
     return cudaGetLastError() == cudaSuccess ? MDF_OK : MDF_E_CUDA;
 }
