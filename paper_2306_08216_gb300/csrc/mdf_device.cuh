@@ -233,15 +233,21 @@ __device__ __forceinline__ void nee2(const F2 g[5], float uw, float vw, float in
 struct Rates {
     float rpp, rp, rbp, rb, rkp, rk;
 };
-__device__ __forceinline__ Rates rates_for(float s, float s_ratio, float dt) {
-    const float sp = s_ratio * s;
+// Rates of the three local maps at a node of viscosity nu, with s = cs^2/nu
+// and s' = s_ratio s: rho(l) = (1 - dt l/2)/(1 + dt l/2) (Eq. 2.2.14),
+// 1/4 + 3/4 rho(l) (Eq. 2.2.15) and kappa(l) = 1/(1 + h l/2) (Eq. 2.2.16) for
+// l = s, s', written in nu (c1 = cs^2 dt/2) so that the per-node power-law
+// solve needs no quotient for s; the quotients take the fast reciprocal
+// (2 ulp).
+__device__ __forceinline__ Rates rates_nu(float nu, float s_ratio, float c1) {
+    const float c1p = s_ratio * c1;
     Rates r;
-    r.rpp = (1.0f - 0.5f * dt * sp) / (1.0f + 0.5f * dt * sp);
-    r.rp = (1.0f - 0.5f * dt * s) / (1.0f + 0.5f * dt * s);
+    r.rpp = __fdividef(nu - c1p, nu + c1p);
+    r.rp = __fdividef(nu - c1, nu + c1);
     r.rbp = 0.25f * (1.0f + 3.0f * r.rpp);
     r.rb = 0.25f * (1.0f + 3.0f * r.rp);
-    r.rkp = 1.0f / (1.0f + 0.25f * dt * sp);
-    r.rk = 1.0f / (1.0f + 0.25f * dt * s);
+    r.rkp = __fdividef(nu, nu + 0.5f * c1p);
+    r.rk = __fdividef(nu, nu + 0.5f * c1);
     return r;
 }
 

@@ -406,7 +406,7 @@ __device__ __forceinline__ void march(const CUtensorMap *tmap, const StepArgs &a
                 split2(splat(c) * n24, gy1, gy2);
                 const float sxy = 0.5f * (gy1 + gx2);
                 const float gg = sqrtf(2.0f * (gx1 * gx1 + gy2 * gy2 + 2.0f * sxy * sxy));
-                const Rates Rr = rates_for(a.cs2 / power_law_nu(gg, a), a.s_ratio, a.dt);
+                const Rates Rr = rates_nu(power_law_nu(gg, a), a.s_ratio, a.a_pl);
                 mKp_ = splat(-(1.0f - Rr.rpp));
                 Dp_ = splat(0.5f * (Rr.rp - Rr.rpp));
                 mKb_ = splat(-(1.0f - Rr.rbp));
