@@ -57,8 +57,9 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, period_ms=50):
         self.gpu = gpu_index
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []
 
@@ -66,7 +67,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.period_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
@@ -174,6 +175,7 @@ def oracle_sample(steps, n=512):
 
 
 CAV_N, CAV_RE, CAV_U0 = 257, 1000.0, 0.1
+CLOCK_WINDOW_MS = 1500.0
 
 
 def time_to_residual(mdf, W, grid, stream, target=1e-8, check_every=100, max_steps=3_000_000):
@@ -430,8 +432,90 @@ def warm_start_benchmark(stream, count=16, target=1e-8, max_steps=130_000):
     return out
 
 
+def oracle_full_configs(threads=0, log=print):
+    """The FP64 oracle on every benchmark configuration at full size, one
+    JSON line each (CPU only; hours of work on a few host cores, so never
+    part of a default run): Taylor-Green 64^2 x 1000 steps; the Re = 1000
+    cavity at 257^2 (uniform and tanh beta = 1.5) marched to residual 1e-8
+    with the library's residual definition (window 100 steps); the power-law
+    trapezoid cavities at 513^2 (n in {0.5, 1, 1.5} x Re in {100, 400,
+    1000}, 200 steps each from rest); the 512-cavity sweep (10 steps of
+    every cavity, one problem after another); Taylor-Green 4096^2 x 2000
+    steps."""
+    import numpy as np
+
+    from oracle.oracle import Oracle, max_threads
+    from paper_2306_08216_gb300 import workloads as W
+    cores = threads or max_threads()
+
+    def emit(name, nodes, steps, sec, **extra):
+        d = {"workload": name, "nodes": nodes, "steps": steps, "seconds": sec,
+             "mlups": nodes * steps / sec / 1e6, "cores": cores, "kind": "oracle"}
+        d.update(extra)
+        log(json.dumps(finite_json(d)))
+
+    def timed(o, steps):
+        t0 = time.perf_counter()
+        o.step(steps)
+        return time.perf_counter() - t0
+
+    o = Oracle(64, 64, nu=NU, lx=2 * math.pi, ly=2 * math.pi, threads=threads)
+    o.init(*W.taylor_green(64, U0))
+    emit("taylor_green_64x64_fp64", 64 * 64, 1000, timed(o, 1000))
+    X, Y = W.trapezoid_grid(513, 513)
+    for n_index in (0.5, 1.0, 1.5):
+        for re in (100.0, 400.0, 1000.0):
+            K = CAV_U0 ** (2.0 - n_index) / re
+            nu_ref = K * CAV_U0 ** (n_index - 1.0)
+            o = Oracle(513, 513, nu=nu_ref, grid="curvilinear", x=X, y=Y, walls=(True, True),
+                       u_wall=(0, 0, 0, CAV_U0), power_law=(K, n_index, nu_ref / 20, nu_ref * 20), threads=threads)
+            o.init(*W.zeros(513, 513))
+            emit("trapezoid_513x513_power_law_n%g_re%g_fp64" % (n_index, re), 513 * 513, 200, timed(o, 200))
+            del o
+    probs = batch_problems()
+    sec, nodes = 0.0, 0
+    for p in probs:
+        kw = dict(p)
+        nx, ny = kw.pop("nx"), kw.pop("ny")
+        o = Oracle(nx, ny, threads=threads, **kw)
+        o.init(*W.zeros(nx, ny))
+        sec += timed(o, 10)
+        nodes += nx * ny
+        del o
+    emit("batch_512_power_law_cavities_fp64", nodes, 10, sec, note="each cavity stepped on its own")
+    o = Oracle(NX, NY, nu=NU, lx=2 * math.pi, ly=2 * math.pi, threads=threads)
+    o.init(*W.taylor_green(NX, U0))
+    emit("taylor_green_4096x4096_fp64", NX * NY, 2000, timed(o, 2000))
+    del o
+    for grid in ("uniform", "tanh_1.5"):
+        kw = dict(nu=CAV_U0 / CAV_RE, walls=(True, True), u_wall=(0, 0, 0, CAV_U0), threads=threads)
+        if grid.startswith("tanh"):
+            xs = W.tanh_nodes(CAV_N, 1.5)
+            kw.update(grid="separable", x=xs, y=xs)
+        o = Oracle(CAV_N, CAV_N, **kw)
+        o.init(*W.zeros(CAV_N, CAV_N))
+        f = o.fields()
+        prev = np.stack([f["u"], f["v"]])
+        steps, sec, r = 0, 0.0, math.inf
+        while r > 1e-8 and steps < 3_000_000:
+            t0 = time.perf_counter()
+            o.step(100)
+            f = o.fields()
+            cur = np.stack([f["u"], f["v"]])
+            r = math.sqrt(((cur - prev) ** 2).sum()) / (100 * math.sqrt((cur ** 2).sum()))
+            sec += time.perf_counter() - t0
+            prev = cur
+            steps += 100
+        emit("cavity_257x257_re1000_%s_to_residual_1e-8_fp64" % grid, CAV_N * CAV_N, steps, sec, residual=r,
+             reached=bool(r <= 1e-8))
+        del o
+
+
 def run_reference(args, rank, world):
     if rank != 0:
+        return 0
+    if args.oracle_configs:
+        oracle_full_configs(args.oracle_threads)
         return 0
     from oracle.oracle import Oracle, max_threads
     from paper_2306_08216_gb300 import workloads as W
@@ -447,8 +531,10 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "taylor_green_4096x4096_fp32", "sample": "512x512 Taylor-Green, one oracle step per bench step",
-                   "nu": NU, "U0": U0, "cfl": 0.5, "eta": 0.8},
+        "config": {"workload": "taylor_green_512x512_fp64_oracle", "nx": n, "ny": n,
+                   "sample_of": "taylor_green_4096x4096_fp32",
+                   "sample": "512x512 Taylor-Green (same per-node work as the 4096^2 workload), one oracle step "
+                             "per bench step", "nu": NU, "U0": U0, "cfl": 0.5, "eta": 0.8},
         "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": max_threads(), "kind": "oracle",
                          "sample": "512x512 Taylor-Green, %d steps" % args.steps},
         "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -464,6 +550,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-configs", action="store_true",
+                    help="with --impl reference: time the FP64 oracle on every benchmark configuration at full "
+                         "size (hours of CPU work; one JSON line per configuration)")
+    ap.add_argument("--oracle-threads", type=int, default=0, help="oracle threads (0 = all)")
     ap.add_argument("--no-time-to-residual", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-storage", action="store_true", help="skip the 16-bit storage runs")
@@ -520,6 +610,16 @@ def main():
         solver.step(args.steps)
         stop.record(stream)
         stop.synchronize()
+        # a timed region shorter than the sampler's period holds no sample:
+        # the same step keeps the GPU loaded for at least 1 s more (outside
+        # the timed region, before the sampler stops) so the line carries
+        # clocks taken under this load
+        ms_timed = start.elapsed_time(stop)
+        extra_steps = 0
+        if ms_timed < CLOCK_WINDOW_MS:
+            extra_steps = int(math.ceil((CLOCK_WINDOW_MS - ms_timed) / max(ms_timed / args.steps, 1e-3)))
+            solver.step(extra_steps)
+            solver.synchronize()
     torch.cuda.synchronize()
     ms = start.elapsed_time(stop)
     barrier()
@@ -588,9 +688,15 @@ def main():
                      "traffic": ncu_traffic_per_launch(), "bytes_per_node": bpn,
                      "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind},
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": 3 * nodes * 4 / e2e_steps,
-                "d2h_bytes_per_step": 3 * nodes * 4 / e2e_steps},
+                "d2h_bytes_per_step": 3 * nodes * 4 / e2e_steps, "steps": e2e_steps, "seconds": e2e_sec,
+                "note": "one upload of u, v, p (pinned host -> device, %d MB) and one download of u, v, P "
+                        "(device -> pinned host, %d MB) per run of %d steps, through mdf_init_fields, mdf_step "
+                        "and mdf_fields; with few steps the host copies dominate"
+                        % (3 * nodes * 4 // 2 ** 20, 3 * nodes * 4 // 2 ** 20, e2e_steps)},
         "gpu_launches": args.steps,
-        "clocks": clocks.summary(),
+        "clocks": dict(clocks.summary(), window="the %d timed steps and %d more steps of the same kernel right "
+                                                 "after them (%.0f ms), sampled every %d ms"
+                       % (args.steps, extra_steps, ms_timed * (1 + extra_steps / args.steps), clocks.period_ms)),
         "cpu_baseline": cpu,
         "check": {"residual": r, "drift_u": drift[0], "drift_v": drift[1]},
         "time_to_residual": ttr,
