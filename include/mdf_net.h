@@ -2,8 +2,10 @@
  *
  * The paper has no learned component; this network is an extension of the
  * library: it predicts the steady state of a power-law lid-driven cavity
- * (Sec. 4.4 set-up with the power-law fluid of Eq. 2.4.2) from its Reynolds
- * number and power-law index, so that the MDF-FDLBM march (mdf_init_fields,
+ * (the Sec. 4.4 set-up with a power-law fluid -- named by the paper, the
+ * model nu = K gdot^(n-1) is the library's reading -- on the square or a
+ * body-fitted trapezoid grid) from its Reynolds number, power-law index and grid
+ * geometry, so that the MDF-FDLBM march (mdf_init_fields,
  * mdf_step) can start from that prediction instead of from rest and still
  * converges to the method's own steady state (the network never replaces
  * the solver's result).
@@ -11,12 +13,17 @@
  * Network: a 3 x 3 convolutional U-Net on R x R nodes (R divisible by 8),
  * 15 layers (32, 64, 128, 256 channels over four resolutions, SiLU
  * activations, 2 x 2 average pooling, nearest upsampling, additive skip
- * connections), 1,754,467 parameters.  Weights and activations are stored in
- * BF16 and every convolution accumulates in FP32 on the tensor cores; the
+ * connections), 1,755,619 parameters.  Weights and activations are stored in
+ * BF16 and every convolution accumulates in FP32 on the tensor cores
+ * (tcgen05 with tensor-memory accumulators; see mdf_net_set_conv_kernel); the
  * master parameters, their gradient and the Adam moments are FP32.
  *
  * Layouts (all row-major, C order):
- *   inputs   [batch][4][R][R] FP32: scaled log Re, scaled n, x, y planes
+ *   inputs   [batch][8][R][R] FP32: scaled log Re, scaled n, the node
+ *            coordinates x, y and the metric coefficients xi_x, xi_y, eta_x,
+ *            eta_y of the cavity's grid (derivatives of the computational
+ *            coordinates xi = i/(R-1), eta = j/(R-1) with respect to x, y;
+ *            1, 0, 0, 1 on the unit square)
  *   outputs  [batch][3][R][R] FP32: u / u_lid, v / u_lid, p / u_lid^2
  *   targets  as outputs
  *   params   flat FP32, layer by layer: weights [Cout][3][3][Cin] (kernel
@@ -45,6 +52,16 @@ typedef struct mdf_net mdf_net;
 mdf_status mdf_net_create(int resolution, int max_batch, mdf_net **out);
 void mdf_net_destroy(mdf_net *net);
 mdf_status mdf_net_set_stream(mdf_net *net, void *cuda_stream);
+
+/* Kernel of the 3 x 3 convolutions (forward and input gradient):
+ * kind 0 (default) runs them on the tcgen05 tensor cores -- operands staged
+ * in shared memory by TMA, FP32 accumulators in tensor memory -- wherever
+ * the resolution of the layer is a power of two, and on the mma.sync kernel
+ * otherwise; kind 1 runs every convolution on the mma.sync kernel (the
+ * reference point the tcgen05 kernel is measured and tested against).  The
+ * weight gradient runs on the mma.sync kernel.  MDF_E_INVALID for another
+ * kind. */
+mdf_status mdf_net_set_conv_kernel(mdf_net *net, int kind);
 
 /* Number of parameters; layer count and the real (cout, cin) of a layer. */
 long long mdf_net_param_count(const mdf_net *net);

@@ -9,11 +9,15 @@ to it.  The method's arithmetic stays in the solver.
 
 Specification (both sides implement exactly this):
 
-* Input: B x 4 x R x R planes (R divisible by 8), output B x 3 x R x R
-  (u / u_lid, v / u_lid, p / u_lid^2 of the steady state on the R x R nodes).
+* Input: B x 8 x R x R planes (R divisible by 8): scaled log Re, scaled
+  power-law index, the node coordinates x, y and the four metric
+  coefficients xi_x, xi_y, eta_x, eta_y of the cavity's grid (derivatives of
+  the computational coordinates, scaled to [0, 1] over the grid, with respect
+  to x and y); output B x 3 x R x R (u / u_lid, v / u_lid, p / u_lid^2 of the
+  steady state on the R x R nodes).
 * Layers, 3 x 3 convolutions (cross-correlation, zero padding 1, stride 1,
   with bias), in this order:
-      e0a 4->32, e0b 32->32          (resolution R)
+      e0a 8->32, e0b 32->32          (resolution R)
       e1a 32->64, e1b 64->64         (R/2)
       e2a 64->128, e2b 128->128      (R/4)
       e3a 128->256, e3b 256->256     (R/8)
@@ -40,7 +44,8 @@ import numpy as np
 import torch
 import torch.nn.functional as Fn
 
-LAYERS = [("e0a", 4, 32), ("e0b", 32, 32), ("e1a", 32, 64), ("e1b", 64, 64),
+IN_PLANES = 8
+LAYERS = [("e0a", IN_PLANES, 32), ("e0b", 32, 32), ("e1a", 32, 64), ("e1b", 64, 64),
           ("e2a", 64, 128), ("e2b", 128, 128), ("e3a", 128, 256), ("e3b", 256, 256),
           ("d2a", 256, 128), ("d2b", 128, 128), ("d1a", 128, 64), ("d1b", 64, 64),
           ("d0a", 64, 32), ("d0b", 32, 32), ("out", 32, 3)]
@@ -76,7 +81,7 @@ def silu(z):
 
 
 def forward_tensors(P, x, quantize=False):
-    """Forward pass on torch tensors (P from `unpack`, x float64 B x 4 x R x R)."""
+    """Forward pass on torch tensors (P from `unpack`, x float64 B x 8 x R x R)."""
     q = lambda t: _q(t, quantize)  # noqa: E731
 
     def conv(h, name, skip=None):

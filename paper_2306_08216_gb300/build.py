@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libmdf.so")
 OBJ_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libmdf_debug.so")
 SOURCES = ["mdf_step.cu", "mdf_step_rho0.cu", "mdf_step_tile.cu", "mdf_step_tile16.cu", "mdf_step_tile_rho0.cu", "mdf_step_fast.cu", "mdf_step_walls.cu", "mdf_step_walls16.cu", "mdf_aux.cu", "mdf_api.cu", "mdf_batch.cu", "mdf_noalloc.cu",
-           "net_kernels.cu", "net_api.cu"]
+           "net_kernels.cu", "net_tc.cu", "net_api.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -15,6 +15,10 @@ using namespace mdfnet;
 
 namespace {
 
+// Input planes: scaled log Re, scaled n, node coordinates x, y and the
+// metric coefficients xi_x, xi_y, eta_x, eta_y (include/mdf_net.h).
+constexpr int kInPlanes = NET_IN_PLANES;
+
 struct LayerSpec {
     const char *name;
     int cin, cout, div;  // real channels; resolution R / div
@@ -23,7 +27,7 @@ struct LayerSpec {
 
 // Parameter order; inputs and skips are wired in forward()/backward().
 const LayerSpec kLayers[] = {
-    {"e0a", 4, 32, 1, true},     {"e0b", 32, 32, 1, true},    {"e1a", 32, 64, 2, true},
+    {"e0a", kInPlanes, 32, 1, true},     {"e0b", 32, 32, 1, true},    {"e1a", 32, 64, 2, true},
     {"e1b", 64, 64, 2, true},    {"e2a", 64, 128, 4, true},   {"e2b", 128, 128, 4, true},
     {"e3a", 128, 256, 8, true},  {"e3b", 256, 256, 8, true},  {"d2a", 256, 128, 4, true},
     {"d2b", 128, 128, 4, true},  {"d1a", 128, 64, 2, true},   {"d1b", 64, 64, 2, true},
@@ -53,6 +57,8 @@ struct mdf_net {
     bf16 *dz[kNL], *dy[kNL];
     bf16 *dp0 = nullptr, *dp1 = nullptr, *dp2 = nullptr, *du0 = nullptr, *du1 = nullptr, *du2 = nullptr;
     double *loss = nullptr, *h_loss = nullptr;
+    int *err = nullptr, *h_err = nullptr;  // error word of the tensor-core kernels
+    int conv_kind = 0;                     // 0: tcgen05 where it applies, 1: mma.sync
     long long adam_t = 0;
     bool prepared = false;
     char last_error[256] = {0};
@@ -95,6 +101,7 @@ static void free_net(mdf_net *n) {
     if (!n) return;
     for (void *p : n->allocs) cudaFree(p);
     if (n->h_loss) cudaFreeHost(n->h_loss);
+    if (n->h_err) cudaFreeHost(n->h_err);
     delete n;
 }
 
@@ -112,21 +119,30 @@ static mdf_status prepare(mdf_net *n) {
     return MDF_OK;
 }
 
-static mdf_status conv(mdf_net *n, int l, int B, const bf16 *x, const bf16 *skip, bf16 *out, float *outf, int nf) {
+// One implicit-GEMM convolution on the tcgen05 tensor cores where that
+// kernel applies (and is not switched off), else on the mma.sync kernel.
+static mdf_status run_conv(mdf_net *n, const ConvArgs &a) {
+    if (n->conv_kind == 0 && conv_tc_applies(a)) NCK(n, conv_forward_tc(a, n->num_sms, n->err, n->stream));
+    else NCK(n, conv_forward(a, n->stream));
+    return MDF_OK;
+}
+
+static mdf_status conv(mdf_net *n, int l, int B, const bf16 *x, const bf16 *skip, bf16 *out, float *outf, int nf,
+                       bf16 *act = nullptr) {
     ConvArgs a;
     a.X = x;
     a.W = n->wf[l];
     a.bias = n->bias[l];
     a.skip = skip;
     a.out = out;
+    a.act = act;
     a.outf = outf;
     a.nf = nf;
     a.B = B;
     a.R = n->R / kLayers[l].div;
     a.Cx = n->cin_pad[l];
     a.N = n->cout_pad[l];
-    NCK(n, conv_forward(a, n->stream));
-    return MDF_OK;
+    return run_conv(n, a);
 }
 
 // dX of layer l's input from dZ (mirrored weights, no bias).
@@ -137,14 +153,14 @@ static mdf_status conv_dx(mdf_net *n, int l, int B, const bf16 *dZ, bf16 *dX) {
     a.bias = nullptr;
     a.skip = nullptr;
     a.out = dX;
+    a.act = nullptr;
     a.outf = nullptr;
     a.nf = 0;
     a.B = B;
     a.R = n->R / kLayers[l].div;
     a.Cx = n->cout_pad[l];
     a.N = n->cin_pad[l];
-    NCK(n, conv_forward(a, n->stream));
-    return MDF_OK;
+    return run_conv(n, a);
 }
 
 static mdf_status wgrad(mdf_net *n, int l, int B, const bf16 *dZ, const bf16 *X) {
@@ -169,11 +185,10 @@ static mdf_status wgrad(mdf_net *n, int l, int B, const bf16 *dZ, const bf16 *X)
         if (s_ != MDF_OK) return s_;    \
     } while (0)
 
-// Layer l with its activation: z = conv(x) + b (+ skip), y = silu(z).
+// Layer l with its activation: z = conv(x) + b (+ skip), y = silu(z), the
+// activation written by the convolution's epilogue.
 static mdf_status layer(mdf_net *n, int l, int B, const bf16 *x, const bf16 *skip) {
-    NRET(conv(n, l, B, x, skip, n->z[l], nullptr, 0));
-    NCK(n, silu_forward(n->z[l], n->y[l], pix(n, B, kLayers[l].div) * n->cout_pad[l], n->stream));
-    return MDF_OK;
+    return conv(n, l, B, x, skip, n->z[l], nullptr, 0, n->y[l]);
 }
 
 static mdf_status forward(mdf_net *n, int B) {
@@ -273,8 +288,17 @@ static mdf_status backward(mdf_net *n, int B) {
     return wgrad(n, 0, B, n->dz[0], n->xin);
 }
 
+// Wait for the stream; a tensor-core kernel that gave up waiting for its
+// copies or MMAs left a nonzero error word, reported here (and cleared).
 static mdf_status wait(mdf_net *n) {
+    NCK(n, cudaMemcpyAsync(n->h_err, n->err, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
     NCK(n, cudaStreamSynchronize(n->stream));
+    if (*n->h_err) {
+        *n->h_err = 0;
+        NCK(n, cudaMemsetAsync(n->err, 0, sizeof(int), n->stream));
+        NCK(n, cudaStreamSynchronize(n->stream));
+        return nfail(n, MDF_E_CUDA, "a tensor-core convolution gave up waiting for its copies or MMAs");
+    }
     return MDF_OK;
 }
 
@@ -283,12 +307,13 @@ static mdf_status stage(mdf_net *n, int B, const float *inputs, const float *tar
     const long long RR = (long long)n->R * n->R;
     const float *in = inputs, *tg = targets;
     if (!on_device) {
-        NCK(n, cudaMemcpyAsync(n->io, inputs, (size_t)B * 4 * RR * sizeof(float), cudaMemcpyHostToDevice, n->stream));
+        NCK(n, cudaMemcpyAsync(n->io, inputs, (size_t)B * kInPlanes * RR * sizeof(float), cudaMemcpyHostToDevice,
+                               n->stream));
         in = n->io;
         if (targets) {
-            NCK(n, cudaMemcpyAsync(n->io + (size_t)B * 4 * RR, targets, (size_t)B * 3 * RR * sizeof(float),
+            NCK(n, cudaMemcpyAsync(n->io + (size_t)B * kInPlanes * RR, targets, (size_t)B * 3 * RR * sizeof(float),
                                    cudaMemcpyHostToDevice, n->stream));
-            tg = n->io + (size_t)B * 4 * RR;
+            tg = n->io + (size_t)B * kInPlanes * RR;
         }
     }
     NCK(n, pack_input(in, n->xin, B, n->R, n->stream));
@@ -373,9 +398,13 @@ mdf_status mdf_net_create(int resolution, int max_batch, mdf_net **out) {
     NCKC(nalloc(n, &n->du0, (size_t)pix(n, B, 1) * 64));
     NCKC(nalloc(n, &n->outf, (size_t)pix(n, B, 1) * 3));
     NCKC(nalloc(n, &n->tgt, (size_t)pix(n, B, 1) * 3));
-    NCKC(nalloc(n, &n->io, (size_t)pix(n, B, 1) * 7));
+    NCKC(nalloc(n, &n->io, (size_t)pix(n, B, 1) * (kInPlanes + 3)));
     NCKC(nalloc(n, &n->loss, 1));
     NCKE(cudaMallocHost(&n->h_loss, sizeof(double)));
+    NCKC(nalloc(n, &n->err, 1));
+    NCKE(cudaMemset(n->err, 0, sizeof(int)));
+    NCKE(cudaMallocHost(&n->h_err, sizeof(int)));
+    *n->h_err = 0;
     (void)R;
     *out = n;
     return MDF_OK;
@@ -392,6 +421,13 @@ void mdf_net_destroy(mdf_net *n) {
 mdf_status mdf_net_set_stream(mdf_net *n, void *stream) {
     if (!n) return MDF_E_INVALID;
     n->stream = (cudaStream_t)stream;
+    return MDF_OK;
+}
+
+mdf_status mdf_net_set_conv_kernel(mdf_net *n, int kind) {
+    if (!n) return MDF_E_INVALID;
+    if (kind != 0 && kind != 1) return nfail(n, MDF_E_INVALID, "kind must be 0 (tcgen05) or 1 (mma.sync)");
+    n->conv_kind = kind;
     return MDF_OK;
 }
 

@@ -16,6 +16,20 @@ namespace mdfnet {
 
 typedef __nv_bfloat16 bf16;
 
+// Input planes of the network (include/mdf_net.h).
+#define NET_IN_PLANES 8
+
+// SiLU(z) = z / (1 + exp(-z)) of a BF16 value, rounded to BF16: the same
+// expression in the elementwise kernels and in the convolution epilogues
+// that fuse it, so both give the same bits.  The exponential and the
+// reciprocal are the fast approximate ones (relative error near 1e-7,
+// far below the BF16 rounding of the result).
+__device__ __forceinline__ float net_sigmoid(float z) { return __frcp_rn(1.0f + __expf(-z)); }
+__device__ __forceinline__ __nv_bfloat16 silu_bf16(__nv_bfloat16 zb) {
+    const float v = __bfloat162float(zb);
+    return __float2bfloat16_rn(v * net_sigmoid(v));
+}
+
 // out[m][n] = sum_k A[m][k] W[n][k] (+ bias[n]) (+ skip[m][n]) over
 // k = (tap, c), A[m][(tap, c)] = X[pixel m shifted by tap][c] (zero outside):
 // the forward convolution (X = activations, W = [Cout][9][Cin]) and the input
@@ -26,11 +40,18 @@ struct ConvArgs {
     const float *bias;  // [N] or null
     const bf16 *skip;   // [B][R][R][N] or null
     bf16 *out;          // [B][R][R][N] (N % 2 == 0), or null if outf is set
+    bf16 *act;          // SiLU of the BF16-rounded out, [B][R][R][N], or null
     float *outf;        // FP32 output [B][R][R][nf] of the first nf channels, or null
     int nf;
     int B, R, Cx, N;
 };
 cudaError_t conv_forward(const ConvArgs &a, cudaStream_t st);
+// The same product on the tcgen05 tensor cores (net_tc.cu): TMA-staged
+// operands, FP32 accumulator in tensor memory.  Applies when R is a power of
+// two, Cx is 32 or a multiple of 64 and N a multiple of 32; a CTA that gives
+// up waiting sets *err to a nonzero value (device memory).
+bool conv_tc_applies(const ConvArgs &a);
+cudaError_t conv_forward_tc(const ConvArgs &a, int num_sms, int *err, cudaStream_t st);
 
 // Weight and bias gradients of one layer, accumulated (atomic FP32) into the
 // flat parameter-gradient vector: g[off + (co * 9 + tap) * cin_real + ci]
@@ -53,7 +74,8 @@ cudaError_t pool_backward(const bf16 *dy, bf16 *dx, int B, int R, int C, cudaStr
 cudaError_t up_forward(const bf16 *x, bf16 *y, int B, int R, int C, cudaStream_t st);      // R = input side
 cudaError_t up_backward(const bf16 *dy, bf16 *dx, int B, int R, int C, cudaStream_t st);
 cudaError_t add_inplace(bf16 *dst, const bf16 *src, long long n, cudaStream_t st);
-// planar FP32 [B][4][R][R] -> NHWC BF16 [B][R][R][32] (zero channels 4..31)
+// planar FP32 [B][NET_IN_PLANES][R][R] -> NHWC BF16 [B][R][R][32] (zero
+// channels NET_IN_PLANES..31)
 cudaError_t pack_input(const float *in, bf16 *x, int B, int R, cudaStream_t st);
 // NHWC FP32 [B][R][R][3] <-> planar FP32 [B][3][R][R]
 cudaError_t unpack_output(const float *o, float *out, int B, int R, cudaStream_t st);

@@ -148,7 +148,11 @@ __global__ void __launch_bounds__(256) conv_kernel(ConvArgs a) {
                     v0 += s.x;
                     v1 += s.y;
                 }
-                if (a.out) *reinterpret_cast<__nv_bfloat162 *>(a.out + m * a.N + col) = __floats2bfloat162_rn(v0, v1);
+                const __nv_bfloat162 zb = __floats2bfloat162_rn(v0, v1);
+                if (a.out) *reinterpret_cast<__nv_bfloat162 *>(a.out + m * a.N + col) = zb;
+                if (a.act)
+                    *reinterpret_cast<__nv_bfloat162 *>(a.act + m * a.N + col) =
+                        __halves2bfloat162(silu_bf16(__low2bfloat16(zb)), silu_bf16(__high2bfloat16(zb)));
                 if (a.outf) {
                     if (col < a.nf) a.outf[m * a.nf + col] = v0;
                     if (col + 1 < a.nf) a.outf[m * a.nf + col + 1] = v1;
@@ -255,93 +259,138 @@ __global__ void bias_grad_kernel(const bf16 *dZ, long long P, int Cout, int cout
 
 // ------------------------------------------------------------- elementwise
 
-__device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + expf(-z)); }
+__device__ __forceinline__ float sigm(float z) { return net_sigmoid(z); }
 
 __global__ void silu_fwd_kernel(const bf16 *z, bf16 *y, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float v = __bfloat162float(z[i]);
-        y[i] = __float2bfloat16_rn(v * sigm(v));
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = silu_bf16(z[i]);
+}
+
+// The elementwise kernels below move 8 BF16 channels (16 bytes) per thread
+// and step: C is a multiple of 32, so a group never straddles two pixels.
+typedef uint4 bf16x8;
+
+__device__ __forceinline__ void unpack8(const bf16x8 &w, float f[8]) {
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&w);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float2 t = __bfloat1622float2(h[e]);
+        f[2 * e] = t.x;
+        f[2 * e + 1] = t.y;
+    }
+}
+__device__ __forceinline__ bf16x8 pack8(const float f[8]) {
+    bf16x8 w;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&w);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+    return w;
+}
+
+// dz = dy silu'(z), silu'(z) = s (1 + z (1 - s)), s = sigmoid(z); n8 = n / 8
+__global__ void silu_bwd_kernel(const bf16x8 *z, const bf16x8 *dy, bf16x8 *dz, long long n8) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += (long long)gridDim.x * blockDim.x) {
+        float a[8], b[8];
+        unpack8(z[i], a);
+        unpack8(dy[i], b);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const float sg = sigm(a[e]);
+            b[e] = b[e] * sg * (1.0f + a[e] * (1.0f - sg));
+        }
+        dz[i] = pack8(b);
     }
 }
 
-__global__ void silu_bwd_kernel(const bf16 *z, const bf16 *dy, bf16 *dz, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float v = __bfloat162float(z[i]);
-        const float s = sigm(v);
-        dz[i] = __float2bfloat16_rn(__bfloat162float(dy[i]) * s * (1.0f + v * (1.0f - s)));
-    }
-}
-
-// x [B][R][R][C] -> y [B][R/2][R/2][C]
-__global__ void pool_fwd_kernel(const bf16 *x, bf16 *y, int B, int R, int C) {
+// x [B][R][R][C] -> y [B][R/2][R/2][C]; C8 = C / 8
+__global__ void pool_fwd_kernel(const bf16x8 *x, bf16x8 *y, int B, int R, int C8) {
     const int h = R / 2;
-    const long long n = (long long)B * h * h * C;
+    const long long n = (long long)B * h * h * C8;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long t = i / C;
+        const int c = (int)(i % C8);
+        long long t = i / C8;
         const int xo = (int)(t % h);
         t /= h;
         const int yo = (int)(t % h);
         const long long b = t / h;
-        const long long base = ((b * R + 2 * yo) * R + 2 * xo) * C + c;
-        const float s = __bfloat162float(x[base]) + __bfloat162float(x[base + C]) +
-                        __bfloat162float(x[base + (long long)R * C]) + __bfloat162float(x[base + (long long)R * C + C]);
-        y[i] = __float2bfloat16_rn(0.25f * s);
+        const long long base = ((b * R + 2 * yo) * R + 2 * xo) * C8 + c;
+        float p[8], q[8], r[8], u[8];
+        unpack8(x[base], p);
+        unpack8(x[base + C8], q);
+        unpack8(x[base + (long long)R * C8], r);
+        unpack8(x[base + (long long)R * C8 + C8], u);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) p[e] = 0.25f * (p[e] + q[e] + r[e] + u[e]);
+        y[i] = pack8(p);
     }
 }
 
 // dy [B][R/2][R/2][C] -> dx [B][R][R][C] = dy / 4 on each 2 x 2 block
-__global__ void pool_bwd_kernel(const bf16 *dy, bf16 *dx, int B, int R, int C) {
-    const long long n = (long long)B * R * R * C;
+__global__ void pool_bwd_kernel(const bf16x8 *dy, bf16x8 *dx, int B, int R, int C8) {
+    const long long n = (long long)B * R * R * C8;
     const int h = R / 2;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long t = i / C;
+        const int c = (int)(i % C8);
+        long long t = i / C8;
         const int x = (int)(t % R);
         t /= R;
         const int y = (int)(t % R);
         const long long b = t / R;
-        dx[i] = __float2bfloat16_rn(0.25f * __bfloat162float(dy[((b * h + y / 2) * h + x / 2) * C + c]));
+        float f[8];
+        unpack8(dy[((b * h + y / 2) * h + x / 2) * C8 + c], f);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] *= 0.25f;
+        dx[i] = pack8(f);
     }
 }
 
 // x [B][R][R][C] -> y [B][2R][2R][C] (nearest)
-__global__ void up_fwd_kernel(const bf16 *x, bf16 *y, int B, int R, int C) {
+__global__ void up_fwd_kernel(const bf16x8 *x, bf16x8 *y, int B, int R, int C8) {
     const int R2 = 2 * R;
-    const long long n = (long long)B * R2 * R2 * C;
+    const long long n = (long long)B * R2 * R2 * C8;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long t = i / C;
+        const int c = (int)(i % C8);
+        long long t = i / C8;
         const int xo = (int)(t % R2);
         t /= R2;
         const int yo = (int)(t % R2);
         const long long b = t / R2;
-        y[i] = x[((b * R + yo / 2) * R + xo / 2) * C + c];
+        y[i] = x[((b * R + yo / 2) * R + xo / 2) * C8 + c];
     }
 }
 
 // dy [B][2R][2R][C] -> dx [B][R][R][C] = sum of the four children
-__global__ void up_bwd_kernel(const bf16 *dy, bf16 *dx, int B, int R, int C) {
+__global__ void up_bwd_kernel(const bf16x8 *dy, bf16x8 *dx, int B, int R, int C8) {
     const int R2 = 2 * R;
-    const long long n = (long long)B * R * R * C;
+    const long long n = (long long)B * R * R * C8;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long t = i / C;
+        const int c = (int)(i % C8);
+        long long t = i / C8;
         const int x = (int)(t % R);
         t /= R;
         const int y = (int)(t % R);
         const long long b = t / R;
-        const long long base = ((b * R2 + 2 * y) * R2 + 2 * x) * C + c;
-        const float s = __bfloat162float(dy[base]) + __bfloat162float(dy[base + C]) +
-                        __bfloat162float(dy[base + (long long)R2 * C]) +
-                        __bfloat162float(dy[base + (long long)R2 * C + C]);
-        dx[i] = __float2bfloat16_rn(s);
+        const long long base = ((b * R2 + 2 * y) * R2 + 2 * x) * C8 + c;
+        float p[8], q[8], r[8], u[8];
+        unpack8(dy[base], p);
+        unpack8(dy[base + C8], q);
+        unpack8(dy[base + (long long)R2 * C8], r);
+        unpack8(dy[base + (long long)R2 * C8 + C8], u);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) p[e] = p[e] + q[e] + r[e] + u[e];
+        dx[i] = pack8(p);
     }
 }
 
-__global__ void add_kernel(bf16 *dst, const bf16 *src, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        dst[i] = __float2bfloat16_rn(__bfloat162float(dst[i]) + __bfloat162float(src[i]));
+__global__ void add_kernel(bf16x8 *dst, const bf16x8 *src, long long n8) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += (long long)gridDim.x * blockDim.x) {
+        float a[8], b[8];
+        unpack8(dst[i], a);
+        unpack8(src[i], b);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) a[e] += b[e];
+        dst[i] = pack8(a);
+    }
 }
 
 __global__ void pack_input_kernel(const float *in, bf16 *x, int B, int R) {
@@ -352,7 +401,8 @@ __global__ void pack_input_kernel(const float *in, bf16 *x, int B, int R) {
         const int s = (int)(p - b * RR);
         bf16 *o = x + p * 32;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) o[c] = __float2bfloat16_rn(c < 4 ? in[(b * 4 + c) * RR + s] : 0.0f);
+        for (int c = 0; c < 32; ++c)
+            o[c] = __float2bfloat16_rn(c < NET_IN_PLANES ? in[(b * NET_IN_PLANES + c) * RR + s] : 0.0f);
     }
 }
 
@@ -467,27 +517,40 @@ cudaError_t silu_forward(const bf16 *z, bf16 *y, long long n, cudaStream_t st) {
     return cudaGetLastError();
 }
 cudaError_t silu_backward(const bf16 *z, const bf16 *dy, bf16 *dz, long long n, cudaStream_t st) {
-    silu_bwd_kernel<<<blocks_for(n), 256, 0, st>>>(z, dy, dz, n);
+    if (n % 8) return cudaErrorInvalidValue;
+    silu_bwd_kernel<<<blocks_for(n / 8), 256, 0, st>>>(reinterpret_cast<const bf16x8 *>(z),
+                                                      reinterpret_cast<const bf16x8 *>(dy),
+                                                      reinterpret_cast<bf16x8 *>(dz), n / 8);
     return cudaGetLastError();
 }
 cudaError_t pool_forward(const bf16 *x, bf16 *y, int B, int R, int C, cudaStream_t st) {
-    pool_fwd_kernel<<<blocks_for((long long)B * R * R * C / 4), 256, 0, st>>>(x, y, B, R, C);
+    if (C % 8) return cudaErrorInvalidValue;
+    pool_fwd_kernel<<<blocks_for((long long)B * R * R * C / 32), 256, 0, st>>>(
+        reinterpret_cast<const bf16x8 *>(x), reinterpret_cast<bf16x8 *>(y), B, R, C / 8);
     return cudaGetLastError();
 }
 cudaError_t pool_backward(const bf16 *dy, bf16 *dx, int B, int R, int C, cudaStream_t st) {
-    pool_bwd_kernel<<<blocks_for((long long)B * R * R * C), 256, 0, st>>>(dy, dx, B, R, C);
+    if (C % 8) return cudaErrorInvalidValue;
+    pool_bwd_kernel<<<blocks_for((long long)B * R * R * C / 8), 256, 0, st>>>(
+        reinterpret_cast<const bf16x8 *>(dy), reinterpret_cast<bf16x8 *>(dx), B, R, C / 8);
     return cudaGetLastError();
 }
 cudaError_t up_forward(const bf16 *x, bf16 *y, int B, int R, int C, cudaStream_t st) {
-    up_fwd_kernel<<<blocks_for((long long)B * R * R * C * 4), 256, 0, st>>>(x, y, B, R, C);
+    if (C % 8) return cudaErrorInvalidValue;
+    up_fwd_kernel<<<blocks_for((long long)B * R * R * C / 2), 256, 0, st>>>(
+        reinterpret_cast<const bf16x8 *>(x), reinterpret_cast<bf16x8 *>(y), B, R, C / 8);
     return cudaGetLastError();
 }
 cudaError_t up_backward(const bf16 *dy, bf16 *dx, int B, int R, int C, cudaStream_t st) {
-    up_bwd_kernel<<<blocks_for((long long)B * R * R * C), 256, 0, st>>>(dy, dx, B, R, C);
+    if (C % 8) return cudaErrorInvalidValue;
+    up_bwd_kernel<<<blocks_for((long long)B * R * R * C / 8), 256, 0, st>>>(
+        reinterpret_cast<const bf16x8 *>(dy), reinterpret_cast<bf16x8 *>(dx), B, R, C / 8);
     return cudaGetLastError();
 }
 cudaError_t add_inplace(bf16 *dst, const bf16 *src, long long n, cudaStream_t st) {
-    add_kernel<<<blocks_for(n), 256, 0, st>>>(dst, src, n);
+    if (n % 8) return cudaErrorInvalidValue;
+    add_kernel<<<blocks_for(n / 8), 256, 0, st>>>(reinterpret_cast<bf16x8 *>(dst),
+                                                  reinterpret_cast<const bf16x8 *>(src), n / 8);
     return cudaGetLastError();
 }
 cudaError_t pack_input(const float *in, bf16 *x, int B, int R, cudaStream_t st) {

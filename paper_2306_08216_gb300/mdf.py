@@ -118,6 +118,7 @@ _SIGNATURES = [
     ("mdf_net_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     ("mdf_net_destroy", None, [ctypes.c_void_p]),
     ("mdf_net_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("mdf_net_set_conv_kernel", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("mdf_net_param_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("mdf_net_layer_count", ctypes.c_int, [ctypes.c_void_p]),
     ("mdf_net_layer_shape", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),

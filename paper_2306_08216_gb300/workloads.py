@@ -15,8 +15,9 @@ Grids: uniform, tanh-stretched (separable) and a trapezoid mapped from the
 unit square (curvilinear).
 
 Warm-start network inputs (the network is the project's extension, not the
-paper's): seeded initial parameters, the four input planes of a cavity
-(Re, power-law index, node coordinates) and seeded (Re, n) draws.
+paper's): seeded initial parameters, the eight input planes of a cavity
+(Re, power-law index, node coordinates, metric coefficients) and seeded
+(Re, n) draws.
 """
 import math
 
@@ -220,22 +221,39 @@ def warm_start_draws(count, seed):
     return re, n
 
 
-def warm_start_inputs(re, n_index, R):
-    """Input planes [B][4][R][R] (float32) of the warm-start network: the
+WARM_IN_PLANES = 8
+
+
+def warm_start_inputs(re, n_index, R, geometry="square"):
+    """Input planes [B][8][R][R] (float32) of the warm-start network: the
     scaled log Reynolds number and power-law index (each mapped to [-1, 1]
-    over the training ranges) and the node coordinates x_i = i/(R-1),
-    y_j = j/(R-1) of the square cavity."""
+    over the training ranges), the node coordinates x, y of the cavity grid
+    and its four metric coefficients xi_x, xi_y, eta_x, eta_y, the
+    derivatives of the computational coordinates xi = i/(R-1), eta = j/(R-1)
+    with respect to x and y.  geometry "square": the unit square (x = xi,
+    y = eta, metrics 1, 0, 0, 1); "trapezoid": trapezoid_grid(R, R) and its
+    exact metrics; or a sequence of those names, one per sample."""
     re = np.atleast_1d(np.asarray(re, dtype=np.float64))
     n_index = np.atleast_1d(np.asarray(n_index, dtype=np.float64))
+    geo = [geometry] * re.size if isinstance(geometry, str) else list(geometry)
+    assert len(geo) == re.size
     lo, hi = math.log(WARM_RE_RANGE[0]), math.log(WARM_RE_RANGE[1])
     a = 2.0 * (np.log(re) - lo) / (hi - lo) - 1.0
     b = 2.0 * (n_index - WARM_N_RANGE[0]) / (WARM_N_RANGE[1] - WARM_N_RANGE[0]) - 1.0
+    planes = {}
     X, Y = np.meshgrid(np.arange(R) / (R - 1.0), np.arange(R) / (R - 1.0))
-    out = np.empty((re.size, 4, R, R), dtype=np.float32)
-    out[:, 0] = a[:, None, None]
-    out[:, 1] = b[:, None, None]
-    out[:, 2] = X
-    out[:, 3] = Y
+    one, zero = np.ones_like(X), np.zeros_like(X)
+    planes["square"] = (X, Y, one, zero, zero, one)
+    if "trapezoid" in geo:
+        Xt, Yt = trapezoid_grid(R, R)
+        m = trapezoid_metrics(R, R)  # d(index)/dx: divide by R - 1 for d(xi)/dx
+        planes["trapezoid"] = (Xt, Yt) + tuple(c / (R - 1.0) for c in m)
+    out = np.empty((re.size, WARM_IN_PLANES, R, R), dtype=np.float32)
+    for k in range(re.size):
+        out[k, 0] = a[k]
+        out[k, 1] = b[k]
+        for c, plane in enumerate(planes[geo[k]]):
+            out[k, 2 + c] = plane
     return out
 
 

@@ -139,3 +139,23 @@ def test_quantized_forward_is_close_to_fp64():
     a, b = N.forward(p, x), N.forward(p, x, quantize=True)
     rel = np.linalg.norm(a - b) / np.linalg.norm(a)
     assert 0 < rel < 0.05  # BF16 storage of ~15 layers: percent level
+
+
+def test_input_planes_of_the_two_geometries():
+    """The eight input planes: the metric coefficients are derivatives of the
+    normalised computational coordinates (1, 0, 0, 1 on the unit square), so
+    both geometries give O(1) inputs; on the trapezoid (bottom 0.5, lid 1)
+    xi_x = 1 / width runs from 2 at the bottom to 1 at the lid, eta_x = 0,
+    eta_y = 1, and xi_y is odd about the centre line."""
+    R = 16
+    x = W.warm_start_inputs([300.0, 300.0], [0.8, 0.8], R, geometry=["square", "trapezoid"])
+    assert x.shape == (2, N.IN_PLANES, R, R)
+    sq, tr = x[0], x[1]
+    np.testing.assert_array_equal(sq[4:], np.stack([np.ones((R, R)), np.zeros((R, R)), np.zeros((R, R)),
+                                                    np.ones((R, R))]).astype(np.float32))
+    np.testing.assert_allclose(tr[4][0], 2.0, rtol=1e-6)
+    np.testing.assert_allclose(tr[4][-1], 1.0, rtol=1e-6)
+    np.testing.assert_allclose(tr[6], 0.0, atol=1e-7)
+    np.testing.assert_allclose(tr[7], 1.0, rtol=1e-6)
+    np.testing.assert_allclose(tr[5], -tr[5][:, ::-1], atol=1e-6)
+    np.testing.assert_allclose(tr[3][:, 0], np.arange(R) / (R - 1.0), rtol=1e-6)
