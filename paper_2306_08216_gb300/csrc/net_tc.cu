@@ -162,13 +162,15 @@ struct TcTile {
     int Wx, Hy, Bn;  // the 128-pixel tile as columns x rows x images
 };
 
-// Shared memory of one CTA: STAGES ring slots of (A box, W box), 1024-byte
-// aligned for the swizzle, then the barriers.
-template <int BN, int BKC, int STAGES>
+// Shared memory of one CTA: STAGES ring slots of G (A box, W box) pairs,
+// 1024-byte aligned for the swizzle, then the barriers.
+template <int BN, int BKC, int STAGES, int G, int MT>
 struct TcSmem {
-    static constexpr int A_BYTES = TC_BM * BKC * 2;
+    static constexpr int SUBTILE = TC_BM * BKC * 2;  // one M = 128 block of an A box
+    static constexpr int A_BYTES = MT * SUBTILE;
     static constexpr int B_BYTES = BN * BKC * 2;
-    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int SUB = A_BYTES + B_BYTES;  // one K step: (A box, W box)
+    static constexpr int STAGE = G * SUB;         // a ring slot holds G K steps
     static constexpr int BARS = STAGES * STAGE;
     // full[STAGES], empty[STAGES], tfull[2], tempty[2], drain; TMEM address
     static constexpr int NBAR = 2 * STAGES + 5;
@@ -199,11 +201,13 @@ __device__ __forceinline__ bool mb_wait_f(uint64_t *bar, uint32_t parity, volati
 //                    activation, BF16/FP32 stores, then release the
 //                    accumulator (tempty) so the MMAs of tile t + 2 may use it.
 // The epilogue of one tile overlaps the copies and MMAs of the next.
-template <int BN, int BKC, int STAGES>
+template <int BN, int BKC, int STAGES, int G, int MT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap,
                    const ConvArgs a, int ntiles, int ntn, int *err) {
-    using S = TcSmem<BN, BKC, STAGES>;
+    using S = TcSmem<BN, BKC, STAGES, G, MT>;
+    constexpr int BMT = TC_BM * MT;      // pixels of a tile (MT blocks of 128)
+    constexpr int ACC = MT * BN;         // TMEM columns of one accumulator
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -221,7 +225,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int R = a.R, RR = R * R;
     const long long M = (long long)a.B * RR;
     const int kchunks = a.Cx / BKC;
-    const int nk = 9 * kchunks;
+    const int nk = 9 * kchunks;         // K steps of a tile
+    const int ns = (nk + G - 1) / G;    // ring slots of a tile (the last may hold fewer steps)
 
     if (tid == 0) {
         s_fail = 0;
@@ -237,7 +242,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mb_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
+    if (warp == 1) tmem_alloc(tmem_slot, 2 * ACC);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -248,22 +253,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // ---- TMA producer
             int k = 0;
             for (int tile = blockIdx.x; tile < ntiles && !*fail; tile += gridDim.x) {
-                const long long m0 = (long long)(tile / ntn) * TC_BM;
+                const long long m0 = (long long)(tile / ntn) * BMT;
                 const int n0 = (tile % ntn) * BN;
                 const int b0 = (int)(m0 / RR);
                 const int rem = (int)(m0 - (long long)b0 * RR);
                 const int y0 = rem / R, x0 = rem - y0 * R;
-                for (int i = 0; i < nk; ++i, ++k) {
+                for (int j = 0; j < ns; ++j, ++k) {
                     const int s = k % STAGES;
                     if (k >= STAGES && !mb_wait_f(&empty[s], (uint32_t)(((k / STAGES) - 1) & 1), fail)) {
                         *fail = 1;
                         break;
                     }
-                    const int tap = i / kchunks, c0 = (i - tap * kchunks) * BKC;
+                    const int g = nk - j * G < G ? nk - j * G : G;
                     unsigned char *sa = smem + s * S::STAGE;
-                    mb_expect_tx(&full[s], S::STAGE);
-                    tma_load_4d(&xmap, &full[s], sa, c0, x0 + tap % 3 - 1, y0 + tap / 3 - 1, b0);
-                    tma_load_3d(&wmap, &full[s], sa + S::A_BYTES, c0, tap, n0);
+                    mb_expect_tx(&full[s], (uint32_t)(g * S::SUB));
+                    for (int u = 0; u < g; ++u) {
+                        const int i = j * G + u;
+                        const int tap = i / kchunks, c0 = (i - tap * kchunks) * BKC;
+                        tma_load_4d(&xmap, &full[s], sa + u * S::SUB, c0, x0 + tap % 3 - 1, y0 + tap / 3 - 1, b0);
+                        tma_load_3d(&wmap, &full[s], sa + u * S::SUB + S::A_BYTES, c0, tap, n0);
+                    }
                     s_issued = k + 1;
                 }
             }
@@ -271,7 +280,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer
-            constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
+            constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);  // every MMA is M = 128
             int k = 0, t = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++t) {
@@ -281,8 +290,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(acc * BN);
-                for (int i = 0; i < nk; ++i, ++k) {
+                const uint32_t d = tmem + (uint32_t)(acc * ACC);
+                for (int j = 0; j < ns; ++j, ++k) {
                     const int s = k % STAGES;
                     if (!mb_wait_f(&full[s], (uint32_t)((k / STAGES) & 1), fail)) {
                         ok = false;
@@ -290,11 +299,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     s_consumed = k + 1;
                     tc_fence_after();
-                    const uint32_t sa = s_u32(smem + s * S::STAGE);
-                    const uint64_t ad = kmajor_desc<BKC>(sa), bd = kmajor_desc<BKC>(sa + S::A_BYTES);
+                    const int g = nk - j * G < G ? nk - j * G : G;
+                    for (int u = 0; u < g; ++u) {
+                        const uint32_t sa = s_u32(smem + s * S::STAGE + u * S::SUB);
+                        const uint64_t bd = kmajor_desc<BKC>(sa + S::A_BYTES);
+                        const int i = j * G + u;
 #pragma unroll
-                    for (int kk = 0; kk < BKC / 16; ++kk)  // K = 16 is 32 bytes along the swizzled row
-                        umma_f16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (i | kk) != 0);
+                        for (int mb = 0; mb < MT; ++mb) {  // the 128-pixel blocks share the W box
+                            const uint64_t ad = kmajor_desc<BKC>(sa + mb * S::SUBTILE);
+#pragma unroll
+                            for (int kk = 0; kk < BKC / 16; ++kk)  // K = 16 is 32 bytes along the swizzled row
+                                umma_f16(d + (uint32_t)(mb * BN), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
+                                         idesc, (i | kk) != 0);
+                        }
+                    }
                     umma_commit(&empty[s]);
                 }
                 if (!ok) break;
@@ -321,14 +339,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 break;
             }
             tc_fence_after();
-            const long long m = (long long)(tile / ntn) * TC_BM + q * 32 + lane;
             const int n0 = (tile % ntn) * BN;
-            const bool mv = m < M;
+#pragma unroll 1
+            for (int mb = 0; mb < MT; ++mb)
 #pragma unroll 1
             for (int c = c_lo; c < c_lo + BN / 2; c += 16) {
+                const long long m = (long long)(tile / ntn) * BMT + mb * TC_BM + q * 32 + lane;
+                const bool mv = m < M;
                 float v[16];
                 __syncwarp();  // tcgen05.ld is warp-collective
-                tmem_ld16(tmem + (uint32_t)(acc * BN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+                tmem_ld16(tmem + (uint32_t)(acc * ACC + mb * BN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
                 const int nb = n0 + c;
                 if (!mv) continue;
                 if (a.bias) {
@@ -388,7 +408,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncthreads();
     }
     tc_fence_after();
-    if (warp == 1) tmem_dealloc(tmem, 2 * BN);
+    if (warp == 1) tmem_dealloc(tmem, 2 * ACC);
 }
 
 // ---- host side
@@ -409,32 +429,37 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return f;
 }
 
-// The tile shape for side R: 128 pixels as whole rows of whole images when
-// R <= 128, a 128-column piece of one row otherwise.
-bool tile_for(int R, TcTile *t) {
-    if (R <= 0 || (R & (R - 1))) return false;  // powers of two only
-    t->Wx = R < TC_BM ? R : TC_BM;
-    t->Hy = R < TC_BM ? (R < TC_BM / R ? R : TC_BM / R) : 1;
-    t->Bn = TC_BM / (t->Wx * t->Hy);
-    return t->Wx * t->Hy * t->Bn == TC_BM;
+// The tile shape for side R: P pixels (a power of two) as whole rows of
+// whole images when R <= P, a P-column piece of one row otherwise (each box
+// dimension at most 256).
+bool tile_for(int R, int P, TcTile *t) {
+    if (R <= 0 || (R & (R - 1)) || P <= 0 || (P & (P - 1))) return false;  // powers of two only
+    t->Wx = R < P ? R : P;
+    t->Hy = R < P ? (R < P / R ? R : P / R) : 1;
+    t->Bn = P / (t->Wx * t->Hy);
+    return t->Wx * t->Hy * t->Bn == P && t->Wx <= 256 && t->Hy <= 256 && t->Bn <= 256;
 }
 
 // CTAs per SM and ring depth.  One thread issues a CTA's copies and one its
-// MMAs, and each K step costs them a few hundred cycles of issue and
+// MMAs, and each ring slot costs them a few hundred cycles of issue and
 // barrier latency, so two CTAs per SM (two independent pipelines) run the
-// small-N layers about twice as fast as one CTA with a deeper ring; the
-// ring takes about 100 KB of shared memory per CTA (at most 16 slots).
-// BN = 256 keeps one CTA per SM (its two accumulators fill the 512 TMEM
-// columns) with a 200 KB ring.
-constexpr int tc_ctas_per_sm(int bn) { return bn <= 128 ? 2 : 1; }
-constexpr int tc_stages(int stage, int bn) {
-    return (tc_ctas_per_sm(bn) == 2 ? 100 : 200) * 1024 / stage < 16
-               ? (tc_ctas_per_sm(bn) == 2 ? 100 : 200) * 1024 / stage
+// small layers about twice as fast as one CTA with a deeper ring, and a
+// slot carries as much work as its shared memory allows: two 32-channel K
+// steps (G = 2), or MT = 4 blocks of 128 pixels that share one weight box
+// (the 32-output-channel layers).  A ring takes about 104 KB of shared
+// memory per CTA (at most 16 slots); a CTA whose two accumulators fill
+// the 512 TMEM columns (BN = 256) runs alone on its SM with a 200 KB ring.
+constexpr int tc_ctas_per_sm(int acc_cols) { return 2 * acc_cols <= 256 ? 2 : 1; }
+constexpr int tc_stages(int stage, int acc_cols) {
+    return (tc_ctas_per_sm(acc_cols) == 2 ? 104 : 200) * 1024 / stage < 16
+               ? (tc_ctas_per_sm(acc_cols) == 2 ? 104 : 200) * 1024 / stage
                : 16;
 }
 
-template <int BN, int BKC>
-cudaError_t launch_bn(const ConvArgs &a, const TcTile &tile, int num_sms, int *err, cudaStream_t st) {
+template <int BN, int BKC, int MT>
+cudaError_t launch_bn(const ConvArgs &a, int num_sms, int *err, cudaStream_t st) {
+    TcTile tile;
+    if (!tile_for(a.R, TC_BM * MT, &tile)) return cudaErrorInvalidValue;
     auto enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
     const CUtensorMapSwizzle sw = BKC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
@@ -460,9 +485,13 @@ cudaError_t launch_bn(const ConvArgs &a, const TcTile &tile, int num_sms, int *e
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
-    constexpr int STAGES = tc_stages((TC_BM + BN) * BKC * 2, BN);
-    using S = TcSmem<BN, BKC, STAGES>;
-    auto k = conv_tc_kernel<BN, BKC, STAGES>;
+    // 32-channel chunks (64-byte rows) of single-block tiles go two K steps
+    // to a ring slot, so a slot carries the same 64 channels of K as a
+    // 128-byte-row slot does
+    constexpr int G = (BKC == 32 && MT == 1) ? 2 : 1;
+    constexpr int STAGES = tc_stages(G * (TC_BM * MT + BN) * BKC * 2, MT * BN);
+    using S = TcSmem<BN, BKC, STAGES, G, MT>;
+    auto k = conv_tc_kernel<BN, BKC, STAGES, G, MT>;
     constexpr int smem = S::TOTAL;
     static std::atomic<unsigned long long> configured{0};  // devices whose attribute is set
     int dev = 0;
@@ -474,23 +503,25 @@ cudaError_t launch_bn(const ConvArgs &a, const TcTile &tile, int num_sms, int *e
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit);
     }
-    const long long mt = ((long long)a.B * a.R * a.R + TC_BM - 1) / TC_BM;
+    const long long mt = ((long long)a.B * a.R * a.R + TC_BM * MT - 1) / (TC_BM * MT);
     const int ntn = a.N / BN;
     const long long ntiles = mt * ntn;
     if (ntiles > (1ll << 30)) return cudaErrorInvalidValue;
-    long long grid = (long long)num_sms * tc_ctas_per_sm(BN);
+    long long grid = (long long)num_sms * tc_ctas_per_sm(MT * BN);
     if (grid > ntiles) grid = ntiles;
     k<<<(unsigned)grid, TC_THREADS, smem, st>>>(xmap, wmap, a, (int)ntiles, ntn, err);
     return cudaGetLastError();
 }
 
 template <int BKC>
-cudaError_t launch_bkc(const ConvArgs &a, const TcTile &tile, int bn, int num_sms, int *err, cudaStream_t st) {
+cudaError_t launch_bkc(const ConvArgs &a, int bn, int mtile, int num_sms, int *err, cudaStream_t st) {
     switch (bn) {
-        case 256: return launch_bn<256, BKC>(a, tile, num_sms, err, st);
-        case 128: return launch_bn<128, BKC>(a, tile, num_sms, err, st);
-        case 64: return launch_bn<64, BKC>(a, tile, num_sms, err, st);
-        default: return launch_bn<32, BKC>(a, tile, num_sms, err, st);
+        case 256: return launch_bn<256, BKC, 1>(a, num_sms, err, st);
+        case 128: return launch_bn<128, BKC, 1>(a, num_sms, err, st);
+        case 64: return launch_bn<64, BKC, 1>(a, num_sms, err, st);
+        default:
+            if (BKC == 32 && mtile == 4) return launch_bn<32, 32, 4>(a, num_sms, err, st);
+            return launch_bn<32, BKC, 1>(a, num_sms, err, st);
     }
 }
 
@@ -498,13 +529,12 @@ cudaError_t launch_bkc(const ConvArgs &a, const TcTile &tile, int bn, int num_sm
 
 bool conv_tc_applies(const ConvArgs &a) {
     TcTile t;
-    return tile_for(a.R, &t) && (a.Cx == 32 || a.Cx % 64 == 0) && a.N % 32 == 0 && a.N >= 32 && a.N <= 1024;
+    return tile_for(a.R, TC_BM, &t) && (a.Cx == 32 || a.Cx % 64 == 0) && a.N % 32 == 0 && a.N >= 32 &&
+           a.N <= 1024;
 }
 
 cudaError_t conv_forward_tc(const ConvArgs &a, int num_sms, int *err, cudaStream_t st) {
-    TcTile tile;
-    if (!tile_for(a.R, &tile) || !(a.Cx == 32 || a.Cx % 64 == 0) || a.N % 32 || a.N < 32)
-        return cudaErrorInvalidValue;
+    if (!conv_tc_applies(a)) return cudaErrorInvalidValue;
     const long long mt = ((long long)a.B * a.R * a.R + TC_BM - 1) / TC_BM;
     // the widest N tile (each A box read once per N tile) that still gives
     // every SM a tile
@@ -515,7 +545,13 @@ cudaError_t conv_forward_tc(const ConvArgs &a, int num_sms, int *err, cudaStream
             break;
         }
     }
-    return a.Cx == 32 ? launch_bkc<32>(a, tile, bn, num_sms, err, st) : launch_bkc<64>(a, tile, bn, num_sms, err, st);
+    // 32 output channels from 32 input channels: tiles of four 128-pixel
+    // blocks sharing the weight box, while there is at least one such tile
+    // for every CTA
+    TcTile t4;
+    const int mtile = (bn == 32 && a.Cx == 32 && tile_for(a.R, 4 * TC_BM, &t4) && mt >= 4ll * 2 * num_sms) ? 4 : 1;
+    return a.Cx == 32 ? launch_bkc<32>(a, bn, mtile, num_sms, err, st)
+                      : launch_bkc<64>(a, bn, mtile, num_sms, err, st);
 }
 
 }  // namespace mdfnet

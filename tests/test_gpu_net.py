@@ -130,6 +130,26 @@ def test_tcgen05_forward_at_the_trained_resolution():
     assert np.abs(y_tc - ref).max() <= 5e-2 * np.abs(ref).max()
 
 
+def test_tcgen05_equals_mma_sync_at_the_training_batch():
+    """R = 128 with the training batch of 16: enough pixels for the tcgen05
+    kernel's tiles of four 128-pixel blocks on the 32-channel layers and
+    its widest N tiles elsewhere.  Forward outputs equal to the bit, the
+    parameter gradient to the order of its FP32 atomic sums."""
+    R, batch = 128, 16
+    p, x, t = case(R, batch, 12)
+    net = warmstart.Net(R, batch)
+    net.set_params(p)
+    res = {}
+    for kind in ("tcgen05", "mma.sync"):
+        net.set_conv_kernel(kind)
+        res[kind] = (net.forward(x), net.gradient(x, t))
+    np.testing.assert_array_equal(res["tcgen05"][0], res["mma.sync"][0])
+    g1, g0 = res["tcgen05"][1][1], res["mma.sync"][1][1]
+    rel = float(np.linalg.norm(g1 - g0) / np.linalg.norm(g0))
+    print("batch 16 gradient rel diff %.3e" % rel)
+    assert rel <= 1e-6
+
+
 def _bias_mask():
     m = np.zeros(N.param_count(), dtype=bool)
     k = 0
