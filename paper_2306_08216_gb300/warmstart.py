@@ -605,6 +605,50 @@ def train_benchmark(R=128, batch=16, steps=50, warmup=5, seed=0, stream=None, co
             "flops_per_step": flops, "conv_kernel": conv_kernel}
 
 
+def layer_benchmark(R=128, batch=16, reps=3, seed=0, stream=None):
+    """Device time of every convolution of one forward pass, per layer and
+    for each kernel (tcgen05, mma.sync): the CUDA kernel events of
+    torch.profiler (CUPTI) over `reps` warm forward passes, median per
+    layer, with the algorithmic TFLOP/s of the layer's real channels."""
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+    net = Net(R, batch, stream=stream)
+    net.set_params(init_params(net, 2306))
+    re, nn = W.warm_start_draws(batch, seed)
+    x = torch.from_numpy(W.warm_start_inputs(re, nn, R)).cuda()
+    res = [1, 1, 2, 2, 4, 4, 8, 8, 4, 4, 2, 2, 1, 1, 1]  # resolution divisor of each layer
+    shapes = net.layer_shapes()
+    out = {}
+    for kind in ("tcgen05", "mma.sync"):
+        net.set_conv_kernel(kind)
+        for _ in range(5):
+            net.forward(x)
+        torch.cuda.synchronize()
+        runs = []
+        for _ in range(reps):
+            with profile(activities=[ProfilerActivity.CUDA]) as prof:
+                net.forward(x)
+                torch.cuda.synchronize()
+            ev = sorted((e for e in prof.events()
+                         if e.device_type == torch.autograd.DeviceType.CUDA and "conv" in e.name),
+                        key=lambda e: e.time_range.start)
+            if len(ev) == len(shapes):
+                runs.append([e.time_range.elapsed_us() for e in ev])
+        if not runs:
+            out[kind] = None
+            continue
+        us = np.median(np.array(runs), axis=0)
+        layers = []
+        for (co, ci), d, t in zip(shapes, res, us):
+            f = 2.0 * batch * (R // d) ** 2 * 9 * ci * co
+            layers.append({"cout": co, "cin": ci, "side": R // d, "us": float(t), "tflops": f / t / 1e6})
+        tot_us = float(us.sum())
+        flops = sum(2.0 * batch * (R // d) ** 2 * 9 * ci * co for (co, ci), d in zip(shapes, res))
+        out[kind] = {"layers": layers, "forward_us": tot_us, "forward_tflops": flops / tot_us / 1e6}
+    net.close()
+    return {"R": R, "batch": batch, "reps": reps, "kernels": out}
+
+
 def channel_stats(t):
     q = [0.0, 0.01, 0.5, 0.99, 1.0]
     return {name: np.quantile(t[:, c], q).tolist() for c, name in enumerate(("u", "v", "p"))}
@@ -635,10 +679,15 @@ def main(argv=None):
     ap.add_argument("--report")
     ap.add_argument("--train-bench", action="store_true",
                     help="only time mdf_net_train_step on random data (--R, --batch, --epochs = timed steps)")
+    ap.add_argument("--layer-bench", action="store_true",
+                    help="only time every convolution of one forward pass, per layer and kernel (--R, --batch)")
     args = ap.parse_args(argv)
 
     from . import build as B
     B.build()
+    if args.layer_bench:
+        print(json.dumps(layer_benchmark(args.R, args.batch)), flush=True)
+        return 0
     if args.train_bench:
         for kind in ("tcgen05", "mma.sync"):
             print(json.dumps(train_benchmark(args.R, args.batch, steps=args.epochs, conv_kernel=kind)), flush=True)
