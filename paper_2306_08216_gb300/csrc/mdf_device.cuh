@@ -70,6 +70,19 @@ __device__ __forceinline__ void sts1(unsigned char *base, int byte_off, float v)
     *reinterpret_cast<float *>(base + byte_off) = v;
 }
 
+// ------------------------------------------------- programmatic dependent launch
+
+// A kernel launched with programmatic stream serialization may start while
+// the previous kernel of its stream still runs.  grid_dependency_wait blocks
+// (in hardware, no spin of ours) until that kernel has completed and its
+// memory is visible; it must precede every global load of data the previous
+// kernel writes and every global store to memory it reads.  Launched without
+// the attribute it returns at once.  launch_dependents lets the next such
+// kernel of the stream be scheduled; it changes no ordering of memory
+// (the next kernel's own wait still covers the whole of this one).
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------ TMA, mbarrier
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {

@@ -520,6 +520,12 @@ __device__ __forceinline__ void tile_output(const StepArgs &a, int X, int Y, int
 template <int TX, int TY, int MK, bool PL, bool WALLS, int ST, bool RHO0>
 __global__ void __launch_bounds__(TX *TY, kTileMinBlocks) tile_kernel(const StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
+    // launched with programmatic stream serialization: the block touches
+    // global memory only after the previous step has completed.  The next
+    // step is released only as this one's blocks exit (no early trigger): a
+    // grid of fewer blocks than resident slots would otherwise place the
+    // next step's blocks on the SMs left free, up to three on one SM
+    grid_dependency_wait();
     tile_step<TX, TY, MK, PL, WALLS, ST, RHO0>(a, blockIdx.x, blockIdx.y, smem);
 }
 
@@ -562,7 +568,20 @@ cudaError_t tile_launch_t(const StepArgs &args, const StepPlan &plan, cudaStream
         if (e != cudaSuccess) return e;
         mark_device_setup(configured);
     }
-    k<<<dim3(plan.gx, plan.gy), kTX * kTY, smem, stream>>>(args);
+    // programmatic stream serialization: the next step's blocks are
+    // scheduled while this one drains (tile_kernel waits for it in hardware)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(plan.gx, plan.gy);
+    cfg.blockDim = dim3(kTX * kTY);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k, args);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
