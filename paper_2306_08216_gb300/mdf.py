@@ -372,16 +372,36 @@ class Solver:
         a = _Arr(fh, 10 * self.nx * self.ny)
         _check(lib().mdf_set_distributions(self._h, a.ptr, a.on_device), self._h)
 
-    def fields(self, names=None):
+    def fields(self, names=None, out=None):
+        """Derived fields as float32 [ny, nx] host arrays, by name.  `out`
+        (optional) maps names to caller-owned C-contiguous float32 host
+        arrays of that shape -- numpy arrays or CPU torch tensors, e.g. in
+        pinned memory, which the device copies into directly -- and is
+        filled and returned in their place."""
         names = FIELD_NAMES if names is None else list(names)
         mask = 0
         for nm in names:
             mask |= 1 << FIELD_NAMES.index(nm)
         order = [nm for nm in FIELD_NAMES if mask & (1 << FIELD_NAMES.index(nm))]
-        outs = [np.empty((self.ny, self.nx), dtype=np.float32) for _ in order]
+        outs = []
+        for nm in order:
+            o = None if out is None else out.get(nm)
+            if o is None:
+                o = np.empty((self.ny, self.nx), dtype=np.float32)
+            elif not isinstance(o, np.ndarray):
+                assert not _is_torch_cuda(o), "fields(out=...) takes host arrays"
+                o = o.numpy()
+            assert o.dtype == np.float32 and o.shape == (self.ny, self.nx) and o.flags["C_CONTIGUOUS"], \
+                "out[%r] must be a C-contiguous float32 array of shape %s" % (nm, (self.ny, self.nx))
+            outs.append(o)
         ptrs = (ctypes.c_void_p * len(outs))(*[o.ctypes.data_as(ctypes.c_void_p) for o in outs])
         _check(lib().mdf_fields(self._h, mask, ptrs, 0), self._h)
-        return dict(zip(order, outs))
+        res = dict(zip(order, outs))
+        if out is not None:
+            for nm in order:
+                if nm in out and not isinstance(out[nm], np.ndarray):
+                    res[nm] = out[nm]
+        return res
 
     def fields_device(self, outs):
         """outs: dict name -> float32 CUDA tensor (ny, nx); asynchronous."""

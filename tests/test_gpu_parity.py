@@ -233,6 +233,27 @@ def test_derived_fields_match_oracle():
         assert maxabs(fg[k], fo[k]) <= 2e-4 * sc, k
 
 
+def test_fields_into_caller_arrays():
+    """fields(out=...) writes into the caller's host arrays (numpy, or CPU
+    torch tensors in pinned memory) the same bits fields() returns; a
+    wrong shape or dtype is refused before any copy."""
+    nx, ny = 37, 29
+    g = mdf.Solver(nx, ny, nu=0.01, walls=(True, True), u_wall=(0, 0, 0, 0.1))
+    g.init(*W.random_fields(nx, ny, 0.02, 3))
+    g.step(40)
+    ref = g.fields(["u", "v", "P", "vorticity"])
+    pinned = {k: torch.empty((ny, nx), dtype=torch.float32).pin_memory() for k in ("u", "P")}
+    plain = {"v": np.zeros((ny, nx), np.float32)}
+    got = g.fields(["u", "v", "P", "vorticity"], out={**pinned, **plain})
+    assert got["u"] is pinned["u"] and got["v"] is plain["v"]
+    for k in ("u", "v", "P", "vorticity"):
+        np.testing.assert_array_equal(np.asarray(got[k]), ref[k])
+    with pytest.raises(AssertionError):
+        g.fields(["u"], out={"u": np.zeros((nx, ny), np.float32)})
+    with pytest.raises(AssertionError):
+        g.fields(["u"], out={"u": np.zeros((ny, nx), np.float64)})
+
+
 # --------------------------------------------------------- residual & drift
 
 
