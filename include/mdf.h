@@ -229,7 +229,10 @@ mdf_status mdf_step(mdf_ctx *ctx, int n);
 
 /* Derived fields from the current state (Sec. 2.4).  mask selects fields by
  * bit, out[] holds one nx*ny FP32 array per set bit in increasing bit order.
- * Host outputs (on_device = 0) are complete on return. */
+ * Host outputs (on_device = 0) are complete on return; each is one
+ * device-to-host copy into the caller's array, at full link speed when the
+ * caller's memory is pinned (page-locked), staged by the driver otherwise.
+ * The same holds for the host inputs of mdf_init_fields. */
 enum {
     MDF_FIELD_U = 1u << 0, MDF_FIELD_V = 1u << 1, MDF_FIELD_P = 1u << 2,        /* Eq. 2.3.23 */
     MDF_FIELD_DUDX = 1u << 3, MDF_FIELD_DUDY = 1u << 4,                          /* Eq. 2.4.1 */
