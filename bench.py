@@ -234,10 +234,12 @@ def batch_problems(count=BATCH_COUNT, seed=BATCH_SEED, u0=0.1):
     return probs
 
 
-def batch_benchmark(mdf, torch, stream, steps=200, solo_sample=16, count=BATCH_COUNT):
+def batch_benchmark(mdf, torch, stream, steps=200, solo_sample=BATCH_COUNT, count=BATCH_COUNT):
     """Throughput of the batched step over the seeded 512-cavity sweep, against
-    the same cavities stepped one problem per launch (timed on a sample of
-    `solo_sample` cavities and scaled by node count)."""
+    the same cavities stepped one problem per launch, each by its own
+    autotuned single-problem solver for the same steps (every cavity by
+    default; with solo_sample < count a sample spread over the sweep, scaled
+    by node count)."""
     probs = batch_problems(count)
     t0 = time.perf_counter()
     batch = mdf.Batch(probs, stream=stream)
@@ -280,7 +282,8 @@ def batch_benchmark(mdf, torch, stream, steps=200, solo_sample=16, count=BATCH_C
         b16.close()
     batch_kernel = info["kernel"]
     batch.close()
-    # one-problem-per-launch reference on a sample, largest and smallest mixed
+    # one-problem-per-launch reference: every cavity, or a sample spread over
+    # the sweep (largest and smallest mixed)
     idx = list(range(0, len(probs), max(1, len(probs) // solo_sample)))[:solo_sample]
     solo_nodes, solo_ms = 0, 0.0
     for i in idx:
@@ -569,6 +572,9 @@ def main():
     ap.add_argument("--no-rho0", action="store_true", help="skip the run with the alpha = 0 distribution")
     ap.add_argument("--launch", default=None,
                     help="threads,rows_per_block: pin the launch plan instead of the autotuned one (profiling)")
+    ap.add_argument("--batch-solo-sample", type=int, default=0,
+                    help="time the one-launch-per-problem reference of the batch on this many cavities "
+                         "(0: every cavity of the sweep)")
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT,
                     help="cavities of the batched sweep (default 512; fewer only for profiling)")
     ap.add_argument("--nx", type=int, default=NX,
@@ -658,7 +664,8 @@ def main():
     rho0 = None if args.no_rho0 else rho0_benchmark(mdf, W, torch, stream, nx)
 
     # ---- batched sweep: many cavities, one launch per step
-    batch = None if args.no_batch else batch_benchmark(mdf, torch, stream, count=args.batch_count)
+    batch = None if args.no_batch else batch_benchmark(
+        mdf, torch, stream, count=args.batch_count, solo_sample=args.batch_solo_sample or args.batch_count)
 
     # ---- power-law cavities on the body-fitted trapezoid grid
     body = None if args.no_body_fitted else body_fitted_benchmark(mdf, W, torch, stream)
