@@ -334,6 +334,31 @@ def test_poiseuille_refinement_reduces_error():
     assert errs[1] < 0.6 * errs[0]
 
 
+def test_poiseuille_error_is_independent_of_the_force_as_in_table2():
+    """Table 2 (nu = 0.01, 32 x 32): the GRE stays at 6.2e-4 for F from 1e-3
+    to 1e-6 and moves slightly at F = 1e-2 -- the developed channel flow has
+    no convective term, so to first order its discrete steady state scales
+    with F and the relative error does not depend on it; what remains comes
+    from the equilibria's velocity products and grows as F^2 (second order
+    in the Mach number).  The oracle: the same GRE at F = 1e-3 and 1e-5 to
+    1e-6 relative, and a deviation at F = 1e-2 about 100 times the one at
+    1e-3 (a force term entering at the wrong power, or a velocity product
+    that should vanish in the developed flow, breaks one of the two)."""
+    n, nu = 32, 0.01
+    errs = []
+    for F in (1e-2, 1e-3, 1e-5):
+        o = Oracle(n, n, nu=nu, walls=(False, True), force=(F, 0.0), cfl=0.5)
+        z = np.zeros((n, n))
+        o.init(z, z, z)
+        o.step(int(15 / (nu * math.pi ** 2) / o.dt) + 1)
+        ue, _ = W.poiseuille_exact(W.wall_nodes(n, 1.0), F, nu)
+        errs.append(gre(o.fields()["u"], np.broadcast_to(ue[:, None], (n, n))))
+    e2, e3, e5 = errs
+    assert abs(e3 - e5) < 1e-6 * e5, errs
+    assert abs(e2 - e5) < 1e-3 * e5, errs
+    assert 50 < abs(e2 - e5) / abs(e3 - e5) < 200, errs
+
+
 def test_poiseuille_diverges_where_table2_diverges():
     """Table 2: at nu = 1e-3 and F = 1e-1 on 32 x 32 the scheme diverges."""
     n = 32
